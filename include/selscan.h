@@ -1,0 +1,190 @@
+/*
+ * selscan_gb300 — C ABI of the GB300 (sm_103a) EHH / iHS / XPEHH scan library.
+ *
+ * The statistics are those of selscan (Szpiech & Hernandez, arXiv:1403.6854):
+ *   EHH    Eq. 1   whole-sample extended haplotype homozygosity
+ *   EHH_c  Eq. 3   EHH of the carriers of core allele c
+ *   iHH_c  Eq. 4   trapezoid integral of EHH_c over the genetic map, both ways
+ *   iHS    Sec 1.2 ln(iHH_1 / iHH_0) (unstandardised; opposite sign to Voight)
+ *   XPEHH  Eq. 5 / Sec 1.3  ln(iHH_A / iHH_B), both sums truncated where the
+ *          EHH of the pooled A+B sample falls below the cutoff
+ * with the Section 1.2 rules: sums truncated once EHH < cutoff, the genetic
+ * step scaled by gap_scale/b when the physical gap b exceeds gap_scale, the
+ * locus aborted at a gap b > max_gap or at the end of the marker array, and
+ * no iHS at cores whose minor allele frequency is below the MAF cutoff.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Haplotype matrix ("rows"): marker-major, row k starts at rows + k * ld
+ * (ld >= W words, W = ceil(n / 64)); haplotype h is bit (h % 64) of word
+ * h / 64, bit value 1 = derived allele, 0 = ancestral.  Pad bits above n in
+ * the last word are ignored (masked by the library).  For XPEHH a row holds
+ * the W_A words of population A followed by the W_B words of population B
+ * (each population starts on a word boundary; ld >= W_A + W_B).
+ * Positions: int64 bp, non-decreasing.  Genetic map: double, non-decreasing,
+ * in the caller's units (cM by convention); g(x_{i-1}, x_i) = |map difference|.
+ * Walk directions: 0 = toward lower marker indices, 1 = toward higher.
+ * Walk step i = 0 is the core itself; `stop` is the step at which a walk
+ * ended: the first i >= 1 with EHH < cutoff (status OK), the step whose gap
+ * exceeded max_gap (ABORT_GAP), or the first step past the array end
+ * (ABORT_EDGE).  The term of the step that crosses the cutoff is not summed
+ * unless include_crossing_term is set.  digest = sum over the computed steps
+ * of (i + 1) * S(i) mod 2^64, where S(i) = sum over distinct extended
+ * haplotypes of C(n_h, 2) — an exact integer fingerprint of the EHH numerators.
+ *
+ * Memory: every pointer passed to a scan entry point is DEVICE memory owned by
+ * the caller (inputs, outputs and the workspace).  The library allocates and
+ * frees nothing.  All scan calls are asynchronous on the given stream
+ * (a cudaStream_t passed as void*; NULL = the legacy default stream); results
+ * and the device error word are valid after the stream is synchronised.
+ * Calls that share a workspace must be ordered on one stream.
+ *
+ * Errors: entry points return SELSCAN_OK (0) or a negative SELSCAN_ERR_*
+ * code for problems visible on the host (bad sizes, null pointers, a bad
+ * rational, a short workspace, a failed launch).  Problems found on the
+ * device (decreasing positions or map, a watchdog timeout) are written to the
+ * output's `error` word (0 = none) instead.  Per-locus outcomes are status
+ * codes, not errors.  No C++ exception crosses this boundary.
+ *
+ * Limits: n (iHS) and n_A + n_B (XPEHH) at most 65,535 haplotypes; m < 2^30
+ * markers.
+ */
+#ifndef SELSCAN_GB300_H
+#define SELSCAN_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ---- */
+#define SELSCAN_OK                 0
+#define SELSCAN_ERR_INVALID_ARG   -1  /* null pointer, n < 2, m < 1, bad rational, ld < W, limits */
+#define SELSCAN_ERR_UNSORTED      -2  /* (device error word) positions or map decrease */
+#define SELSCAN_ERR_WORKSPACE     -3  /* ws_bytes < selscan_workspace_bytes(...) */
+#define SELSCAN_ERR_CUDA          -4  /* a kernel launch or CUDA runtime call failed */
+#define SELSCAN_ERR_TIMEOUT       -5  /* (device error word) a bounded device wait gave up */
+#define SELSCAN_ERR_UNSUPPORTED   -6  /* no sm_103a device, or a launch shape it cannot run */
+
+/* ---- per-locus status (Section 1.2 rules) ---- */
+#define SELSCAN_LOCUS_OK            0
+#define SELSCAN_LOCUS_MAF_FILTERED  1  /* core MAF below the cutoff: not walked, no score */
+#define SELSCAN_LOCUS_UNDEFINED     2  /* n_c < 2 or an iHH of 0: ratio undefined */
+#define SELSCAN_LOCUS_ABORT_EDGE    3  /* a walk reached the array end with EHH >= cutoff */
+#define SELSCAN_LOCUS_ABORT_GAP     4  /* a walk met a gap b > max_gap while running */
+
+/* Statistic parameters (Section 1.2, "flexible parameters").  Cutoffs are
+ * rationals so that "EHH < cutoff" and "MAF < cutoff" are decided exactly in
+ * integers (den * S < num * C(N,2); den * minor < num * n). */
+typedef struct {
+    uint32_t ehh_cut_num, ehh_cut_den;   /* EHH truncation, default 1/20 */
+    uint32_t maf_num, maf_den;           /* core MAF cutoff, default 1/20 */
+    int64_t gap_scale_bp;                /* default 20000: b > 20 kbp => g * 20/b */
+    int64_t max_gap_bp;                  /* default 200000: b > 200 kbp => abort */
+    int32_t include_crossing_term;       /* 0 (default) or 1 */
+    int32_t xpehh_maf_filter;            /* 0 (default): XPEHH at every marker */
+} selscan_params;
+
+/* Scheduling of the walk kernel.  Changes how the work runs, never the
+ * results.  A NULL selscan_launch* selects the library defaults. */
+#define SELSCAN_SCHED_LONGEST_FIRST 0  /* persistent kernel, probe pass + longest-first queue */
+#define SELSCAN_SCHED_IN_ORDER      1  /* persistent kernel, one queue in core order */
+#define SELSCAN_SCHED_PLAIN         2  /* one CTA per core, no persistence, no ordering */
+typedef struct {
+    int32_t schedule;       /* SELSCAN_SCHED_* */
+    int32_t warps_per_cta;  /* 1..16 (0 = default) */
+    int32_t ctas_per_sm;    /* persistent grid = SMs x this (0 = max resident) */
+    int32_t smem_entries;   /* per-warp on-chip group-word capacity (0 = default) */
+    int32_t probe_steps;    /* first-pass step cap of the longest-first schedule (0 = default) */
+    int32_t reserved[3];
+    void *walk_begin_event; /* optional cudaEvent_t, recorded on the stream before the first walk kernel */
+    void *walk_end_event;   /* optional cudaEvent_t, recorded after the last walk kernel */
+} selscan_launch;
+
+/* iHS outputs: device arrays of length m (one record per marker). */
+typedef struct {
+    int8_t *status;     /* SELSCAN_LOCUS_* */
+    int32_t *n1;        /* derived-allele count at the marker */
+    double *ihh1;       /* iHH of the derived allele (down + up) */
+    double *ihh0;       /* iHH of the ancestral allele */
+    double *lnratio;    /* ln(ihh1 / ihh0) if status == OK, else NaN */
+    int32_t *stop;      /* [m * 4]: (allele 1, down), (1, up), (0, down), (0, up) */
+    uint64_t *digest;   /* [m * 4], same order */
+    int32_t *error;     /* [1] device error word (0 or SELSCAN_ERR_*) */
+} selscan_ihs_out;
+
+/* XPEHH outputs: device arrays of length m. */
+typedef struct {
+    int8_t *status;
+    int32_t *n1;        /* pooled derived-allele count */
+    double *ihhA;
+    double *ihhB;
+    double *lnratio;    /* ln(ihhA / ihhB) if status == OK, else NaN */
+    int32_t *stop;      /* [m * 2]: down, up (pooled truncation) */
+    uint64_t *digest;   /* [m * 6]: down (A, B, pooled), up (A, B, pooled) */
+    int32_t *error;
+} selscan_xpehh_out;
+
+/* Single-locus EHH report: walks w = 0 (carriers of allele 1, Eq. 3),
+ * w = 1 (carriers of allele 0, Eq. 3), w = 2 (whole sample, Eq. 1), each in
+ * both directions, index q = w * 2 + dir. */
+typedef struct {
+    uint64_t *S;        /* [6 * capacity]: S[q * capacity + i] = S(i), i < capacity */
+    int64_t *len;       /* [6] S values computed (> capacity means truncated) */
+    int32_t *stop;      /* [6] */
+    int8_t *status;     /* [6] SELSCAN_LOCUS_OK / UNDEFINED / ABORT_EDGE / ABORT_GAP */
+    double *ihh;        /* [6] the walk's trapezoid sum (Eq. 4 / Eq. 5, one direction) */
+    uint64_t *denom;    /* [3] C(n_c,2) for allele 1, allele 0, C(n,2) */
+    int32_t *error;
+} selscan_ehh_out;
+
+#define SELSCAN_MODE_IHS   0
+#define SELSCAN_MODE_XPEHH 1
+#define SELSCAN_MODE_EHH   2
+
+/* Fill p with the Section 1.2 defaults (cutoffs 1/20, 20 kbp, 200 kbp). */
+void selscan_default_params(selscan_params *p);
+
+/* Workspace bytes needed by one call of the given mode on a problem of
+ * n_total haplotypes (n, or n_A + n_B) and m markers, for the given launch
+ * (NULL = defaults).  The workspace must be 256-byte aligned. */
+size_t selscan_workspace_bytes(int32_t n_total, int64_t m, int32_t mode,
+                               const selscan_launch *launch);
+
+/* iHS at every marker (Eq. 3, Eq. 4, Section 1.2).  hap/pos/gmap: device
+ * inputs as described above; out: device outputs of length m. */
+int selscan_ihs(const uint64_t *hap, int64_t ld, int32_t n, int64_t m,
+                const int64_t *pos_bp, const double *gmap, const selscan_params *p,
+                const selscan_ihs_out *out, void *workspace, size_t ws_bytes,
+                const selscan_launch *launch, void *stream);
+
+/* XPEHH at every marker (Eq. 1, Eq. 5, Section 1.3). */
+int selscan_xpehh(const uint64_t *hap, int64_t ld, int32_t nA, int32_t nB, int64_t m,
+                  const int64_t *pos_bp, const double *gmap, const selscan_params *p,
+                  const selscan_xpehh_out *out, void *workspace, size_t ws_bytes,
+                  const selscan_launch *launch, void *stream);
+
+/* EHH decay around one locus (Eq. 1 and Eq. 3 at every step, Section 1.1),
+ * S(i) recorded for i < capacity. */
+int selscan_ehh(const uint64_t *hap, int64_t ld, int32_t n, int64_t m,
+                const int64_t *pos_bp, const double *gmap, int64_t locus,
+                const selscan_params *p, const selscan_ehh_out *out, int64_t capacity,
+                void *workspace, size_t ws_bytes, void *stream);
+
+/* Pack a 0/1 uint8 matrix into rows (Section 1.1 coding, 0 ancestral / 1
+ * derived).  hap_major = 0: hap01 is [m][n] (marker-major); 1: [n][m].
+ * Values other than 0/1 are read as (v & 1).  rows: [m][ld], pad bits and
+ * words beyond W written as 0. */
+int selscan_pack(const uint8_t *hap01, int32_t n, int64_t m, int32_t hap_major,
+                 uint64_t *rows, int64_t ld, void *stream);
+
+/* Static description of a return or error code. */
+const char *selscan_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SELSCAN_GB300_H */

@@ -1,0 +1,291 @@
+"""GB300-native EHH / iHS / XPEHH scans (selscan, arXiv:1403.6854).
+
+Thin ctypes binding of ``libselscan_gb300.so`` (C ABI in include/selscan.h).
+Every function here only marshals arguments: buffers are torch CUDA tensors
+(PyTorch is the device allocator and supplies the stream), all arithmetic runs
+in the library's sm_103a kernels.  There is no CPU fallback: if the library is
+missing, importing the binding's functions raises.
+
+Names follow the C ABI: ``selscan_ihs``, ``selscan_xpehh``, ``selscan_ehh``,
+``selscan_pack``, ``selscan_workspace_bytes``, ``selscan_default_params``,
+``selscan_strerror``.  The tensor-level helpers allocate outputs (and a
+workspace, unless one is passed) and return them in a dict; calls are
+asynchronous on the current (or given) stream; ``check(out)`` synchronises
+and raises on a device-side error.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Dict, Optional
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libselscan_gb300.so")
+
+# return codes and per-locus status codes (include/selscan.h)
+OK = 0
+ERR_INVALID_ARG, ERR_UNSORTED, ERR_WORKSPACE, ERR_CUDA, ERR_TIMEOUT, ERR_UNSUPPORTED = -1, -2, -3, -4, -5, -6
+LOCUS_OK, LOCUS_MAF_FILTERED, LOCUS_UNDEFINED, LOCUS_ABORT_EDGE, LOCUS_ABORT_GAP = 0, 1, 2, 3, 4
+MODE_IHS, MODE_XPEHH, MODE_EHH = 0, 1, 2
+SCHED_LONGEST_FIRST, SCHED_IN_ORDER, SCHED_PLAIN = 0, 1, 2
+
+_P = ctypes.c_void_p
+
+
+class selscan_params(ctypes.Structure):
+    _fields_ = [("ehh_cut_num", ctypes.c_uint32), ("ehh_cut_den", ctypes.c_uint32),
+                ("maf_num", ctypes.c_uint32), ("maf_den", ctypes.c_uint32),
+                ("gap_scale_bp", ctypes.c_int64), ("max_gap_bp", ctypes.c_int64),
+                ("include_crossing_term", ctypes.c_int32), ("xpehh_maf_filter", ctypes.c_int32)]
+
+
+class selscan_launch(ctypes.Structure):
+    _fields_ = [("schedule", ctypes.c_int32), ("warps_per_cta", ctypes.c_int32),
+                ("ctas_per_sm", ctypes.c_int32), ("smem_entries", ctypes.c_int32),
+                ("probe_steps", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3),
+                ("walk_begin_event", ctypes.c_void_p), ("walk_end_event", ctypes.c_void_p)]
+
+
+class selscan_ihs_out(ctypes.Structure):
+    _fields_ = [(f, _P) for f in ("status", "n1", "ihh1", "ihh0", "lnratio", "stop", "digest",
+                                  "error")]
+
+
+class selscan_xpehh_out(ctypes.Structure):
+    _fields_ = [(f, _P) for f in ("status", "n1", "ihhA", "ihhB", "lnratio", "stop", "digest",
+                                  "error")]
+
+
+class selscan_ehh_out(ctypes.Structure):
+    _fields_ = [(f, _P) for f in ("S", "len", "stop", "status", "ihh", "denom", "error")]
+
+
+EXPORTS = ("selscan_default_params", "selscan_workspace_bytes", "selscan_ihs", "selscan_xpehh",
+           "selscan_ehh", "selscan_pack", "selscan_strerror")
+
+_lib = None
+
+
+def load_library():
+    """Load the built library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                           "(nvcc, sm_103a); there is no fallback path")
+    lib = ctypes.CDLL(LIB_PATH)
+    lib.selscan_default_params.restype = None
+    lib.selscan_default_params.argtypes = [ctypes.POINTER(selscan_params)]
+    lib.selscan_workspace_bytes.restype = ctypes.c_size_t
+    lib.selscan_workspace_bytes.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_int32,
+                                            ctypes.POINTER(selscan_launch)]
+    lib.selscan_ihs.restype = ctypes.c_int
+    lib.selscan_ihs.argtypes = [_P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int64, _P, _P,
+                                ctypes.POINTER(selscan_params), ctypes.POINTER(selscan_ihs_out),
+                                _P, ctypes.c_size_t, ctypes.POINTER(selscan_launch), _P]
+    lib.selscan_xpehh.restype = ctypes.c_int
+    lib.selscan_xpehh.argtypes = [_P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                  ctypes.c_int64, _P, _P, ctypes.POINTER(selscan_params),
+                                  ctypes.POINTER(selscan_xpehh_out), _P, ctypes.c_size_t,
+                                  ctypes.POINTER(selscan_launch), _P]
+    lib.selscan_ehh.restype = ctypes.c_int
+    lib.selscan_ehh.argtypes = [_P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int64, _P, _P,
+                                ctypes.c_int64, ctypes.POINTER(selscan_params),
+                                ctypes.POINTER(selscan_ehh_out), ctypes.c_int64, _P,
+                                ctypes.c_size_t, _P]
+    lib.selscan_pack.restype = ctypes.c_int
+    lib.selscan_pack.argtypes = [_P, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, _P,
+                                 ctypes.c_int64, _P]
+    lib.selscan_strerror.restype = ctypes.c_char_p
+    lib.selscan_strerror.argtypes = [ctypes.c_int]
+    _lib = lib
+    return lib
+
+
+class SelscanError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {selscan_strerror(code)} ({code})")
+
+
+def selscan_strerror(code: int) -> str:
+    return load_library().selscan_strerror(code).decode()
+
+
+def selscan_default_params(**overrides) -> selscan_params:
+    p = selscan_params()
+    load_library().selscan_default_params(ctypes.byref(p))
+    for k, v in overrides.items():
+        if k == "ehh_cut":
+            p.ehh_cut_num, p.ehh_cut_den = int(v[0]), int(v[1])
+        elif k == "maf":
+            p.maf_num, p.maf_den = int(v[0]), int(v[1])
+        else:
+            setattr(p, k, int(v))
+    return p
+
+
+def make_launch(schedule: int = SCHED_LONGEST_FIRST, warps_per_cta: int = 0, ctas_per_sm: int = 0,
+                smem_entries: int = 0, probe_steps: int = 0, events=None) -> selscan_launch:
+    """events: optional (begin, end) torch.cuda.Event pair bracketing the walk kernels."""
+    L = selscan_launch(schedule, warps_per_cta, ctas_per_sm, smem_entries, probe_steps)
+    if events is not None:
+        L.walk_begin_event = ctypes.c_void_p(events[0].cuda_event)
+        L.walk_end_event = ctypes.c_void_p(events[1].cuda_event)
+    return L
+
+
+def selscan_workspace_bytes(n_total: int, m: int, mode: int,
+                            launch: Optional[selscan_launch] = None) -> int:
+    lib = load_library()
+    return int(lib.selscan_workspace_bytes(n_total, m, mode,
+                                           ctypes.byref(launch) if launch is not None else None))
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _workspace(nbytes: int, device, workspace: Optional[torch.Tensor]):
+    if workspace is not None:
+        if workspace.numel() * workspace.element_size() < nbytes or workspace.data_ptr() % 256:
+            raise SelscanError(ERR_WORKSPACE, "workspace")
+        return workspace
+    ws = torch.empty(max(nbytes, 256) + 256, dtype=torch.uint8, device=device)
+    off = (-ws.data_ptr()) % 256
+    return ws[off:off + max(nbytes, 256)]
+
+
+def _as_rows(hap: torch.Tensor) -> torch.Tensor:
+    if hap.dim() != 2 or hap.element_size() != 8 or not hap.is_cuda or not hap.is_contiguous():
+        raise ValueError("hap must be a contiguous 2-D 64-bit CUDA tensor [m, ld]")
+    return hap
+
+
+def selscan_ihs(hap: torch.Tensor, n: int, pos: torch.Tensor, gmap: torch.Tensor,
+                params: Optional[selscan_params] = None, launch: Optional[selscan_launch] = None,
+                stream=None, workspace: Optional[torch.Tensor] = None,
+                out: Optional[Dict[str, torch.Tensor]] = None) -> Dict[str, torch.Tensor]:
+    """iHS at every marker; returns device tensors (valid after stream sync)."""
+    lib = load_library()
+    hap = _as_rows(hap)
+    m, ld = hap.shape
+    dev = hap.device
+    if out is None:
+        out = dict(status=torch.empty(m, dtype=torch.int8, device=dev),
+                   n1=torch.empty(m, dtype=torch.int32, device=dev),
+                   ihh1=torch.empty(m, dtype=torch.float64, device=dev),
+                   ihh0=torch.empty(m, dtype=torch.float64, device=dev),
+                   lnratio=torch.empty(m, dtype=torch.float64, device=dev),
+                   stop=torch.empty((m, 4), dtype=torch.int32, device=dev),
+                   digest=torch.empty((m, 4), dtype=torch.int64, device=dev),
+                   error=torch.zeros(1, dtype=torch.int32, device=dev))
+    p = params if params is not None else selscan_default_params()
+    ws = _workspace(selscan_workspace_bytes(n, m, MODE_IHS, launch), dev, workspace)
+    o = selscan_ihs_out(*(_ptr(out[f]) for f in ("status", "n1", "ihh1", "ihh0", "lnratio",
+                                                  "stop", "digest", "error")))
+    rc = lib.selscan_ihs(_ptr(hap), ld, n, m, _ptr(pos), _ptr(gmap), ctypes.byref(p),
+                         ctypes.byref(o), _ptr(ws), ws.numel(),
+                         ctypes.byref(launch) if launch is not None else None, _stream(stream))
+    if rc != OK:
+        raise SelscanError(rc, "selscan_ihs")
+    out["_workspace"] = ws
+    return out
+
+
+def selscan_xpehh(hap: torch.Tensor, nA: int, nB: int, pos: torch.Tensor, gmap: torch.Tensor,
+                  params: Optional[selscan_params] = None,
+                  launch: Optional[selscan_launch] = None, stream=None,
+                  workspace: Optional[torch.Tensor] = None,
+                  out: Optional[Dict[str, torch.Tensor]] = None) -> Dict[str, torch.Tensor]:
+    """XPEHH at every marker; rows hold W_A words of A then W_B words of B."""
+    lib = load_library()
+    hap = _as_rows(hap)
+    m, ld = hap.shape
+    dev = hap.device
+    if out is None:
+        out = dict(status=torch.empty(m, dtype=torch.int8, device=dev),
+                   n1=torch.empty(m, dtype=torch.int32, device=dev),
+                   ihhA=torch.empty(m, dtype=torch.float64, device=dev),
+                   ihhB=torch.empty(m, dtype=torch.float64, device=dev),
+                   lnratio=torch.empty(m, dtype=torch.float64, device=dev),
+                   stop=torch.empty((m, 2), dtype=torch.int32, device=dev),
+                   digest=torch.empty((m, 6), dtype=torch.int64, device=dev),
+                   error=torch.zeros(1, dtype=torch.int32, device=dev))
+    p = params if params is not None else selscan_default_params()
+    ws = _workspace(selscan_workspace_bytes(nA + nB, m, MODE_XPEHH, launch), dev, workspace)
+    o = selscan_xpehh_out(*(_ptr(out[f]) for f in ("status", "n1", "ihhA", "ihhB", "lnratio",
+                                                    "stop", "digest", "error")))
+    rc = lib.selscan_xpehh(_ptr(hap), ld, nA, nB, m, _ptr(pos), _ptr(gmap), ctypes.byref(p),
+                           ctypes.byref(o), _ptr(ws), ws.numel(),
+                           ctypes.byref(launch) if launch is not None else None, _stream(stream))
+    if rc != OK:
+        raise SelscanError(rc, "selscan_xpehh")
+    out["_workspace"] = ws
+    return out
+
+
+def selscan_ehh(hap: torch.Tensor, n: int, pos: torch.Tensor, gmap: torch.Tensor, locus: int,
+                capacity: int, params: Optional[selscan_params] = None, stream=None,
+                workspace: Optional[torch.Tensor] = None) -> Dict[str, torch.Tensor]:
+    """S(i) of the six walks around one locus: [allele 1, allele 0, whole] x [down, up]."""
+    lib = load_library()
+    hap = _as_rows(hap)
+    m, ld = hap.shape
+    dev = hap.device
+    out = dict(S=torch.zeros((3, 2, max(capacity, 0)), dtype=torch.int64, device=dev),
+               len=torch.empty((3, 2), dtype=torch.int64, device=dev),
+               stop=torch.empty((3, 2), dtype=torch.int32, device=dev),
+               status=torch.empty((3, 2), dtype=torch.int8, device=dev),
+               ihh=torch.empty((3, 2), dtype=torch.float64, device=dev),
+               denom=torch.empty(3, dtype=torch.int64, device=dev),
+               error=torch.zeros(1, dtype=torch.int32, device=dev))
+    p = params if params is not None else selscan_default_params()
+    ws = _workspace(selscan_workspace_bytes(n, m, MODE_EHH, None), dev, workspace)
+    o = selscan_ehh_out(*(_ptr(out[f]) if out[f].numel() else None
+                          for f in ("S", "len", "stop", "status", "ihh", "denom", "error")))
+    rc = lib.selscan_ehh(_ptr(hap), ld, n, m, _ptr(pos), _ptr(gmap), locus, ctypes.byref(p),
+                         ctypes.byref(o), capacity, _ptr(ws), ws.numel(), _stream(stream))
+    if rc != OK:
+        raise SelscanError(rc, "selscan_ehh")
+    return out
+
+
+def selscan_pack(hap01: torch.Tensor, n: int, hap_major: bool = False, ld: Optional[int] = None,
+                 stream=None) -> torch.Tensor:
+    """uint8 0/1 matrix ([m, n], or [n, m] if hap_major) -> packed rows [m, ld] (int64 bits)."""
+    lib = load_library()
+    if hap01.dtype != torch.uint8 or not hap01.is_cuda or not hap01.is_contiguous():
+        raise ValueError("hap01 must be a contiguous uint8 CUDA tensor")
+    m = hap01.shape[1] if hap_major else hap01.shape[0]
+    W = (n + 63) // 64
+    ld = W if ld is None else ld
+    rows = torch.empty((m, ld), dtype=torch.int64, device=hap01.device)
+    rc = lib.selscan_pack(_ptr(hap01), n, m, 1 if hap_major else 0, _ptr(rows), ld, _stream(stream))
+    if rc != OK:
+        raise SelscanError(rc, "selscan_pack")
+    return rows
+
+
+def check(out: Dict[str, torch.Tensor]) -> None:
+    """Synchronise on the device error word and raise if a device check failed."""
+    e = int(out["error"].item())
+    if e != OK:
+        raise SelscanError(e, "device")
+
+
+def to_device(rows, pos, gmap, device="cuda"):
+    """numpy packed rows / positions / map -> CUDA tensors of the ABI's types."""
+    import numpy as np
+    r = torch.from_numpy(np.ascontiguousarray(rows).view(np.int64)).to(device)
+    p = torch.from_numpy(np.ascontiguousarray(pos, dtype=np.int64)).to(device)
+    g = torch.from_numpy(np.ascontiguousarray(gmap, dtype=np.float64)).to(device)
+    return r, p, g

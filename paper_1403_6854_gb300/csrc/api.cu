@@ -1,0 +1,309 @@
+// C ABI of the scan library (see include/selscan.h for the contract).
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include "../../include/selscan.h"
+#include "internal.h"
+
+namespace selscan {
+int device_sms();
+}
+
+using namespace selscan;
+
+namespace {
+
+constexpr int kDefaultWarpsPerCta = 8;
+constexpr int kDefaultSmemEntries = 128;
+constexpr int kDefaultProbeSteps = 48;
+constexpr int kMaxHaplotypes = 65535;
+constexpr size_t kMaxSmemPerCta = 227 * 1024;
+
+struct Plan {
+    int schedule;
+    int wpc;            // warps per CTA of the walk kernel
+    int ctas;           // persistent grid size
+    int nslots;         // global scratch slices (warps)
+    int cap_s, gcap_s;
+    int probe;
+};
+
+inline size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+bool params_ok(const selscan_params *p)
+{
+    return p && p->ehh_cut_den > 0 && p->maf_den > 0 && p->gap_scale_bp > 0 && p->max_gap_bp >= 0 &&
+           (p->include_crossing_term == 0 || p->include_crossing_term == 1);
+}
+
+Plan make_plan(int mode, const selscan_launch *L)
+{
+    Plan p;
+    p.schedule = L ? L->schedule : SELSCAN_SCHED_LONGEST_FIRST;
+    if (p.schedule < 0 || p.schedule > SELSCAN_SCHED_PLAIN) p.schedule = -1;
+    p.cap_s = (L && L->smem_entries > 0) ? L->smem_entries : kDefaultSmemEntries;
+    if (p.cap_s > 4096) p.cap_s = 4096;
+    p.cap_s = (p.cap_s + 1) & ~1;
+    p.gcap_s = p.cap_s / 2;
+    p.probe = (L && L->probe_steps > 0) ? L->probe_steps : kDefaultProbeSteps;
+    const int sms = device_sms();
+    if (mode == SELSCAN_MODE_EHH) {
+        p.schedule = SELSCAN_SCHED_IN_ORDER;
+        p.wpc = 6;
+        p.ctas = 1;
+        p.nslots = 6;
+        return p;
+    }
+    const int ipc = mode == SELSCAN_MODE_XPEHH ? 2 : 4;
+    if (p.schedule == SELSCAN_SCHED_PLAIN) {
+        p.wpc = ipc;
+        const size_t smem = smem_per_warp(p.cap_s, p.gcap_s) * (size_t)ipc;
+        int per_sm = max_ctas_per_sm(p.schedule, ipc, smem);
+        if (per_sm < 1) per_sm = 64 / ipc;                 // no device: the architectural maximum
+        p.ctas = 0;
+        p.nslots = sms * per_sm * ipc;
+        return p;
+    }
+    p.wpc = (L && L->warps_per_cta > 0) ? L->warps_per_cta : kDefaultWarpsPerCta;
+    if (p.wpc > 16) p.wpc = 16;
+    const size_t smem = smem_per_warp(p.cap_s, p.gcap_s) * (size_t)p.wpc;
+    int per_sm = max_ctas_per_sm(p.schedule, p.wpc, smem);
+    if (per_sm < 1) per_sm = 64 / p.wpc > 0 ? 64 / p.wpc : 1;
+    int want = (L && L->ctas_per_sm > 0) ? L->ctas_per_sm : per_sm;
+    if (want > per_sm) want = per_sm;
+    p.ctas = sms * want;
+    p.nslots = p.ctas * p.wpc;
+    return p;
+}
+
+struct Layout {
+    size_t queue, slotmap, item_status, item_ihh, list2, key2, sorted2, bucket, scratch, total;
+    size_t per_warp;
+};
+
+Layout make_layout(int n_total, long long m, int mode, const Plan &p)
+{
+    Layout l;
+    const long long items = mode == SELSCAN_MODE_EHH ? 0 : m * (mode == SELSCAN_MODE_XPEHH ? 2 : 4);
+    size_t o = 0;
+    l.queue = o;        o += up256(sizeof(Queue));
+    l.slotmap = o;      o += up256(((size_t)p.nslots + 31) / 32 * 4);
+    l.item_status = o;  o += up256((size_t)items);
+    l.item_ihh = o;     o += up256((size_t)items * 8 * (mode == SELSCAN_MODE_XPEHH ? 2 : 1));
+    l.list2 = o;        o += up256((size_t)items * 4);
+    l.key2 = o;         o += up256((size_t)items * 4);
+    l.sorted2 = o;      o += up256((size_t)items * 4);
+    l.bucket = o;       o += up256((NBUCKET + 1) * 4);
+    l.per_warp = scratch_per_warp(n_total);
+    l.scratch = o;      o += (size_t)p.nslots * l.per_warp;
+    l.total = o;
+    return l;
+}
+
+inline unsigned long long last_mask(int n)
+{
+    return (n % 64) ? ((1ull << (n % 64)) - 1ull) : ~0ull;
+}
+
+ScanArgs make_args(const uint64_t *hap, int64_t ld, int nA, int nB, int64_t m, const int64_t *pos,
+                   const double *gmap, const selscan_params *p)
+{
+    ScanArgs a;
+    a.hap = (const unsigned long long *)hap;
+    a.ld = ld;
+    a.m = m;
+    a.pos = (const long long *)pos;
+    a.gmap = gmap;
+    a.WA = (nA + 63) / 64;
+    a.W = a.WA + (nB + 63) / 64;
+    a.nA = nA;
+    a.nB = nB;
+    a.lastA = last_mask(nA);
+    a.lastB = nB > 0 ? last_mask(nB) : ~0ull;
+    a.cut_num = p->ehh_cut_num;
+    a.cut_den = p->ehh_cut_den;
+    a.gap_scale = p->gap_scale_bp;
+    a.max_gap = p->max_gap_bp;
+    a.crossing = p->include_crossing_term;
+    return a;
+}
+
+Scratch make_scratch(unsigned char *ws, const Layout &l, int n_total, const Plan &p)
+{
+    Scratch sc;
+    sc.base = ws + l.scratch;
+    sc.per_warp = l.per_warp;
+    sc.cap = n_total;
+    sc.gcap = n_total / 2 + 1;
+    sc.cap_s = p.cap_s;
+    sc.gcap_s = p.gcap_s;
+    return sc;
+}
+
+int run_scan(int mode, const uint64_t *hap, int64_t ld, int32_t nA, int32_t nB, int64_t m,
+             const int64_t *pos, const double *gmap, const selscan_params *p, int8_t *status,
+             int32_t *n1, int32_t *stop, uint64_t *digest, int32_t *err, double *o1, double *o2,
+             double *lnratio, void *workspace, size_t ws_bytes, const selscan_launch *launch,
+             void *stream)
+{
+    const int n_total = nA + nB;
+    const Plan plan = make_plan(mode, launch);
+    if (plan.schedule < 0 || (launch && launch->warps_per_cta < 0)) return SELSCAN_ERR_INVALID_ARG;
+    if (smem_per_warp(plan.cap_s, plan.gcap_s) * (size_t)plan.wpc > kMaxSmemPerCta)
+        return SELSCAN_ERR_UNSUPPORTED;
+    const Layout l = make_layout(n_total, m, mode, plan);
+    if (!workspace || ws_bytes < l.total || ((uintptr_t)workspace & 255)) return SELSCAN_ERR_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned char *ws = (unsigned char *)workspace;
+
+    const ScanArgs a = make_args(hap, ld, nA, nB, m, pos, gmap, p);
+    ItemSink sk;
+    sk.mode = mode == SELSCAN_MODE_XPEHH ? 1 : 0;
+    sk.core_status = status;
+    sk.item_status = (int8_t *)(ws + l.item_status);
+    sk.item_ihh = (double *)(ws + l.item_ihh);
+    sk.stop = stop;
+    sk.digest = (unsigned long long *)digest;
+    sk.list2 = (uint32_t *)(ws + l.list2);
+    sk.key2 = (uint32_t *)(ws + l.key2);
+    sk.sorted2 = (uint32_t *)(ws + l.sorted2);
+    sk.bucket = (uint32_t *)(ws + l.bucket);
+    sk.slotmap = (uint32_t *)(ws + l.slotmap);
+    sk.q = (Queue *)(ws + l.queue);
+    const Scratch sc = make_scratch(ws, l, n_total, plan);
+
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(ws, 0, l.item_status, s)) != cudaSuccess) return SELSCAN_ERR_CUDA;
+    if ((e = cudaMemsetAsync(ws + l.bucket, 0, (NBUCKET + 1) * 4, s)) != cudaSuccess) return SELSCAN_ERR_CUDA;
+    if ((e = cudaMemsetAsync(err, 0, sizeof(int32_t), s)) != cudaSuccess) return SELSCAN_ERR_CUDA;
+    if (launch_validate((const long long *)pos, gmap, m, err, s) != cudaSuccess) return SELSCAN_ERR_CUDA;
+    if (launch_core_select(a, sk.mode, p->maf_num, p->maf_den, p->xpehh_maf_filter, n1, status, s) !=
+        cudaSuccess)
+        return SELSCAN_ERR_CUDA;
+    const int ctas_or_slots = plan.schedule == SELSCAN_SCHED_PLAIN ? plan.nslots : plan.ctas;
+    if (launch && launch->walk_begin_event &&
+        cudaEventRecord((cudaEvent_t)launch->walk_begin_event, s) != cudaSuccess)
+        return SELSCAN_ERR_CUDA;
+    if (launch_walk(a, sk, sc, plan.schedule, plan.wpc, ctas_or_slots, plan.probe, m, s) != cudaSuccess)
+        return SELSCAN_ERR_CUDA;
+    if (launch && launch->walk_end_event &&
+        cudaEventRecord((cudaEvent_t)launch->walk_end_event, s) != cudaSuccess)
+        return SELSCAN_ERR_CUDA;
+    if (sk.mode == 1)
+        e = launch_finalize_xpehh(sk, m, o1, o2, lnratio, status, s);
+    else
+        e = launch_finalize_ihs(sk, m, o1, o2, lnratio, status, s);
+    return e == cudaSuccess ? SELSCAN_OK : SELSCAN_ERR_CUDA;
+}
+
+}  // namespace
+
+extern "C" {
+
+void selscan_default_params(selscan_params *p)
+{
+    if (!p) return;
+    p->ehh_cut_num = 1;
+    p->ehh_cut_den = 20;
+    p->maf_num = 1;
+    p->maf_den = 20;
+    p->gap_scale_bp = 20000;
+    p->max_gap_bp = 200000;
+    p->include_crossing_term = 0;
+    p->xpehh_maf_filter = 0;
+}
+
+size_t selscan_workspace_bytes(int32_t n_total, int64_t m, int32_t mode, const selscan_launch *launch)
+{
+    if (n_total < 2 || m < 1 || mode < 0 || mode > 2) return 0;
+    const Plan p = make_plan(mode, launch);
+    return make_layout(n_total, m, mode, p).total;
+}
+
+int selscan_ihs(const uint64_t *hap, int64_t ld, int32_t n, int64_t m, const int64_t *pos_bp,
+                const double *gmap, const selscan_params *p, const selscan_ihs_out *out,
+                void *workspace, size_t ws_bytes, const selscan_launch *launch, void *stream)
+{
+    if (!hap || !pos_bp || !gmap || !out || !params_ok(p)) return SELSCAN_ERR_INVALID_ARG;
+    if (n < 2 || n > kMaxHaplotypes || m < 1 || m >= (1ll << 30) || ld < (n + 63) / 64)
+        return SELSCAN_ERR_INVALID_ARG;
+    if (!out->status || !out->n1 || !out->ihh1 || !out->ihh0 || !out->lnratio || !out->stop ||
+        !out->digest || !out->error)
+        return SELSCAN_ERR_INVALID_ARG;
+    return run_scan(SELSCAN_MODE_IHS, hap, ld, n, 0, m, pos_bp, gmap, p, out->status, out->n1,
+                    out->stop, out->digest, out->error, out->ihh1, out->ihh0, out->lnratio,
+                    workspace, ws_bytes, launch, stream);
+}
+
+int selscan_xpehh(const uint64_t *hap, int64_t ld, int32_t nA, int32_t nB, int64_t m,
+                  const int64_t *pos_bp, const double *gmap, const selscan_params *p,
+                  const selscan_xpehh_out *out, void *workspace, size_t ws_bytes,
+                  const selscan_launch *launch, void *stream)
+{
+    if (!hap || !pos_bp || !gmap || !out || !params_ok(p)) return SELSCAN_ERR_INVALID_ARG;
+    if (nA < 2 || nB < 2 || (long long)nA + nB > kMaxHaplotypes || m < 1 || m >= (1ll << 30) ||
+        ld < (nA + 63) / 64 + (nB + 63) / 64)
+        return SELSCAN_ERR_INVALID_ARG;
+    if (!out->status || !out->n1 || !out->ihhA || !out->ihhB || !out->lnratio || !out->stop ||
+        !out->digest || !out->error)
+        return SELSCAN_ERR_INVALID_ARG;
+    return run_scan(SELSCAN_MODE_XPEHH, hap, ld, nA, nB, m, pos_bp, gmap, p, out->status, out->n1,
+                    out->stop, out->digest, out->error, out->ihhA, out->ihhB, out->lnratio,
+                    workspace, ws_bytes, launch, stream);
+}
+
+int selscan_ehh(const uint64_t *hap, int64_t ld, int32_t n, int64_t m, const int64_t *pos_bp,
+                const double *gmap, int64_t locus, const selscan_params *p,
+                const selscan_ehh_out *out, int64_t capacity, void *workspace, size_t ws_bytes,
+                void *stream)
+{
+    if (!hap || !pos_bp || !gmap || !out || !params_ok(p)) return SELSCAN_ERR_INVALID_ARG;
+    if (n < 2 || n > kMaxHaplotypes || m < 1 || m >= (1ll << 30) || ld < (n + 63) / 64 ||
+        locus < 0 || locus >= m || capacity < 0)
+        return SELSCAN_ERR_INVALID_ARG;
+    if ((capacity > 0 && !out->S) || !out->len || !out->stop || !out->status || !out->ihh ||
+        !out->denom || !out->error)
+        return SELSCAN_ERR_INVALID_ARG;
+    const Plan plan = make_plan(SELSCAN_MODE_EHH, nullptr);
+    const Layout l = make_layout(n, m, SELSCAN_MODE_EHH, plan);
+    if (!workspace || ws_bytes < l.total || ((uintptr_t)workspace & 255)) return SELSCAN_ERR_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    const ScanArgs a = make_args(hap, ld, n, 0, m, pos_bp, gmap, p);
+    const Scratch sc = make_scratch((unsigned char *)workspace, l, n, plan);
+    if (cudaMemsetAsync(out->error, 0, sizeof(int32_t), s) != cudaSuccess) return SELSCAN_ERR_CUDA;
+    if (launch_validate((const long long *)pos_bp, gmap, m, out->error, s) != cudaSuccess)
+        return SELSCAN_ERR_CUDA;
+    if (launch_ehh(a, locus, sc, (unsigned long long *)out->S, capacity, (long long *)out->len,
+                   out->stop, out->status, out->ihh, (unsigned long long *)out->denom, s) !=
+        cudaSuccess)
+        return SELSCAN_ERR_CUDA;
+    return SELSCAN_OK;
+}
+
+int selscan_pack(const uint8_t *hap01, int32_t n, int64_t m, int32_t hap_major, uint64_t *rows,
+                 int64_t ld, void *stream)
+{
+    if (!hap01 || !rows || n < 1 || m < 1 || ld < (n + 63) / 64 || (hap_major != 0 && hap_major != 1))
+        return SELSCAN_ERR_INVALID_ARG;
+    if (launch_pack(hap01, n, m, hap_major, (unsigned long long *)rows, ld, (cudaStream_t)stream) !=
+        cudaSuccess)
+        return SELSCAN_ERR_CUDA;
+    return SELSCAN_OK;
+}
+
+const char *selscan_strerror(int code)
+{
+    switch (code) {
+    case SELSCAN_OK: return "ok";
+    case SELSCAN_ERR_INVALID_ARG: return "invalid argument";
+    case SELSCAN_ERR_UNSORTED: return "positions or genetic map decrease";
+    case SELSCAN_ERR_WORKSPACE: return "workspace too small or not 256-byte aligned";
+    case SELSCAN_ERR_CUDA: return "CUDA launch or runtime error";
+    case SELSCAN_ERR_TIMEOUT: return "bounded device wait gave up";
+    case SELSCAN_ERR_UNSUPPORTED: return "unsupported device or launch shape";
+    default: return "unknown error code";
+    }
+}
+
+}  // extern "C"

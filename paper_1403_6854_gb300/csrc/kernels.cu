@@ -1,0 +1,527 @@
+// Kernels of the EHH / iHS / XPEHH scan (sm_103a).
+//
+//   validate      positions and map non-decreasing (device error word)
+//   core_select   derived count n_1 per marker and the MAF filter (Section 1.2)
+//   walk_*        the EHH walks (walk.cuh): persistent with a global queue, or
+//                 one CTA per core (plain launch)
+//   bucket_*      longest-first ordering of the walks that outlive the probe pass
+//   finalize_*    iHH_c = downstream + upstream, status, ln ratio (Eq. 4, Eq. 5)
+//   ehh_trace     the single-locus report (Eq. 1, Eq. 3 per step)
+//   pack          0/1 bytes -> bit rows
+#include <math.h>
+
+#include "../../include/selscan.h"
+#include "internal.h"
+
+namespace selscan {
+
+__device__ __forceinline__ WarpBufs make_bufs(unsigned char *sm, unsigned char *gm,
+                                              const Scratch &sc)
+{
+    WarpBufs b;
+    b.cap_s = sc.cap_s;
+    b.gcap_s = sc.gcap_s;
+    unsigned char *p = sm;
+    b.mask[0] = (unsigned long long *)p; p += (size_t)sc.cap_s * 8;
+    b.mask[1] = (unsigned long long *)p; p += (size_t)sc.cap_s * 8;
+    b.meta[0] = (unsigned int *)p; p += (size_t)sc.cap_s * 4;
+    b.meta[1] = (unsigned int *)p; p += (size_t)sc.cap_s * 4;
+    b.cnt[0] = (unsigned int *)p; p += (size_t)sc.gcap_s * 4;
+    b.cntB[0] = (unsigned int *)p; p += (size_t)sc.gcap_s * 4;
+    b.nid[0] = (unsigned int *)p;
+    p = gm;
+    b.mask[2] = (unsigned long long *)p; p += (size_t)sc.cap * 8;
+    b.mask[3] = (unsigned long long *)p; p += (size_t)sc.cap * 8;
+    b.meta[2] = (unsigned int *)p; p += (size_t)sc.cap * 4;
+    b.meta[3] = (unsigned int *)p; p += (size_t)sc.cap * 4;
+    b.cnt[1] = (unsigned int *)p; p += (size_t)sc.gcap * 4;
+    b.cntB[1] = (unsigned int *)p; p += (size_t)sc.gcap * 4;
+    b.nid[1] = (unsigned int *)p;
+    return b;
+}
+
+// the count arrays must be zero when a walk starts; walks leave them zero
+__device__ __forceinline__ void zero_counts(WarpBufs &b, const Scratch &sc, bool global_too)
+{
+    const int lane = threadIdx.x & 31;
+    for (int g = lane; g < sc.gcap_s; g += 32) { b.cnt[0][g] = 0; b.cntB[0][g] = 0; }
+    if (global_too)
+        for (int g = lane; g < sc.gcap; g += 32) { b.cnt[1][g] = 0; b.cntB[1][g] = 0; }
+    __syncwarp();
+}
+
+// ------------------------------------------------------------ validate
+__global__ void validate_kernel(const long long *pos, const double *gmap, long long m, int32_t *err)
+{
+    for (long long k = 1 + blockIdx.x * (long long)blockDim.x + threadIdx.x; k < m;
+         k += (long long)gridDim.x * blockDim.x) {
+        if (pos[k] < pos[k - 1] || !(gmap[k] >= gmap[k - 1])) atomicExch(err, SELSCAN_ERR_UNSORTED);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0 && m >= 1 && !(gmap[0] == gmap[0]))
+        atomicExch(err, SELSCAN_ERR_UNSORTED);
+}
+
+cudaError_t launch_validate(const long long *pos, const double *gmap, long long m, int32_t *err,
+                            cudaStream_t s)
+{
+    long long blocks = (m + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    if (blocks < 1) blocks = 1;
+    validate_kernel<<<(unsigned)blocks, 256, 0, s>>>(pos, gmap, m, err);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ core select
+__global__ void core_select_kernel(ScanArgs a, int mode, unsigned maf_num, unsigned maf_den,
+                                   int maf_filter, int32_t *n1, int8_t *core_status)
+{
+    const int lane = threadIdx.x & 31;
+    const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    const unsigned n_total = (unsigned)(a.nA + a.nB);
+    for (long long k = warp; k < a.m; k += nw) {
+        const unsigned long long *row = a.hap + k * a.ld;
+        unsigned c = 0;
+        for (int w = lane; w < a.W; w += 32) c += (unsigned)__popcll(__ldg(row + w) & valid_word(a, w));
+        c = __reduce_add_sync(FULLMASK, c);
+        if (lane == 0) {
+            n1[k] = (int32_t)c;
+            const unsigned minor = c < n_total - c ? c : n_total - c;
+            const bool filt = (mode == 0 || maf_filter) &&
+                              (unsigned long long)maf_den * minor < (unsigned long long)maf_num * n_total;
+            core_status[k] = filt ? (int8_t)SELSCAN_LOCUS_MAF_FILTERED : (int8_t)0;
+        }
+    }
+}
+
+cudaError_t launch_core_select(const ScanArgs &a, int mode, unsigned maf_num, unsigned maf_den,
+                               int maf_filter, int32_t *n1, int8_t *core_status, cudaStream_t s)
+{
+    long long blocks = (a.m * 32 + 255) / 256;
+    if (blocks > 8192) blocks = 8192;
+    core_select_kernel<<<(unsigned)blocks, 256, 0, s>>>(a, mode, maf_num, maf_den, maf_filter,
+                                                         n1, core_status);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ walks
+__device__ __forceinline__ uint32_t bucket_of(float ehh)
+{
+    // longer expected walks (higher EHH at the probe cap) get lower buckets
+    if (!(ehh > 0.f)) return NBUCKET - 1;
+    float b = -__log2f(ehh) * 16.f;
+    if (b < 0.f) b = 0.f;
+    if (b > (float)(NBUCKET - 1)) b = (float)(NBUCKET - 1);
+    return (uint32_t)b;
+}
+
+template <int NPOP>
+__device__ __forceinline__ void run_item(const ScanArgs &a, const ItemSink &sk, WarpBufs &b,
+                                         uint32_t item, int max_steps)
+{
+    const int lane = threadIdx.x & 31;
+    const int ipc = NPOP == 2 ? 2 : 4;
+    const long long core = item / ipc;
+    const int q = (int)(item % ipc);
+    const int dir = q & 1;
+    const int sel = NPOP == 2 ? 0 : (q < 2 ? 0 : 1);
+    WalkOut o = walk<NPOP>(a, core, dir, sel, b, nullptr, 0, max_steps);
+    if (lane != 0) return;
+    if (o.status == W_UNFINISHED) {
+        const unsigned long long slot = atomicAdd(&sk.q->n2, 1ull);
+        sk.list2[slot] = item;
+        sk.key2[slot] = bucket_of(o.key);
+        return;
+    }
+    sk.item_status[item] = (int8_t)o.status;
+    sk.stop[item] = o.stop;
+    if (NPOP == 2) {
+        sk.item_ihh[2 * (size_t)item] = o.ihh[0];
+        sk.item_ihh[2 * (size_t)item + 1] = o.ihh[1];
+        sk.digest[3 * (size_t)item] = o.dig[0];
+        sk.digest[3 * (size_t)item + 1] = o.dig[1];
+        sk.digest[3 * (size_t)item + 2] = o.dig[2];
+    } else {
+        sk.item_ihh[item] = o.ihh[0];
+        sk.digest[item] = o.dig[0];
+    }
+}
+
+// Persistent walk kernel.  pass 1: items in core order (a warp takes one
+// core's items per queue fetch), optionally capped at max_steps; pass 2:
+// the sorted list of walks the first pass left unfinished, one per fetch.
+template <int NPOP>
+__global__ void __launch_bounds__(512) walk_persistent_kernel(ScanArgs a, ItemSink sk, Scratch sc,
+                                                              long long n_cores, int pass,
+                                                              int max_steps)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int wpc = blockDim.x >> 5;
+    const long long gw = (long long)blockIdx.x * wpc + warp;
+    WarpBufs b = make_bufs(smem + (size_t)warp * smem_per_warp(sc.cap_s, sc.gcap_s),
+                           sc.base + (size_t)gw * sc.per_warp, sc);
+    zero_counts(b, sc, true);
+    const int ipc = NPOP == 2 ? 2 : 4;
+    const unsigned long long total = pass == 2 ? sk.q->n2 : (unsigned long long)n_cores;
+    for (;;) {
+        unsigned long long idx = 0;
+        if (lane == 0) idx = atomicAdd(&sk.q->head, 1ull);
+        idx = __shfl_sync(FULLMASK, idx, 0);
+        if (idx >= total) break;
+        if (pass == 2) {
+            run_item<NPOP>(a, sk, b, sk.sorted2[idx], 0);
+        } else {
+            if (sk.core_status[idx] == (int8_t)SELSCAN_LOCUS_MAF_FILTERED) continue;
+            for (int q = 0; q < ipc; ++q) run_item<NPOP>(a, sk, b, (uint32_t)(idx * ipc + q), max_steps);
+        }
+    }
+}
+
+// Plain launch: one CTA per core, one warp per walk; global scratch slots
+// are taken from a bitmap (at most nslots warps are resident at once).
+template <int NPOP>
+__global__ void __launch_bounds__(128) walk_plain_kernel(ScanArgs a, ItemSink sk, Scratch sc,
+                                                         unsigned int *slotmap, int nslots)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const long long core = blockIdx.x;
+    if (sk.core_status[core] == (int8_t)SELSCAN_LOCUS_MAF_FILTERED) return;
+    int slot = -1;
+    if (lane == 0) {
+        const int start = (int)(((long long)blockIdx.x * (blockDim.x >> 5) + warp) % nslots);
+        for (int t = 0; t < nslots; ++t) {
+            const int s = (start + t) % nslots;
+            const unsigned bit = 1u << (s & 31);
+            if (!(atomicOr(slotmap + (s >> 5), bit) & bit)) { slot = s; break; }
+        }
+        __threadfence();
+    }
+    slot = __shfl_sync(FULLMASK, slot, 0);
+    if (slot < 0) {                       // cannot happen: nslots >= resident warps
+        if (lane == 0) sk.item_status[core * (NPOP == 2 ? 2 : 4) + warp] = (int8_t)W_UNFINISHED;
+        return;
+    }
+    WarpBufs b = make_bufs(smem + (size_t)warp * smem_per_warp(sc.cap_s, sc.gcap_s),
+                           sc.base + (size_t)slot * sc.per_warp, sc);
+    zero_counts(b, sc, false);
+    run_item<NPOP>(a, sk, b, (uint32_t)(core * (NPOP == 2 ? 2 : 4) + warp), 0);
+    __syncwarp();
+    if (lane == 0) {
+        __threadfence();
+        atomicAnd(slotmap + (slot >> 5), ~(1u << (slot & 31)));
+    }
+}
+
+__global__ void zero_scratch_counts_kernel(Scratch sc, long long nwarps)
+{
+    const long long words = (long long)sc.gcap * 2;   // cnt and cntB are adjacent
+    const size_t off = (size_t)sc.cap * 2 * 8 + (size_t)sc.cap * 2 * 4;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nwarps * words;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long w = t / words, k = t % words;
+        ((unsigned int *)(sc.base + (size_t)w * sc.per_warp + off))[k] = 0u;
+    }
+}
+
+__global__ void bucket_hist_kernel(ItemSink sk)
+{
+    const unsigned long long n2 = sk.q->n2;
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n2;
+         i += (unsigned long long)gridDim.x * blockDim.x)
+        atomicAdd(sk.bucket + sk.key2[i], 1u);
+}
+
+__global__ void bucket_scan_kernel(ItemSink sk)
+{
+    // one block of NBUCKET threads: exclusive scan in place, head reset
+    __shared__ uint32_t t[NBUCKET];
+    const int i = threadIdx.x;
+    t[i] = sk.bucket[i];
+    __syncthreads();
+    for (int o = 1; o < NBUCKET; o <<= 1) {
+        uint32_t v = i >= o ? t[i - o] : 0u;
+        __syncthreads();
+        t[i] += v;
+        __syncthreads();
+    }
+    sk.bucket[i] = t[i] - sk.bucket[i];
+    if (i == 0) sk.q->head = 0ull;
+}
+
+__global__ void bucket_scatter_kernel(ItemSink sk)
+{
+    const unsigned long long n2 = sk.q->n2;
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n2;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        const uint32_t p = atomicAdd(sk.bucket + sk.key2[i], 1u);
+        sk.sorted2[p] = sk.list2[i];
+    }
+}
+
+static int g_sms = 0;
+static int sm_count()
+{
+    if (g_sms == 0) {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
+            g_sms = v;
+        else
+            return 152;
+    }
+    return g_sms;
+}
+
+int max_ctas_per_sm(int schedule, int warps_per_cta, size_t smem_bytes)
+{
+    int nb = 0;
+    cudaError_t e;
+    if (schedule == SELSCAN_SCHED_PLAIN)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, walk_plain_kernel<1>,
+                                                          warps_per_cta * 32, smem_bytes);
+    else
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, walk_persistent_kernel<1>,
+                                                          warps_per_cta * 32, smem_bytes);
+    if (e != cudaSuccess || nb < 1) { cudaGetLastError(); return -1; }
+    int nb2 = 0;
+    if (schedule == SELSCAN_SCHED_PLAIN)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb2, walk_plain_kernel<2>,
+                                                          warps_per_cta * 32, smem_bytes);
+    else
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb2, walk_persistent_kernel<2>,
+                                                          warps_per_cta * 32, smem_bytes);
+    if (e == cudaSuccess && nb2 > nb) nb = nb2;
+    cudaGetLastError();
+    return nb;
+}
+
+int device_sms() { return sm_count(); }
+
+template <int NPOP>
+static cudaError_t walk_impl(const ScanArgs &a, const ItemSink &sk, const Scratch &sc,
+                             int schedule, int wpc, int ctas, int probe, long long n_cores,
+                             cudaStream_t s)
+{
+    const size_t smem = smem_per_warp(sc.cap_s, sc.gcap_s) * (size_t)wpc;
+    cudaError_t e;
+    if (schedule == SELSCAN_SCHED_PLAIN) {
+        const int ipc = NPOP == 2 ? 2 : 4;
+        const size_t smem_p = smem_per_warp(sc.cap_s, sc.gcap_s) * (size_t)ipc;
+        e = cudaFuncSetAttribute(walk_plain_kernel<NPOP>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p);
+        if (e != cudaSuccess) return e;
+        // `ctas` carries the number of scratch slots; the bitmap was reset by the caller
+        zero_scratch_counts_kernel<<<1024, 256, 0, s>>>(sc, ctas);
+        walk_plain_kernel<NPOP><<<(unsigned)n_cores, ipc * 32, smem_p, s>>>(a, sk, sc, sk.slotmap,
+                                                                            ctas);
+        return cudaGetLastError();
+    }
+    e = cudaFuncSetAttribute(walk_persistent_kernel<NPOP>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    // persistent warps zero their own count arrays on entry
+    const int cap = schedule == SELSCAN_SCHED_LONGEST_FIRST ? probe : 0;
+    walk_persistent_kernel<NPOP><<<ctas, wpc * 32, smem, s>>>(a, sk, sc, n_cores, 1, cap);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (schedule == SELSCAN_SCHED_LONGEST_FIRST && probe > 0) {
+        bucket_hist_kernel<<<2 * sm_count(), 256, 0, s>>>(sk);
+        bucket_scan_kernel<<<1, NBUCKET, 0, s>>>(sk);
+        bucket_scatter_kernel<<<2 * sm_count(), 256, 0, s>>>(sk);
+        walk_persistent_kernel<NPOP><<<ctas, wpc * 32, smem, s>>>(a, sk, sc, n_cores, 2, 0);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_walk(const ScanArgs &a, const ItemSink &sink, const Scratch &sc,
+                        int schedule, int warps_per_cta, int ctas, int probe_steps,
+                        long long n_cores, cudaStream_t s)
+{
+    if (sink.mode == 1)
+        return walk_impl<2>(a, sink, sc, schedule, warps_per_cta, ctas, probe_steps, n_cores, s);
+    return walk_impl<1>(a, sink, sc, schedule, warps_per_cta, ctas, probe_steps, n_cores, s);
+}
+
+// ------------------------------------------------------------ finalize
+__global__ void finalize_ihs_kernel(ItemSink sk, long long m, double *ihh1, double *ihh0,
+                                    double *lnratio, int8_t *status)
+{
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < m;
+         c += (long long)gridDim.x * blockDim.x) {
+        if (sk.core_status[c] == (int8_t)SELSCAN_LOCUS_MAF_FILTERED) {
+            ihh1[c] = 0.0;
+            ihh0[c] = 0.0;
+            lnratio[c] = __longlong_as_double(0x7ff8000000000000ll);
+            for (int q = 0; q < 4; ++q) { sk.stop[4 * c + q] = 0; sk.digest[4 * c + q] = 0ull; }
+            continue;
+        }
+        int worst = 0;
+        for (int q = 0; q < 4; ++q) {
+            const int st = sk.item_status[4 * c + q];
+            worst = st > worst ? st : worst;
+        }
+        const double a1 = sk.item_ihh[4 * c] + sk.item_ihh[4 * c + 1];   // down + up
+        const double a0 = sk.item_ihh[4 * c + 2] + sk.item_ihh[4 * c + 3];
+        if (worst == 0 && (a1 == 0.0 || a0 == 0.0)) worst = SELSCAN_LOCUS_UNDEFINED;
+        ihh1[c] = a1;
+        ihh0[c] = a0;
+        status[c] = (int8_t)worst;
+        lnratio[c] = worst == 0 ? log(a1 / a0) : __longlong_as_double(0x7ff8000000000000ll);
+    }
+}
+
+__global__ void finalize_xpehh_kernel(ItemSink sk, long long m, double *ihhA, double *ihhB,
+                                      double *lnratio, int8_t *status)
+{
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < m;
+         c += (long long)gridDim.x * blockDim.x) {
+        if (sk.core_status[c] == (int8_t)SELSCAN_LOCUS_MAF_FILTERED) {
+            ihhA[c] = 0.0;
+            ihhB[c] = 0.0;
+            lnratio[c] = __longlong_as_double(0x7ff8000000000000ll);
+            for (int q = 0; q < 2; ++q) sk.stop[2 * c + q] = 0;
+            for (int q = 0; q < 6; ++q) sk.digest[6 * c + q] = 0ull;
+            continue;
+        }
+        int worst = 0;
+        for (int q = 0; q < 2; ++q) {
+            const int st = sk.item_status[2 * c + q];
+            worst = st > worst ? st : worst;
+        }
+        const double a = sk.item_ihh[4 * c] + sk.item_ihh[4 * c + 2];      // down + up, pop A
+        const double bb = sk.item_ihh[4 * c + 1] + sk.item_ihh[4 * c + 3]; // pop B
+        if (worst == 0 && (a == 0.0 || bb == 0.0)) worst = SELSCAN_LOCUS_UNDEFINED;
+        ihhA[c] = a;
+        ihhB[c] = bb;
+        status[c] = (int8_t)worst;
+        lnratio[c] = worst == 0 ? log(a / bb) : __longlong_as_double(0x7ff8000000000000ll);
+    }
+}
+
+cudaError_t launch_finalize_ihs(const ItemSink &sink, long long m, double *ihh1, double *ihh0,
+                                double *lnratio, int8_t *status, cudaStream_t s)
+{
+    long long blocks = (m + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    finalize_ihs_kernel<<<(unsigned)blocks, 256, 0, s>>>(sink, m, ihh1, ihh0, lnratio, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize_xpehh(const ItemSink &sink, long long m, double *ihhA,
+                                  double *ihhB, double *lnratio, int8_t *status, cudaStream_t s)
+{
+    long long blocks = (m + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    finalize_xpehh_kernel<<<(unsigned)blocks, 256, 0, s>>>(sink, m, ihhA, ihhB, lnratio, status);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ EHH trace
+__global__ void __launch_bounds__(192) ehh_trace_kernel(ScanArgs a, long long locus, Scratch sc,
+                                                        unsigned long long *S, long long cap,
+                                                        long long *len, int32_t *stop,
+                                                        int8_t *status, double *ihh,
+                                                        unsigned long long *denom)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31;
+    const int q = threadIdx.x >> 5;           // walk w = q / 2, direction q % 2
+    WarpBufs b = make_bufs(smem + (size_t)q * smem_per_warp(sc.cap_s, sc.gcap_s),
+                           sc.base + (size_t)q * sc.per_warp, sc);
+    zero_counts(b, sc, true);
+    const int w = q >> 1, dir = q & 1;
+    WalkOut o = walk<1>(a, locus, dir, w, b, S + (size_t)q * cap, cap, 0);
+    if (lane == 0) {
+        long long steps = 0;
+        if (o.status == W_OK) steps = o.stop + 1;
+        else if (o.status == W_EDGE || o.status == W_GAP) steps = o.stop;
+        len[q] = steps;
+        stop[q] = o.stop;
+        status[q] = (int8_t)o.status;
+        ihh[q] = o.ihh[0];
+    }
+    if (q == 0 && lane == 0) {
+        // denominators from the core row
+        const unsigned long long *row = a.hap + locus * a.ld;
+        unsigned long long c1 = 0;
+        for (int k = 0; k < a.W; ++k) c1 += (unsigned long long)__popcll(row[k] & valid_word(a, k));
+        const unsigned long long n = (unsigned long long)a.nA;
+        denom[0] = choose2(c1);
+        denom[1] = choose2(n - c1);
+        denom[2] = choose2(n);
+    }
+}
+
+cudaError_t launch_ehh(const ScanArgs &a, long long locus, const Scratch &sc,
+                       unsigned long long *S, long long cap, long long *len, int32_t *stop,
+                       int8_t *status, double *ihh, unsigned long long *denom, cudaStream_t s)
+{
+    const size_t smem = smem_per_warp(sc.cap_s, sc.gcap_s) * 6;
+    cudaError_t e = cudaFuncSetAttribute(ehh_trace_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    ehh_trace_kernel<<<1, 192, smem, s>>>(a, locus, sc, S, cap, len, stop, status, ihh, denom);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ pack
+// marker-major input: one warp per (marker, word); two ballots make a word
+__global__ void pack_mm_kernel(const uint8_t *hap01, int n, long long m, int W,
+                               unsigned long long *rows, long long ld)
+{
+    const int lane = threadIdx.x & 31;
+    const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long t = warp; t < m * ld; t += nw) {
+        const long long k = t / ld;
+        const int w = (int)(t % ld);
+        unsigned lo = 0, hi = 0;
+        if (w < W) {
+            const long long h0 = 64ll * w + lane, h1 = h0 + 32;
+            const bool b0 = h0 < n && (hap01[k * n + h0] & 1);
+            const bool b1 = h1 < n && (hap01[k * n + h1] & 1);
+            lo = __ballot_sync(FULLMASK, b0);
+            hi = __ballot_sync(FULLMASK, b1);
+        }
+        if (lane == 0) rows[k * ld + w] = (unsigned long long)lo | ((unsigned long long)hi << 32);
+    }
+}
+
+// haplotype-major input: one thread per (marker, word), threads along markers
+__global__ void pack_hm_kernel(const uint8_t *hap01, int n, long long m, int W,
+                               unsigned long long *rows, long long ld)
+{
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < m * ld;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long w = t / m, k = t % m;
+        unsigned long long v = 0;
+        if (w < W) {
+            for (int b = 0; b < 64; ++b) {
+                const long long h = 64 * w + b;
+                if (h < n && (hap01[h * m + k] & 1)) v |= 1ull << b;
+            }
+        }
+        rows[k * ld + w] = v;
+    }
+}
+
+cudaError_t launch_pack(const uint8_t *hap01, int n, long long m, int hap_major,
+                        unsigned long long *rows, long long ld, cudaStream_t s)
+{
+    const int W = (n + 63) / 64;
+    if (hap_major) {
+        long long blocks = (m * ld + 255) / 256;
+        if (blocks > 65536) blocks = 65536;
+        pack_hm_kernel<<<(unsigned)blocks, 256, 0, s>>>(hap01, n, m, W, rows, ld);
+    } else {
+        long long blocks = (m * ld * 32 + 255) / 256;
+        if (blocks > 65536) blocks = 65536;
+        pack_mm_kernel<<<(unsigned)blocks, 256, 0, s>>>(hap01, n, m, W, rows, ld);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace selscan

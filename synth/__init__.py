@@ -202,14 +202,16 @@ def spec(name: str, seed: int = 0) -> ScanSpec:
         return ScanSpec("xpehh", "xpehh", m, 35_000_000, seed,
                         [PopSpec(204, 30, [(17_500_000.0, 400_000.0, 0.6)]), PopSpec(210, 60)],
                         map_rate=1.2, map_spread=0.5, gaps=_chr22_gaps(m))
-    if name == "ihs1m":
-        m, L = 1_000_000, 250_000_000
+    if name in ("ihs1m", "ihs250k"):
+        # ihs250k: the same recipe on a quarter of the chromosome (5 sweeps), a
+        # profiling-sized case whose matrix (158 MB) still exceeds L2
+        m, L, ns = (1_000_000, 250_000_000, 20) if name == "ihs1m" else (250_000, 62_500_000, 5)
         sweeps = []
-        for k in range(20):
+        for k in range(ns):
             width = 50_000.0 + 450_000.0 * uniform(seed, 1, k)
             freq = 0.3 + 0.6 * uniform(seed, 2, k)
-            sweeps.append(((k + 0.5) / 20.0 * L, width, freq))
-        return ScanSpec("ihs1m", "ihs", m, L, seed, [PopSpec(5000, 200, sweeps)],
+            sweeps.append(((k + 0.5) / ns * L, width, freq))
+        return ScanSpec(name, "ihs", m, L, seed, [PopSpec(5000, 200, sweeps)],
                         map_rate=1.2, map_spread=0.5)
     raise KeyError(name)
 

@@ -1,0 +1,102 @@
+"""C ABI library: builds for sm_103a, loads, exports every declared symbol,
+and rejects bad arguments on the host (no GPU needed)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "selscan.h")
+
+
+@pytest.fixture(scope="module")
+def sg():
+    from paper_1403_6854_gb300 import _build
+    _build.build()
+    import paper_1403_6854_gb300 as sg
+    sg.load_library()
+    return sg
+
+
+def declared():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(selscan_[a-z_]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = declared()
+    for n in ("selscan_ihs", "selscan_xpehh", "selscan_ehh", "selscan_pack",
+              "selscan_workspace_bytes", "selscan_strerror", "selscan_default_params"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(sg):
+    lib = sg.load_library()
+    for name in declared():
+        assert hasattr(lib, name), name
+    out = subprocess.run(["nm", "-D", "--defined-only", sg.LIB_PATH], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (selscan_\w+)", out))
+    assert exported == set(declared())
+    assert set(sg.EXPORTS) == set(declared())
+
+
+def test_built_for_sm103a_only(sg):
+    from paper_1403_6854_gb300 import _build
+    assert _build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_strerror_and_defaults(sg):
+    assert sg.selscan_strerror(0) == "ok"
+    assert "workspace" in sg.selscan_strerror(sg.ERR_WORKSPACE)
+    assert sg.selscan_strerror(12345) == "unknown error code"
+    p = sg.selscan_default_params()
+    assert (p.ehh_cut_num, p.ehh_cut_den, p.maf_num, p.maf_den) == (1, 20, 1, 20)
+    assert (p.gap_scale_bp, p.max_gap_bp, p.include_crossing_term) == (20000, 200000, 0)
+
+
+def test_workspace_bytes(sg):
+    a = sg.selscan_workspace_bytes(100, 2000, sg.MODE_IHS)
+    b = sg.selscan_workspace_bytes(100, 4000, sg.MODE_IHS)
+    c = sg.selscan_workspace_bytes(5000, 2000, sg.MODE_IHS)
+    assert 0 < a < b and a < c
+    assert sg.selscan_workspace_bytes(1, 10, sg.MODE_IHS) == 0
+    assert sg.selscan_workspace_bytes(414, 100, sg.MODE_XPEHH) > 0
+    assert sg.selscan_workspace_bytes(100, 100, sg.MODE_EHH) > 0
+
+
+def test_host_side_argument_errors(sg):
+    lib = sg.load_library()
+    p = sg.selscan_default_params()
+    o = sg.selscan_ihs_out()
+    fake = ctypes.c_void_p(0x1000)
+    # null pointers
+    assert lib.selscan_ihs(None, 2, 100, 10, fake, fake, ctypes.byref(p), ctypes.byref(o), fake,
+                           1 << 20, None, None) == sg.ERR_INVALID_ARG
+    # n < 2 and ld < W, before any device work
+    o2 = sg.selscan_ihs_out(*([fake] * 8))
+    assert lib.selscan_ihs(fake, 2, 1, 10, fake, fake, ctypes.byref(p), ctypes.byref(o2), fake,
+                           1 << 20, None, None) == sg.ERR_INVALID_ARG
+    assert lib.selscan_ihs(fake, 1, 100, 10, fake, fake, ctypes.byref(p), ctypes.byref(o2), fake,
+                           1 << 20, None, None) == sg.ERR_INVALID_ARG
+    assert lib.selscan_ihs(fake, 2000, 70000, 10, fake, fake, ctypes.byref(p), ctypes.byref(o2),
+                           fake, 1 << 30, None, None) == sg.ERR_INVALID_ARG
+    # a zero denominator
+    bad = sg.selscan_default_params(ehh_cut=(1, 0))
+    assert lib.selscan_ihs(fake, 2, 100, 10, fake, fake, ctypes.byref(bad), ctypes.byref(o2), fake,
+                           1 << 20, None, None) == sg.ERR_INVALID_ARG
+    # workspace too small / misaligned
+    assert lib.selscan_ihs(fake, 2, 100, 10, fake, fake, ctypes.byref(p), ctypes.byref(o2), fake,
+                           16, None, None) == sg.ERR_WORKSPACE
+    assert lib.selscan_ihs(fake, 2, 100, 10, fake, fake, ctypes.byref(p), ctypes.byref(o2),
+                           ctypes.c_void_p(0x1008), 1 << 30, None, None) == sg.ERR_WORKSPACE
+    ox = sg.selscan_xpehh_out(*([fake] * 8))
+    assert lib.selscan_xpehh(fake, 2, 1, 5, 10, fake, fake, ctypes.byref(p), ctypes.byref(ox),
+                             fake, 1 << 20, None, None) == sg.ERR_INVALID_ARG
+    oe = sg.selscan_ehh_out(*([fake] * 7))
+    assert lib.selscan_ehh(fake, 2, 100, 10, fake, fake, 10, ctypes.byref(p), ctypes.byref(oe), 4,
+                           fake, 1 << 20, None) == sg.ERR_INVALID_ARG
+    assert lib.selscan_pack(fake, 100, 10, 2, fake, 2, None) == sg.ERR_INVALID_ARG
