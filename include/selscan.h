@@ -173,6 +173,26 @@ int selscan_ehh(const uint64_t *hap, int64_t ld, int32_t n, int64_t m,
                 const selscan_params *p, const selscan_ehh_out *out, int64_t capacity,
                 void *workspace, size_t ws_bytes, void *stream);
 
+/* Allocation-free variant of selscan_ehh, for callers that must not allocate
+ * device memory while they run (a process whose device memory belongs to
+ * another framework's pool, a service that reserves everything at start-up,
+ * or a path that cannot afford cudaMalloc's implicit synchronisation).  The
+ * paper has no counterpart; the results are those of selscan_ehh.  The walks'
+ * scratch is a fixed array inside the library's device image (about 1.4 MiB,
+ * held by every GPU that loads the library until the process exits), so there
+ * is no workspace argument and nothing is allocated or freed.
+ * - n above SELSCAN_EHH_NOALLOC_MAX_N is refused with SELSCAN_ERR_INVALID_ARG.
+ * - The first call on each device looks up the array's device address (with
+ *   that device current); make that first call before any stream capture.
+ * - Every call on a device shares the one array, which keeps the last call's
+ *   contents (the parts that must start at zero are cleared by the call);
+ *   calls that overlap on the same GPU race, so order them on one stream. */
+#define SELSCAN_EHH_NOALLOC_MAX_N 8192
+int selscan_ehh_noalloc(const uint64_t *hap, int64_t ld, int32_t n, int64_t m,
+                        const int64_t *pos_bp, const double *gmap, int64_t locus,
+                        const selscan_params *p, const selscan_ehh_out *out, int64_t capacity,
+                        void *stream);
+
 /* Pack a 0/1 uint8 matrix into rows (Section 1.1 coding, 0 ancestral / 1
  * derived).  hap_major = 0: hap01 is [m][n] (marker-major); 1: [n][m].
  * Values other than 0/1 are read as (v & 1).  rows: [m][ld], pad bits and

@@ -63,7 +63,8 @@ class selscan_ehh_out(ctypes.Structure):
 
 
 EXPORTS = ("selscan_default_params", "selscan_workspace_bytes", "selscan_ihs", "selscan_xpehh",
-           "selscan_ehh", "selscan_pack", "selscan_strerror")
+           "selscan_ehh", "selscan_ehh_noalloc", "selscan_pack", "selscan_strerror")
+EHH_NOALLOC_MAX_N = 8192
 
 _lib = None
 
@@ -96,6 +97,10 @@ def load_library():
                                 ctypes.c_int64, ctypes.POINTER(selscan_params),
                                 ctypes.POINTER(selscan_ehh_out), ctypes.c_int64, _P,
                                 ctypes.c_size_t, _P]
+    lib.selscan_ehh_noalloc.restype = ctypes.c_int
+    lib.selscan_ehh_noalloc.argtypes = [_P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int64, _P,
+                                        _P, ctypes.c_int64, ctypes.POINTER(selscan_params),
+                                        ctypes.POINTER(selscan_ehh_out), ctypes.c_int64, _P]
     lib.selscan_pack.restype = ctypes.c_int
     lib.selscan_pack.argtypes = [_P, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, _P,
                                  ctypes.c_int64, _P]
@@ -256,6 +261,33 @@ def selscan_ehh(hap: torch.Tensor, n: int, pos: torch.Tensor, gmap: torch.Tensor
                          ctypes.byref(o), capacity, _ptr(ws), ws.numel(), _stream(stream))
     if rc != OK:
         raise SelscanError(rc, "selscan_ehh")
+    return out
+
+
+def selscan_ehh_noalloc(hap: torch.Tensor, n: int, pos: torch.Tensor, gmap: torch.Tensor,
+                        locus: int, capacity: int, params: Optional[selscan_params] = None,
+                        stream=None) -> Dict[str, torch.Tensor]:
+    """selscan_ehh without a workspace: the library's fixed device scratch is
+    used instead (n <= EHH_NOALLOC_MAX_N; calls on one GPU must not overlap).
+    The output tensors are still allocated here, by the caller's side."""
+    lib = load_library()
+    hap = _as_rows(hap)
+    m, ld = hap.shape
+    dev = hap.device
+    out = dict(S=torch.zeros((3, 2, max(capacity, 0)), dtype=torch.int64, device=dev),
+               len=torch.empty((3, 2), dtype=torch.int64, device=dev),
+               stop=torch.empty((3, 2), dtype=torch.int32, device=dev),
+               status=torch.empty((3, 2), dtype=torch.int8, device=dev),
+               ihh=torch.empty((3, 2), dtype=torch.float64, device=dev),
+               denom=torch.empty(3, dtype=torch.int64, device=dev),
+               error=torch.zeros(1, dtype=torch.int32, device=dev))
+    p = params if params is not None else selscan_default_params()
+    o = selscan_ehh_out(*(_ptr(out[f]) if out[f].numel() else None
+                          for f in ("S", "len", "stop", "status", "ihh", "denom", "error")))
+    rc = lib.selscan_ehh_noalloc(_ptr(hap), ld, n, m, _ptr(pos), _ptr(gmap), locus,
+                                 ctypes.byref(p), ctypes.byref(o), capacity, _stream(stream))
+    if rc != OK:
+        raise SelscanError(rc, "selscan_ehh_noalloc")
     return out
 
 

@@ -51,12 +51,10 @@ __host__ __device__ inline size_t smem_per_warp(int cap_s, int gcap_s)
 
 // bytes of one warp's global slice: entries never exceed the sample size,
 // groups (two or more members each) never exceed half of it
-__host__ __device__ inline size_t scratch_per_warp(int n_total)
+__host__ __device__ constexpr size_t scratch_per_warp(int n_total)
 {
-    const size_t cap = (size_t)n_total;
-    const size_t gcap = (size_t)n_total / 2 + 1;
-    size_t b = cap * 2 * 8 + cap * 2 * 4 + gcap * 3 * 4;
-    return (b + 255) & ~(size_t)255;
+    return ((size_t)n_total * 2 * 8 + (size_t)n_total * 2 * 4 + ((size_t)n_total / 2 + 1) * 3 * 4 +
+            255) & ~(size_t)255;
 }
 
 // kernel launchers (kernels.cu)
