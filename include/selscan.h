@@ -46,7 +46,7 @@
  * output's `error` word (0 = none) instead.  Per-locus outcomes are status
  * codes, not errors.  No C++ exception crosses this boundary.
  *
- * Limits: n (iHS) and n_A + n_B (XPEHH) at most 65,535 haplotypes; m < 2^30
+ * Limits: n (iHS) and n_A + n_B (XPEHH) at most 65,000 haplotypes; m < 2^30
  * markers.
  */
 #ifndef SELSCAN_GB300_H
@@ -67,6 +67,7 @@ extern "C" {
 #define SELSCAN_ERR_CUDA          -4  /* a kernel launch or CUDA runtime call failed */
 #define SELSCAN_ERR_TIMEOUT       -5  /* (device error word) a bounded device wait gave up */
 #define SELSCAN_ERR_UNSUPPORTED   -6  /* no sm_103a device, or a launch shape it cannot run */
+#define SELSCAN_ERR_INTERNAL      -7  /* (device error word) an internal consistency check failed */
 
 /* ---- per-locus status (Section 1.2 rules) ---- */
 #define SELSCAN_LOCUS_OK            0
@@ -88,13 +89,14 @@ typedef struct {
 } selscan_params;
 
 /* Scheduling of the walk kernel.  Changes how the work runs, never the
- * results.  A NULL selscan_launch* selects the library defaults. */
+ * results.  A NULL selscan_launch* selects the library defaults (in-order
+ * persistent schedule, 8 warps per CTA, 512 on-chip group words per warp). */
 #define SELSCAN_SCHED_LONGEST_FIRST 0  /* persistent kernel, probe pass + longest-first queue */
 #define SELSCAN_SCHED_IN_ORDER      1  /* persistent kernel, one queue in core order */
 #define SELSCAN_SCHED_PLAIN         2  /* one CTA per core, no persistence, no ordering */
 typedef struct {
     int32_t schedule;       /* SELSCAN_SCHED_* */
-    int32_t warps_per_cta;  /* 1..16 (0 = default) */
+    int32_t warps_per_cta;  /* 1..8 (0 = default) */
     int32_t ctas_per_sm;    /* persistent grid = SMs x this (0 = max resident) */
     int32_t smem_entries;   /* per-warp on-chip group-word capacity (0 = default) */
     int32_t probe_steps;    /* first-pass step cap of the longest-first schedule (0 = default) */
@@ -178,14 +180,14 @@ int selscan_ehh(const uint64_t *hap, int64_t ld, int32_t n, int64_t m,
  * another framework's pool, a service that reserves everything at start-up,
  * or a path that cannot afford cudaMalloc's implicit synchronisation).  The
  * paper has no counterpart; the results are those of selscan_ehh.  The walks'
- * scratch is a fixed array inside the library's device image (about 1.4 MiB,
+ * scratch is a fixed array inside the library's device image (about 1.2 MiB,
  * held by every GPU that loads the library until the process exits), so there
  * is no workspace argument and nothing is allocated or freed.
  * - n above SELSCAN_EHH_NOALLOC_MAX_N is refused with SELSCAN_ERR_INVALID_ARG.
  * - The first call on each device looks up the array's device address (with
  *   that device current); make that first call before any stream capture.
  * - Every call on a device shares the one array, which keeps the last call's
- *   contents (the parts that must start at zero are cleared by the call);
+ *   contents (each call initialises what it reads, so no clearing is needed);
  *   calls that overlap on the same GPU race, so order them on one stream. */
 #define SELSCAN_EHH_NOALLOC_MAX_N 8192
 int selscan_ehh_noalloc(const uint64_t *hap, int64_t ld, int32_t n, int64_t m,

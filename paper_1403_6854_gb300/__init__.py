@@ -27,6 +27,7 @@ LIB_PATH = os.path.join(_PKG, "libselscan_gb300.so")
 # return codes and per-locus status codes (include/selscan.h)
 OK = 0
 ERR_INVALID_ARG, ERR_UNSORTED, ERR_WORKSPACE, ERR_CUDA, ERR_TIMEOUT, ERR_UNSUPPORTED = -1, -2, -3, -4, -5, -6
+ERR_INTERNAL = -7
 LOCUS_OK, LOCUS_MAF_FILTERED, LOCUS_UNDEFINED, LOCUS_ABORT_EDGE, LOCUS_ABORT_GAP = 0, 1, 2, 3, 4
 MODE_IHS, MODE_XPEHH, MODE_EHH = 0, 1, 2
 SCHED_LONGEST_FIRST, SCHED_IN_ORDER, SCHED_PLAIN = 0, 1, 2
@@ -133,7 +134,7 @@ def selscan_default_params(**overrides) -> selscan_params:
     return p
 
 
-def make_launch(schedule: int = SCHED_LONGEST_FIRST, warps_per_cta: int = 0, ctas_per_sm: int = 0,
+def make_launch(schedule: int = SCHED_IN_ORDER, warps_per_cta: int = 0, ctas_per_sm: int = 0,
                 smem_entries: int = 0, probe_steps: int = 0, events=None) -> selscan_launch:
     """events: optional (begin, end) torch.cuda.Event pair bracketing the walk kernels."""
     L = selscan_launch(schedule, warps_per_cta, ctas_per_sm, smem_entries, probe_steps)

@@ -15,9 +15,9 @@ using namespace selscan;
 namespace {
 
 constexpr int kDefaultWarpsPerCta = 8;
-constexpr int kDefaultSmemEntries = 128;
+constexpr int kDefaultSmemEntries = 512;
 constexpr int kDefaultProbeSteps = 48;
-constexpr int kMaxHaplotypes = 65535;
+constexpr int kMaxHaplotypes = 65000;
 constexpr size_t kMaxSmemPerCta = 227 * 1024;
 
 struct Plan {
@@ -25,8 +25,9 @@ struct Plan {
     int wpc;            // warps per CTA of the walk kernel
     int ctas;           // persistent grid size
     int nslots;         // global scratch slices (warps)
-    int cap_s, gcap_s;
+    int cap_s, tcap_s;
     int probe;
+    int R, rowcap, poscap;
 };
 
 inline size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -37,16 +38,19 @@ bool params_ok(const selscan_params *p)
            (p->include_crossing_term == 0 || p->include_crossing_term == 1);
 }
 
-Plan make_plan(int mode, const selscan_launch *L)
+Plan make_plan(int mode, long long ld, const selscan_launch *L)
 {
     Plan p;
-    p.schedule = L ? L->schedule : SELSCAN_SCHED_LONGEST_FIRST;
+    p.schedule = L ? L->schedule : SELSCAN_SCHED_IN_ORDER;
     if (p.schedule < 0 || p.schedule > SELSCAN_SCHED_PLAIN) p.schedule = -1;
     p.cap_s = (L && L->smem_entries > 0) ? L->smem_entries : kDefaultSmemEntries;
-    if (p.cap_s > 4096) p.cap_s = 4096;
-    p.cap_s = (p.cap_s + 1) & ~1;
-    p.gcap_s = p.cap_s / 2;
+    if (p.cap_s > 8192) p.cap_s = 8192;
+    p.cap_s = (p.cap_s + 31) & ~31;
+    p.tcap_s = ((p.cap_s / 4) + 31) & ~31;
     p.probe = (L && L->probe_steps > 0) ? L->probe_steps : kDefaultProbeSteps;
+    p.R = window_rows(ld);
+    p.rowcap = win_rowcap(p.R, ld);
+    p.poscap = win_poscap(p.R);
     const int sms = device_sms();
     if (mode == SELSCAN_MODE_EHH) {
         p.schedule = SELSCAN_SCHED_IN_ORDER;
@@ -58,7 +62,7 @@ Plan make_plan(int mode, const selscan_launch *L)
     const int ipc = mode == SELSCAN_MODE_XPEHH ? 2 : 4;
     if (p.schedule == SELSCAN_SCHED_PLAIN) {
         p.wpc = ipc;
-        const size_t smem = smem_per_warp(p.cap_s, p.gcap_s) * (size_t)ipc;
+        const size_t smem = smem_per_warp(p.cap_s, p.tcap_s, p.rowcap, p.poscap) * (size_t)ipc;
         int per_sm = max_ctas_per_sm(p.schedule, ipc, smem);
         if (per_sm < 1) per_sm = 64 / ipc;                 // no device: the architectural maximum
         p.ctas = 0;
@@ -66,8 +70,8 @@ Plan make_plan(int mode, const selscan_launch *L)
         return p;
     }
     p.wpc = (L && L->warps_per_cta > 0) ? L->warps_per_cta : kDefaultWarpsPerCta;
-    if (p.wpc > 16) p.wpc = 16;
-    const size_t smem = smem_per_warp(p.cap_s, p.gcap_s) * (size_t)p.wpc;
+    if (p.wpc > 8) p.wpc = 8;
+    const size_t smem = smem_per_warp(p.cap_s, p.tcap_s, p.rowcap, p.poscap) * (size_t)p.wpc;
     int per_sm = max_ctas_per_sm(p.schedule, p.wpc, smem);
     if (per_sm < 1) per_sm = 64 / p.wpc > 0 ? 64 / p.wpc : 1;
     int want = (L && L->ctas_per_sm > 0) ? L->ctas_per_sm : per_sm;
@@ -82,13 +86,13 @@ struct Layout {
     size_t per_warp;
 };
 
-Layout make_layout(int n_total, long long m, int mode, const Plan &p)
+Layout make_layout(int n_total, long long m, int mode, int nslots)
 {
     Layout l;
     const long long items = mode == SELSCAN_MODE_EHH ? 0 : m * (mode == SELSCAN_MODE_XPEHH ? 2 : 4);
     size_t o = 0;
     l.queue = o;        o += up256(sizeof(Queue));
-    l.slotmap = o;      o += up256(((size_t)p.nslots + 31) / 32 * 4);
+    l.slotmap = o;      o += up256(((size_t)nslots + 31) / 32 * 4);
     l.item_status = o;  o += up256((size_t)items);
     l.item_ihh = o;     o += up256((size_t)items * 8 * (mode == SELSCAN_MODE_XPEHH ? 2 : 1));
     l.list2 = o;        o += up256((size_t)items * 4);
@@ -96,7 +100,7 @@ Layout make_layout(int n_total, long long m, int mode, const Plan &p)
     l.sorted2 = o;      o += up256((size_t)items * 4);
     l.bucket = o;       o += up256((NBUCKET + 1) * 4);
     l.per_warp = scratch_per_warp(n_total);
-    l.scratch = o;      o += (size_t)p.nslots * l.per_warp;
+    l.scratch = o;      o += (size_t)nslots * l.per_warp;
     l.total = o;
     return l;
 }
@@ -134,10 +138,13 @@ Scratch make_scratch(unsigned char *ws, const Layout &l, int n_total, const Plan
     Scratch sc;
     sc.base = ws + l.scratch;
     sc.per_warp = l.per_warp;
-    sc.cap = n_total;
-    sc.gcap = n_total / 2 + 1;
+    sc.cap = list_cap(n_total);
+    sc.tcap = table_cap(n_total);
     sc.cap_s = p.cap_s;
-    sc.gcap_s = p.gcap_s;
+    sc.tcap_s = p.tcap_s;
+    sc.R = p.R;
+    sc.rowcap = p.rowcap;
+    sc.poscap = p.poscap;
     return sc;
 }
 
@@ -148,11 +155,11 @@ int run_scan(int mode, const uint64_t *hap, int64_t ld, int32_t nA, int32_t nB, 
              void *stream)
 {
     const int n_total = nA + nB;
-    const Plan plan = make_plan(mode, launch);
+    const Plan plan = make_plan(mode, ld, launch);
     if (plan.schedule < 0 || (launch && launch->warps_per_cta < 0)) return SELSCAN_ERR_INVALID_ARG;
-    if (smem_per_warp(plan.cap_s, plan.gcap_s) * (size_t)plan.wpc > kMaxSmemPerCta)
+    if (smem_per_warp(plan.cap_s, plan.tcap_s, plan.rowcap, plan.poscap) * (size_t)plan.wpc > kMaxSmemPerCta)
         return SELSCAN_ERR_UNSUPPORTED;
-    const Layout l = make_layout(n_total, m, mode, plan);
+    const Layout l = make_layout(n_total, m, mode, plan.nslots);
     if (!workspace || ws_bytes < l.total || ((uintptr_t)workspace & 255)) return SELSCAN_ERR_WORKSPACE;
     cudaStream_t s = (cudaStream_t)stream;
     unsigned char *ws = (unsigned char *)workspace;
@@ -171,7 +178,8 @@ int run_scan(int mode, const uint64_t *hap, int64_t ld, int32_t nA, int32_t nB, 
     sk.bucket = (uint32_t *)(ws + l.bucket);
     sk.slotmap = (uint32_t *)(ws + l.slotmap);
     sk.q = (Queue *)(ws + l.queue);
-    const Scratch sc = make_scratch(ws, l, n_total, plan);
+    Scratch sc = make_scratch(ws, l, n_total, plan);
+    sc.err = err;
 
     cudaError_t e;
     if ((e = cudaMemsetAsync(ws, 0, l.item_status, s)) != cudaSuccess) return SELSCAN_ERR_CUDA;
@@ -217,8 +225,11 @@ void selscan_default_params(selscan_params *p)
 size_t selscan_workspace_bytes(int32_t n_total, int64_t m, int32_t mode, const selscan_launch *launch)
 {
     if (n_total < 2 || m < 1 || mode < 0 || mode > 2) return 0;
-    const Plan p = make_plan(mode, launch);
-    return make_layout(n_total, m, mode, p).total;
+    // scratch slots for the most warps an SM can hold (64), so the size does
+    // not depend on the row stride, registers or shared memory of the call
+    const Plan p = make_plan(mode, (n_total + 63) / 64, launch);
+    const int nslots = mode == SELSCAN_MODE_EHH ? p.nslots : device_sms() * 64;
+    return make_layout(n_total, m, mode, nslots).total;
 }
 
 int selscan_ihs(const uint64_t *hap, int64_t ld, int32_t n, int64_t m, const int64_t *pos_bp,
@@ -265,12 +276,13 @@ int selscan_ehh(const uint64_t *hap, int64_t ld, int32_t n, int64_t m, const int
     if ((capacity > 0 && !out->S) || !out->len || !out->stop || !out->status || !out->ihh ||
         !out->denom || !out->error)
         return SELSCAN_ERR_INVALID_ARG;
-    const Plan plan = make_plan(SELSCAN_MODE_EHH, nullptr);
-    const Layout l = make_layout(n, m, SELSCAN_MODE_EHH, plan);
+    const Plan plan = make_plan(SELSCAN_MODE_EHH, ld, nullptr);
+    const Layout l = make_layout(n, m, SELSCAN_MODE_EHH, plan.nslots);
     if (!workspace || ws_bytes < l.total || ((uintptr_t)workspace & 255)) return SELSCAN_ERR_WORKSPACE;
     cudaStream_t s = (cudaStream_t)stream;
     const ScanArgs a = make_args(hap, ld, n, 0, m, pos_bp, gmap, p);
-    const Scratch sc = make_scratch((unsigned char *)workspace, l, n, plan);
+    Scratch sc = make_scratch((unsigned char *)workspace, l, n, plan);
+    sc.err = out->error;
     if (cudaMemsetAsync(out->error, 0, sizeof(int32_t), s) != cudaSuccess) return SELSCAN_ERR_CUDA;
     if (launch_validate((const long long *)pos_bp, gmap, m, out->error, s) != cudaSuccess)
         return SELSCAN_ERR_CUDA;
@@ -302,6 +314,7 @@ const char *selscan_strerror(int code)
     case SELSCAN_ERR_CUDA: return "CUDA launch or runtime error";
     case SELSCAN_ERR_TIMEOUT: return "bounded device wait gave up";
     case SELSCAN_ERR_UNSUPPORTED: return "unsupported device or launch shape";
+    case SELSCAN_ERR_INTERNAL: return "internal consistency check failed on the device";
     default: return "unknown error code";
     }
 }

@@ -35,26 +35,45 @@ constexpr int NBUCKET = 256;
 
 // Per-warp scratch layout in global memory.
 struct Scratch {
-    unsigned char *base;          // nwarps * per_warp bytes
+    unsigned char *base;          // nslots * per_warp bytes
     size_t per_warp;
-    int cap;                      // entries per global buffer (>= n_total)
-    int gcap;                     // groups per global array
-    int cap_s, gcap_s;            // on-chip capacities
+    int cap;                      // pool entries per walk
+    int tcap;                     // table rows per walk
+    int cap_s, tcap_s;            // on-chip tier sizes (multiples of 32)
+    int R;                        // marker-window rows per buffer
+    int rowcap, poscap;           // window buffer bytes (rows; positions or map values)
+    int *err;                     // device error word
 };
 
-// bytes of one warp's on-chip slice: two entry buffers + three group arrays
-__host__ __device__ inline size_t smem_per_warp(int cap_s, int gcap_s)
+// pool: live entries never exceed the sample size (disjoint, non-empty member
+// masks) and one step at most doubles the pool before it is compacted
+__host__ __device__ constexpr int list_cap(int n_total) { return ((2 * n_total + 64) + 31) & ~31; }
+// table: live groups have two or more members, one step at most doubles the rows
+__host__ __device__ constexpr int table_cap(int n_total) { return ((n_total + 64) + 31) & ~31; }
+
+// marker window: rows per buffer so that one buffer holds about 1 KB of rows
+__host__ __device__ constexpr int window_rows(long long ld)
 {
-    size_t b = (size_t)cap_s * 2 * 8 + (size_t)cap_s * 2 * 4 + (size_t)gcap_s * 3 * 4;
-    return (b + 15) & ~(size_t)15;
+    return 1024 / (ld * 8) < 2 ? 2 : (1024 / (ld * 8) > 64 ? 64 : (int)(1024 / (ld * 8)));
+}
+// one buffer's bytes: R rows (+ up to 8 bytes of alignment), 16-byte multiple
+__host__ __device__ constexpr int win_rowcap(int R, long long ld) { return (int)((R * ld * 8 + 8 + 15) & ~15ll); }
+// positions (or map values) of R + 2 markers (+ alignment)
+__host__ __device__ constexpr int win_poscap(int R) { return ((R + 2) * 8 + 8 + 15) & ~15; }
+
+// bytes of one warp's on-chip slice: pool entries, one table word per row,
+// and the marker window (two row buffers, two position and two map buffers,
+// two mbarriers)
+__host__ __device__ constexpr size_t smem_per_warp(int cap_s, int tcap_s, int rowcap, int poscap)
+{
+    return (size_t)cap_s * 8 + (size_t)tcap_s * 8 + 2 * (size_t)rowcap + 4 * (size_t)poscap + 16;
 }
 
-// bytes of one warp's global slice: entries never exceed the sample size,
-// groups (two or more members each) never exceed half of it
+// bytes of one warp's global slice: pool, one table word and one 16-bit
+// row list per row
 __host__ __device__ constexpr size_t scratch_per_warp(int n_total)
 {
-    return ((size_t)n_total * 2 * 8 + (size_t)n_total * 2 * 4 + ((size_t)n_total / 2 + 1) * 3 * 4 +
-            255) & ~(size_t)255;
+    return ((size_t)list_cap(n_total) * 8 + (size_t)table_cap(n_total) * 10 + 255) & ~(size_t)255;
 }
 
 // kernel launchers (kernels.cu)

@@ -20,34 +20,41 @@ __device__ __forceinline__ WarpBufs make_bufs(unsigned char *sm, unsigned char *
 {
     WarpBufs b;
     b.cap_s = sc.cap_s;
-    b.gcap_s = sc.gcap_s;
-    unsigned char *p = sm;
-    b.mask[0] = (unsigned long long *)p; p += (size_t)sc.cap_s * 8;
-    b.mask[1] = (unsigned long long *)p; p += (size_t)sc.cap_s * 8;
-    b.meta[0] = (unsigned int *)p; p += (size_t)sc.cap_s * 4;
-    b.meta[1] = (unsigned int *)p; p += (size_t)sc.cap_s * 4;
-    b.cnt[0] = (unsigned int *)p; p += (size_t)sc.gcap_s * 4;
-    b.cntB[0] = (unsigned int *)p; p += (size_t)sc.gcap_s * 4;
-    b.nid[0] = (unsigned int *)p;
-    p = gm;
-    b.mask[2] = (unsigned long long *)p; p += (size_t)sc.cap * 8;
-    b.mask[3] = (unsigned long long *)p; p += (size_t)sc.cap * 8;
-    b.meta[2] = (unsigned int *)p; p += (size_t)sc.cap * 4;
-    b.meta[3] = (unsigned int *)p; p += (size_t)sc.cap * 4;
-    b.cnt[1] = (unsigned int *)p; p += (size_t)sc.gcap * 4;
-    b.cntB[1] = (unsigned int *)p; p += (size_t)sc.gcap * 4;
-    b.nid[1] = (unsigned int *)p;
+    b.cap = sc.cap;
+    b.tcap_s = sc.tcap_s;
+    b.tcap = sc.tcap;
+    b.pool_s = (unsigned long long *)sm;
+    b.tab_s = (unsigned long long *)(sm + (size_t)sc.cap_s * 8);
+    b.pool_g = (unsigned long long *)gm;
+    b.tab_g = (unsigned long long *)(gm + (size_t)sc.cap * 8);
+    b.big = (unsigned short *)(b.tab_g + sc.tcap);
+    b.err = sc.err;
+    unsigned char *w = sm + (size_t)sc.cap_s * 8 + (size_t)sc.tcap_s * 8;
+    b.wrow[0] = w; w += sc.rowcap;
+    b.wrow[1] = w; w += sc.rowcap;
+    b.wpos[0] = (long long *)w; w += sc.poscap;
+    b.wpos[1] = (long long *)w; w += sc.poscap;
+    b.wgm[0] = (double *)w; w += sc.poscap;
+    b.wgm[1] = (double *)w; w += sc.poscap;
+    b.bar = (unsigned long long *)w;
+    b.R = sc.R;
     return b;
 }
 
-// the count arrays must be zero when a walk starts; walks leave them zero
-__device__ __forceinline__ void zero_counts(WarpBufs &b, const Scratch &sc, bool global_too)
+// one-time set-up of the warp's two window mbarriers (fresh shared memory)
+__device__ __forceinline__ void init_window(const WarpBufs &b)
 {
-    const int lane = threadIdx.x & 31;
-    for (int g = lane; g < sc.gcap_s; g += 32) { b.cnt[0][g] = 0; b.cntB[0][g] = 0; }
-    if (global_too)
-        for (int g = lane; g < sc.gcap; g += 32) { b.cnt[1][g] = 0; b.cntB[1][g] = 0; }
+    if ((threadIdx.x & 31) == 0) {
+        mbar_init(b.bar, 1u);
+        mbar_init(b.bar + 1, 1u);
+    }
+    fence_proxy_async();
     __syncwarp();
+}
+
+__host__ __device__ __forceinline__ size_t slice_bytes(const Scratch &sc)
+{
+    return smem_per_warp(sc.cap_s, sc.tcap_s, sc.rowcap, sc.poscap);
 }
 
 // ------------------------------------------------------------ validate
@@ -80,9 +87,9 @@ __global__ void core_select_kernel(ScanArgs a, int mode, unsigned maf_num, unsig
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
     const unsigned n_total = (unsigned)(a.nA + a.nB);
     for (long long k = warp; k < a.m; k += nw) {
-        const unsigned long long *row = a.hap + k * a.ld;
+        const unsigned int *row = (const unsigned int *)(a.hap + k * a.ld);
         unsigned c = 0;
-        for (int w = lane; w < a.W; w += 32) c += (unsigned)__popcll(__ldg(row + w) & valid_word(a, w));
+        for (int w = lane; w < 2 * a.W; w += 32) c += (unsigned)__popc(__ldg(row + w) & valid32(a, w));
         c = __reduce_add_sync(FULLMASK, c);
         if (lane == 0) {
             n1[k] = (int32_t)c;
@@ -117,7 +124,7 @@ __device__ __forceinline__ uint32_t bucket_of(float ehh)
 
 template <int NPOP>
 __device__ __forceinline__ void run_item(const ScanArgs &a, const ItemSink &sk, WarpBufs &b,
-                                         uint32_t item, int max_steps)
+                                         uint32_t item, int max_steps, unsigned wpar[2])
 {
     const int lane = threadIdx.x & 31;
     const int ipc = NPOP == 2 ? 2 : 4;
@@ -125,7 +132,7 @@ __device__ __forceinline__ void run_item(const ScanArgs &a, const ItemSink &sk, 
     const int q = (int)(item % ipc);
     const int dir = q & 1;
     const int sel = NPOP == 2 ? 0 : (q < 2 ? 0 : 1);
-    WalkOut o = walk<NPOP>(a, core, dir, sel, b, nullptr, 0, max_steps);
+    WalkOut o = walk<NPOP>(a, core, dir, sel, b, nullptr, 0, max_steps, wpar);
     if (lane != 0) return;
     if (o.status == W_UNFINISHED) {
         const unsigned long long slot = atomicAdd(&sk.q->n2, 1ull);
@@ -151,7 +158,7 @@ __device__ __forceinline__ void run_item(const ScanArgs &a, const ItemSink &sk, 
 // core's items per queue fetch), optionally capped at max_steps; pass 2:
 // the sorted list of walks the first pass left unfinished, one per fetch.
 template <int NPOP>
-__global__ void __launch_bounds__(512) walk_persistent_kernel(ScanArgs a, ItemSink sk, Scratch sc,
+__global__ void __launch_bounds__(256, 2) walk_persistent_kernel(ScanArgs a, ItemSink sk, Scratch sc,
                                                               long long n_cores, int pass,
                                                               int max_steps)
 {
@@ -160,9 +167,10 @@ __global__ void __launch_bounds__(512) walk_persistent_kernel(ScanArgs a, ItemSi
     const int warp = threadIdx.x >> 5;
     const int wpc = blockDim.x >> 5;
     const long long gw = (long long)blockIdx.x * wpc + warp;
-    WarpBufs b = make_bufs(smem + (size_t)warp * smem_per_warp(sc.cap_s, sc.gcap_s),
+    WarpBufs b = make_bufs(smem + (size_t)warp * slice_bytes(sc),
                            sc.base + (size_t)gw * sc.per_warp, sc);
-    zero_counts(b, sc, true);
+    init_window(b);
+    unsigned wpar[2] = {0u, 0u};
     const int ipc = NPOP == 2 ? 2 : 4;
     const unsigned long long total = pass == 2 ? sk.q->n2 : (unsigned long long)n_cores;
     for (;;) {
@@ -171,10 +179,11 @@ __global__ void __launch_bounds__(512) walk_persistent_kernel(ScanArgs a, ItemSi
         idx = __shfl_sync(FULLMASK, idx, 0);
         if (idx >= total) break;
         if (pass == 2) {
-            run_item<NPOP>(a, sk, b, sk.sorted2[idx], 0);
+            run_item<NPOP>(a, sk, b, sk.sorted2[idx], 0, wpar);
         } else {
             if (sk.core_status[idx] == (int8_t)SELSCAN_LOCUS_MAF_FILTERED) continue;
-            for (int q = 0; q < ipc; ++q) run_item<NPOP>(a, sk, b, (uint32_t)(idx * ipc + q), max_steps);
+            for (int q = 0; q < ipc; ++q)
+                run_item<NPOP>(a, sk, b, (uint32_t)(idx * ipc + q), max_steps, wpar);
         }
     }
 }
@@ -205,25 +214,15 @@ __global__ void __launch_bounds__(128) walk_plain_kernel(ScanArgs a, ItemSink sk
         if (lane == 0) sk.item_status[core * (NPOP == 2 ? 2 : 4) + warp] = (int8_t)W_UNFINISHED;
         return;
     }
-    WarpBufs b = make_bufs(smem + (size_t)warp * smem_per_warp(sc.cap_s, sc.gcap_s),
+    WarpBufs b = make_bufs(smem + (size_t)warp * slice_bytes(sc),
                            sc.base + (size_t)slot * sc.per_warp, sc);
-    zero_counts(b, sc, false);
-    run_item<NPOP>(a, sk, b, (uint32_t)(core * (NPOP == 2 ? 2 : 4) + warp), 0);
+    init_window(b);
+    unsigned wpar[2] = {0u, 0u};
+    run_item<NPOP>(a, sk, b, (uint32_t)(core * (NPOP == 2 ? 2 : 4) + warp), 0, wpar);
     __syncwarp();
     if (lane == 0) {
         __threadfence();
         atomicAnd(slotmap + (slot >> 5), ~(1u << (slot & 31)));
-    }
-}
-
-__global__ void zero_scratch_counts_kernel(Scratch sc, long long nwarps)
-{
-    const long long words = (long long)sc.gcap * 2;   // cnt and cntB are adjacent
-    const size_t off = (size_t)sc.cap * 2 * 8 + (size_t)sc.cap * 2 * 4;
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nwarps * words;
-         t += (long long)gridDim.x * blockDim.x) {
-        const long long w = t / words, k = t % words;
-        ((unsigned int *)(sc.base + (size_t)w * sc.per_warp + off))[k] = 0u;
     }
 }
 
@@ -280,12 +279,19 @@ int max_ctas_per_sm(int schedule, int warps_per_cta, size_t smem_bytes)
 {
     int nb = 0;
     cudaError_t e;
-    if (schedule == SELSCAN_SCHED_PLAIN)
+    if (schedule == SELSCAN_SCHED_PLAIN) {
+        cudaFuncSetAttribute(walk_plain_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem_bytes);
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, walk_plain_kernel<1>,
                                                           warps_per_cta * 32, smem_bytes);
-    else
+    } else {
+        cudaFuncSetAttribute(walk_persistent_kernel<1>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+        cudaFuncSetAttribute(walk_persistent_kernel<1>,
+                             cudaFuncAttributePreferredSharedMemoryCarveout, 100);
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, walk_persistent_kernel<1>,
                                                           warps_per_cta * 32, smem_bytes);
+    }
     if (e != cudaSuccess || nb < 1) { cudaGetLastError(); return -1; }
     int nb2 = 0;
     if (schedule == SELSCAN_SCHED_PLAIN)
@@ -301,21 +307,30 @@ int max_ctas_per_sm(int schedule, int warps_per_cta, size_t smem_bytes)
 
 int device_sms() { return sm_count(); }
 
+// percentage of the unified L1/shared array to reserve for shared memory so
+// that the CTAs one SM holds at once fit (228 KB per SM on this part)
+static int carveout_pct(size_t smem_per_cta, int ctas)
+{
+    const int per_sm = (ctas + sm_count() - 1) / sm_count();
+    const size_t need = (smem_per_cta + 1024) * (size_t)per_sm;
+    int pct = (int)((need * 100 + 228 * 1024 - 1) / (228 * 1024));
+    return pct > 100 ? 100 : (pct < 10 ? 10 : pct);
+}
+
 template <int NPOP>
 static cudaError_t walk_impl(const ScanArgs &a, const ItemSink &sk, const Scratch &sc,
                              int schedule, int wpc, int ctas, int probe, long long n_cores,
                              cudaStream_t s)
 {
-    const size_t smem = smem_per_warp(sc.cap_s, sc.gcap_s) * (size_t)wpc;
+    const size_t smem = slice_bytes(sc) * (size_t)wpc;
     cudaError_t e;
     if (schedule == SELSCAN_SCHED_PLAIN) {
         const int ipc = NPOP == 2 ? 2 : 4;
-        const size_t smem_p = smem_per_warp(sc.cap_s, sc.gcap_s) * (size_t)ipc;
+        const size_t smem_p = slice_bytes(sc) * (size_t)ipc;
         e = cudaFuncSetAttribute(walk_plain_kernel<NPOP>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p);
         if (e != cudaSuccess) return e;
         // `ctas` carries the number of scratch slots; the bitmap was reset by the caller
-        zero_scratch_counts_kernel<<<1024, 256, 0, s>>>(sc, ctas);
         walk_plain_kernel<NPOP><<<(unsigned)n_cores, ipc * 32, smem_p, s>>>(a, sk, sc, sk.slotmap,
                                                                             ctas);
         return cudaGetLastError();
@@ -323,7 +338,10 @@ static cudaError_t walk_impl(const ScanArgs &a, const ItemSink &sk, const Scratc
     e = cudaFuncSetAttribute(walk_persistent_kernel<NPOP>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    // persistent warps zero their own count arrays on entry
+    // shared memory as large as the resident CTAs need; the rest stays L1
+    e = cudaFuncSetAttribute(walk_persistent_kernel<NPOP>,
+                             cudaFuncAttributePreferredSharedMemoryCarveout, carveout_pct(smem, ctas));
+    if (e != cudaSuccess) return e;
     const int cap = schedule == SELSCAN_SCHED_LONGEST_FIRST ? probe : 0;
     walk_persistent_kernel<NPOP><<<ctas, wpc * 32, smem, s>>>(a, sk, sc, n_cores, 1, cap);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -429,11 +447,12 @@ __global__ void __launch_bounds__(192) ehh_trace_kernel(ScanArgs a, long long lo
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31;
     const int q = threadIdx.x >> 5;           // walk w = q / 2, direction q % 2
-    WarpBufs b = make_bufs(smem + (size_t)q * smem_per_warp(sc.cap_s, sc.gcap_s),
+    WarpBufs b = make_bufs(smem + (size_t)q * slice_bytes(sc),
                            sc.base + (size_t)q * sc.per_warp, sc);
-    zero_counts(b, sc, true);
+    init_window(b);
+    unsigned wpar[2] = {0u, 0u};
     const int w = q >> 1, dir = q & 1;
-    WalkOut o = walk<1>(a, locus, dir, w, b, S + (size_t)q * cap, cap, 0);
+    WalkOut o = walk<1>(a, locus, dir, w, b, S + (size_t)q * cap, cap, 0, wpar);
     if (lane == 0) {
         long long steps = 0;
         if (o.status == W_OK) steps = o.stop + 1;
@@ -445,9 +464,9 @@ __global__ void __launch_bounds__(192) ehh_trace_kernel(ScanArgs a, long long lo
     }
     if (q == 0 && lane == 0) {
         // denominators from the core row
-        const unsigned long long *row = a.hap + locus * a.ld;
+        const unsigned int *row = (const unsigned int *)(a.hap + locus * a.ld);
         unsigned long long c1 = 0;
-        for (int k = 0; k < a.W; ++k) c1 += (unsigned long long)__popcll(row[k] & valid_word(a, k));
+        for (int k = 0; k < 2 * a.W; ++k) c1 += (unsigned long long)__popc(row[k] & valid32(a, k));
         const unsigned long long n = (unsigned long long)a.nA;
         denom[0] = choose2(c1);
         denom[1] = choose2(n - c1);
@@ -459,7 +478,7 @@ cudaError_t launch_ehh(const ScanArgs &a, long long locus, const Scratch &sc,
                        unsigned long long *S, long long cap, long long *len, int32_t *stop,
                        int8_t *status, double *ihh, unsigned long long *denom, cudaStream_t s)
 {
-    const size_t smem = smem_per_warp(sc.cap_s, sc.gcap_s) * 6;
+    const size_t smem = slice_bytes(sc) * 6;
     cudaError_t e = cudaFuncSetAttribute(ehh_trace_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

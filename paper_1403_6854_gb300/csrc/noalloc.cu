@@ -9,15 +9,15 @@
 // synchronisation or failure modes of cudaMalloc are unacceptable.  The
 // paper has no counterpart: this is an interface convenience only.
 //
-// The array (about 1.4 MiB) is a module-scope __device__ variable, so every
+// The array (about 1.2 MiB) is a module-scope __device__ variable, so every
 // GPU that loads the library holds it until the process exits.  Host code
 // cannot use its name as a device address: the set-up below asks the
 // runtime for the address once per device (with that device current) and
 // passes it to the kernel.  The first call on each device performs that
 // set-up, so it should happen before any stream capture.  All calls share
-// the one array and it keeps the previous call's contents: the kernel
-// zeroes the parts that must start at zero, and calls that overlap on the
-// same GPU (for example on two streams) race on it, so the caller must
+// the one array and it keeps the previous call's contents: every walk
+// initialises each word before it reads it, so nothing there has to start
+// at zero; calls that overlap on the same GPU (for example on two streams) race on it, so the caller must
 // order them (each device has its own copy of the array).
 #include <mutex>
 
@@ -98,10 +98,14 @@ extern "C" int selscan_ehh_noalloc(const uint64_t *hap, int64_t ld, int32_t n, i
     Scratch sc;
     sc.base = (unsigned char *)base;
     sc.per_warp = scratch_per_warp(n);   // six slices of this size fit in the array
-    sc.cap = n;
-    sc.gcap = n / 2 + 1;
+    sc.cap = list_cap(n);
+    sc.tcap = table_cap(n);
     sc.cap_s = kSmemEntries;
-    sc.gcap_s = kSmemEntries / 2;
+    sc.tcap_s = kSmemEntries / 4;
+    sc.R = window_rows(ld);
+    sc.rowcap = win_rowcap(sc.R, ld);
+    sc.poscap = win_poscap(sc.R);
+    sc.err = out->error;
 
     cudaStream_t s = (cudaStream_t)stream;
     if (cudaMemsetAsync(out->error, 0, sizeof(int32_t), s) != cudaSuccess) return SELSCAN_ERR_CUDA;
