@@ -195,6 +195,49 @@ int selscan_ehh_noalloc(const uint64_t *hap, int64_t ld, int32_t n, int64_t m,
                         const selscan_params *p, const selscan_ehh_out *out, int64_t capacity,
                         void *stream);
 
+/* ---- batched scans (continuous batching) -------------------------------
+ * Several scans (iHS and XPEHH, any sizes) share one persistent walk launch
+ * ("tick"): the caller hands each tick core ranges from any admitted scans,
+ * and walks of different scans run side by side on the GPU.  Results are
+ * exactly those of selscan_ihs / selscan_xpehh on each scan alone.
+ * Life of a scan: selscan_batch_prepare (validate + core selection), one or
+ * more ticks covering every core [0, m) exactly once, selscan_batch_finalize.
+ * All buffers in selscan_scan are caller-owned device memory; ticks and the
+ * prepare/finalize calls of one scan must be ordered on one stream. */
+typedef struct {
+    int32_t mode;                 /* SELSCAN_MODE_IHS or SELSCAN_MODE_XPEHH */
+    int32_t nA, nB;               /* iHS: n, (ignored); XPEHH: n_A, n_B */
+    int64_t m, ld;
+    const uint64_t *hap;          /* rows as for selscan_ihs / selscan_xpehh */
+    const int64_t *pos_bp;
+    const double *gmap;
+    selscan_params params;
+    int8_t *status;               /* outputs: as selscan_ihs_out / selscan_xpehh_out */
+    int32_t *n1;
+    double *ihh_a;                /* iHH_1 (iHS) or iHH_A (XPEHH) */
+    double *ihh_b;                /* iHH_0 (iHS) or iHH_B (XPEHH) */
+    double *lnratio;
+    int32_t *stop;
+    uint64_t *digest;
+    int32_t *error;
+    void *items;                  /* per-walk results, selscan_batch_item_bytes(m, mode) bytes, 256-aligned */
+} selscan_scan;
+
+size_t selscan_batch_item_bytes(int64_t m, int32_t mode);
+/* Workspace of one tick for scans of at most max_n_total haplotypes and row
+ * stride max_ld, at most max_scans scans and max_units core ranges. */
+size_t selscan_batch_workspace_bytes(int32_t max_n_total, int64_t max_ld, int32_t max_scans,
+                                     int32_t max_units);
+int selscan_batch_prepare(const selscan_scan *scan, void *stream);
+/* One tick: core ranges [unit_c0[u], unit_c1[u]) of scans[unit_scan[u]]
+ * (host arrays; the scan array and unit arrays may be reused once the call
+ * returns).  max_n_total / max_ld bound the scans of this tick. */
+int selscan_batch_run(const selscan_scan *scans, int32_t nscans, const int32_t *unit_scan,
+                      const int64_t *unit_c0, const int64_t *unit_c1, int32_t nunits,
+                      int32_t max_n_total, int64_t max_ld, void *workspace, size_t ws_bytes,
+                      void *stream);
+int selscan_batch_finalize(const selscan_scan *scan, void *stream);
+
 /* Pack a 0/1 uint8 matrix into rows (Section 1.1 coding, 0 ancestral / 1
  * derived).  hap_major = 0: hap01 is [m][n] (marker-major); 1: [n][m].
  * Values other than 0/1 are read as (v & 1).  rows: [m][ld], pad bits and

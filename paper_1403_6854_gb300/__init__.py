@@ -63,8 +63,18 @@ class selscan_ehh_out(ctypes.Structure):
     _fields_ = [(f, _P) for f in ("S", "len", "stop", "status", "ihh", "denom", "error")]
 
 
+class selscan_scan(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("nA", ctypes.c_int32), ("nB", ctypes.c_int32),
+                ("m", ctypes.c_int64), ("ld", ctypes.c_int64), ("hap", _P), ("pos_bp", _P),
+                ("gmap", _P), ("params", selscan_params), ("status", _P), ("n1", _P),
+                ("ihh_a", _P), ("ihh_b", _P), ("lnratio", _P), ("stop", _P), ("digest", _P),
+                ("error", _P), ("items", _P)]
+
+
 EXPORTS = ("selscan_default_params", "selscan_workspace_bytes", "selscan_ihs", "selscan_xpehh",
-           "selscan_ehh", "selscan_ehh_noalloc", "selscan_pack", "selscan_strerror")
+           "selscan_ehh", "selscan_ehh_noalloc", "selscan_pack", "selscan_strerror",
+           "selscan_batch_item_bytes", "selscan_batch_workspace_bytes", "selscan_batch_prepare",
+           "selscan_batch_run", "selscan_batch_finalize")
 EHH_NOALLOC_MAX_N = 8192
 
 _lib = None
@@ -105,6 +115,19 @@ def load_library():
     lib.selscan_pack.restype = ctypes.c_int
     lib.selscan_pack.argtypes = [_P, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, _P,
                                  ctypes.c_int64, _P]
+    lib.selscan_batch_item_bytes.restype = ctypes.c_size_t
+    lib.selscan_batch_item_bytes.argtypes = [ctypes.c_int64, ctypes.c_int32]
+    lib.selscan_batch_workspace_bytes.restype = ctypes.c_size_t
+    lib.selscan_batch_workspace_bytes.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_int32,
+                                                  ctypes.c_int32]
+    lib.selscan_batch_prepare.restype = ctypes.c_int
+    lib.selscan_batch_prepare.argtypes = [ctypes.POINTER(selscan_scan), _P]
+    lib.selscan_batch_run.restype = ctypes.c_int
+    lib.selscan_batch_run.argtypes = [ctypes.POINTER(selscan_scan), ctypes.c_int32, _P, _P, _P,
+                                      ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, _P,
+                                      ctypes.c_size_t, _P]
+    lib.selscan_batch_finalize.restype = ctypes.c_int
+    lib.selscan_batch_finalize.argtypes = [ctypes.POINTER(selscan_scan), _P]
     lib.selscan_strerror.restype = ctypes.c_char_p
     lib.selscan_strerror.argtypes = [ctypes.c_int]
     _lib = lib
@@ -306,6 +329,43 @@ def selscan_pack(hap01: torch.Tensor, n: int, hap_major: bool = False, ld: Optio
     if rc != OK:
         raise SelscanError(rc, "selscan_pack")
     return rows
+
+
+def selscan_batch_item_bytes(m: int, mode: int) -> int:
+    return int(load_library().selscan_batch_item_bytes(m, mode))
+
+
+def selscan_batch_workspace_bytes(max_n_total: int, max_ld: int, max_scans: int,
+                                  max_units: int) -> int:
+    return int(load_library().selscan_batch_workspace_bytes(max_n_total, max_ld, max_scans,
+                                                            max_units))
+
+
+def selscan_batch_prepare(scan: selscan_scan, stream=None) -> None:
+    rc = load_library().selscan_batch_prepare(ctypes.byref(scan), _stream(stream))
+    if rc != OK:
+        raise SelscanError(rc, "selscan_batch_prepare")
+
+
+def selscan_batch_run(scans, unit_scan, unit_c0, unit_c1, max_n_total: int, max_ld: int,
+                      workspace: torch.Tensor, stream=None) -> None:
+    """One tick over core ranges of several scans (host-side arrays)."""
+    import numpy as np
+    arr = (selscan_scan * len(scans))(*scans)
+    us = np.ascontiguousarray(unit_scan, dtype=np.int32)
+    c0 = np.ascontiguousarray(unit_c0, dtype=np.int64)
+    c1 = np.ascontiguousarray(unit_c1, dtype=np.int64)
+    rc = load_library().selscan_batch_run(arr, len(scans), us.ctypes.data, c0.ctypes.data,
+                                          c1.ctypes.data, len(us), max_n_total, max_ld,
+                                          _ptr(workspace), workspace.numel(), _stream(stream))
+    if rc != OK:
+        raise SelscanError(rc, "selscan_batch_run")
+
+
+def selscan_batch_finalize(scan: selscan_scan, stream=None) -> None:
+    rc = load_library().selscan_batch_finalize(ctypes.byref(scan), _stream(stream))
+    if rc != OK:
+        raise SelscanError(rc, "selscan_batch_finalize")
 
 
 def check(out: Dict[str, torch.Tensor]) -> None:

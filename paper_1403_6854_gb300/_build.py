@@ -10,8 +10,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libselscan_gb300.so")
-SOURCES = ["api.cu", "kernels.cu", "noalloc.cu"]
-HEADERS = ["walk.cuh", "internal.h"]
+SOURCES = ["api.cu", "kernels.cu", "batch.cu", "noalloc.cu"]
+HEADERS = ["walk.cuh", "internal.h", "device_common.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 

@@ -1,0 +1,296 @@
+// Batched scans: several admitted scans (iHS and XPEHH, any sizes) share one
+// persistent walk launch ("tick").  The host hands each tick a list of core
+// ranges from any of the scans; warps pull ranges from one queue, so walks of
+// different scans run side by side on the GPU.  Used by the serving loop for
+// continuous batching; the statistics are exactly those of selscan_ihs /
+// selscan_xpehh (same walk code, same finalize).
+#include <string.h>
+
+#include "../../include/selscan.h"
+#include "device_common.cuh"
+#include "internal.h"
+
+namespace selscan {
+int device_sms();
+int max_ctas_per_sm(int schedule, int warps_per_cta, size_t smem_bytes);
+}
+
+using namespace selscan;
+
+namespace {
+
+constexpr int kBatchWarps = 8;
+constexpr int kBatchSmemEntries = 512;
+
+struct BatchDesc {
+    ScanArgs a;
+    ItemSink sk;
+    int R;          // window rows per buffer for this scan's row stride
+    int *err;
+};
+
+struct BatchUnit {
+    int scan;
+    int pad;
+    long long c0, c1;   // core range [c0, c1)
+};
+
+inline size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct BatchPlan {
+    int ctas, wpc, nslots;
+    Scratch sc;     // base filled at run time
+    size_t smem;
+};
+
+BatchPlan batch_plan(int max_n_total, long long max_ld)
+{
+    BatchPlan p;
+    p.wpc = kBatchWarps;
+    p.sc.cap = list_cap(max_n_total);
+    p.sc.tcap = table_cap(max_n_total);
+    p.sc.cap_s = kBatchSmemEntries;
+    p.sc.tcap_s = kBatchSmemEntries / 4;
+    p.sc.R = window_rows(max_ld);
+    p.sc.rowcap = win_rowcap(p.sc.R, max_ld);   // >= 2 rows of the widest scan
+    p.sc.poscap = win_poscap(64);               // narrower scans use up to 64 rows
+    p.sc.per_warp = scratch_per_warp(max_n_total);
+    p.sc.err = nullptr;
+    p.sc.base = nullptr;
+    p.smem = smem_per_warp(p.sc.cap_s, p.sc.tcap_s, p.sc.rowcap, p.sc.poscap) * (size_t)p.wpc;
+    int per_sm = max_ctas_per_sm(SELSCAN_SCHED_IN_ORDER, p.wpc, p.smem);
+    if (per_sm < 1) per_sm = 64 / p.wpc;
+    p.ctas = device_sms() * per_sm;
+    p.nslots = p.ctas * p.wpc;
+    return p;
+}
+
+struct BatchLayout {
+    size_t head, descs, units, scratch, total;
+};
+
+BatchLayout batch_layout(int max_scans, int max_units, int nslots, size_t per_warp)
+{
+    BatchLayout l;
+    size_t o = 0;
+    l.head = o;    o += 256;
+    l.descs = o;   o += up256((size_t)max_scans * sizeof(BatchDesc));
+    l.units = o;   o += up256((size_t)max_units * sizeof(BatchUnit));
+    l.scratch = o; o += (size_t)nslots * per_warp;
+    l.total = o;
+    return l;
+}
+
+size_t item_bytes_layout(long long m, int mode, size_t *off_ihh)
+{
+    const long long items = m * (mode == SELSCAN_MODE_XPEHH ? 2 : 4);
+    const size_t a = up256((size_t)items);
+    if (off_ihh) *off_ihh = a;
+    return a + up256((size_t)items * 8 * (mode == SELSCAN_MODE_XPEHH ? 2 : 1));
+}
+
+bool scan_ok(const selscan_scan *s)
+{
+    if (!s || !s->hap || !s->pos_bp || !s->gmap || !s->status || !s->n1 || !s->ihh_a || !s->ihh_b ||
+        !s->lnratio || !s->stop || !s->digest || !s->error || !s->items)
+        return false;
+    if (s->mode != SELSCAN_MODE_IHS && s->mode != SELSCAN_MODE_XPEHH) return false;
+    const int nB = s->mode == SELSCAN_MODE_XPEHH ? s->nB : 0;
+    if (s->nA < 2 || (s->mode == SELSCAN_MODE_XPEHH && s->nB < 2) || (long long)s->nA + nB > 65000)
+        return false;
+    if (s->m < 1 || s->m >= (1ll << 30) || s->ld < (s->nA + 63) / 64 + (nB + 63) / 64) return false;
+    const selscan_params *p = &s->params;
+    if (p->ehh_cut_den == 0 || p->maf_den == 0 || p->gap_scale_bp <= 0 || p->max_gap_bp < 0 ||
+        (p->include_crossing_term != 0 && p->include_crossing_term != 1))
+        return false;
+    return ((uintptr_t)s->items & 255) == 0;
+}
+
+BatchDesc make_desc(const selscan_scan *s)
+{
+    BatchDesc d;
+    const int nB = s->mode == SELSCAN_MODE_XPEHH ? s->nB : 0;
+    ScanArgs &a = d.a;
+    a.hap = (const unsigned long long *)s->hap;
+    a.ld = s->ld;
+    a.m = s->m;
+    a.pos = (const long long *)s->pos_bp;
+    a.gmap = s->gmap;
+    a.WA = (s->nA + 63) / 64;
+    a.W = a.WA + (nB + 63) / 64;
+    a.nA = s->nA;
+    a.nB = nB;
+    a.lastA = (s->nA % 64) ? ((1ull << (s->nA % 64)) - 1ull) : ~0ull;
+    a.lastB = nB > 0 ? ((nB % 64) ? ((1ull << (nB % 64)) - 1ull) : ~0ull) : ~0ull;
+    a.cut_num = s->params.ehh_cut_num;
+    a.cut_den = s->params.ehh_cut_den;
+    a.gap_scale = s->params.gap_scale_bp;
+    a.max_gap = s->params.max_gap_bp;
+    a.crossing = s->params.include_crossing_term;
+    size_t off_ihh = 0;
+    item_bytes_layout(s->m, s->mode, &off_ihh);
+    ItemSink &k = d.sk;
+    memset(&k, 0, sizeof(k));
+    k.mode = s->mode == SELSCAN_MODE_XPEHH ? 1 : 0;
+    k.core_status = s->status;
+    k.item_status = (int8_t *)s->items;
+    k.item_ihh = (double *)((unsigned char *)s->items + off_ihh);
+    k.stop = s->stop;
+    k.digest = (unsigned long long *)s->digest;
+    d.R = 2;
+    d.err = s->error;
+    return d;
+}
+
+}  // namespace
+
+namespace selscan {
+
+__global__ void __launch_bounds__(256, 2) walk_batch_kernel(const BatchDesc *descs,
+                                                            const BatchUnit *units, int nunits,
+                                                            Scratch sc, unsigned long long *head)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int wpc = blockDim.x >> 5;
+    const long long gw = (long long)blockIdx.x * wpc + warp;
+    WarpBufs b = make_bufs(smem + (size_t)warp * slice_bytes(sc),
+                           sc.base + (size_t)gw * sc.per_warp, sc);
+    init_window(b);
+    unsigned wpar[2] = {0u, 0u};
+    for (;;) {
+        unsigned long long idx = 0;
+        if (lane == 0) idx = atomicAdd(head, 1ull);
+        idx = __shfl_sync(FULLMASK, idx, 0);
+        if (idx >= (unsigned long long)nunits) break;
+        const BatchUnit u = units[idx];
+        const BatchDesc &d = descs[u.scan];
+        const ScanArgs a = d.a;
+        const ItemSink sk = d.sk;
+        b.R = d.R;
+        b.err = d.err;
+        for (long long c = u.c0; c < u.c1; ++c) {
+            if (sk.core_status[c] == (int8_t)SELSCAN_LOCUS_MAF_FILTERED) continue;
+            if (sk.mode == 1) {
+                for (int q = 0; q < 2; ++q) run_item<2>(a, sk, b, (uint32_t)(c * 2 + q), 0, wpar);
+            } else {
+                for (int q = 0; q < 4; ++q) run_item<1>(a, sk, b, (uint32_t)(c * 4 + q), 0, wpar);
+            }
+        }
+    }
+}
+
+}  // namespace selscan
+
+extern "C" {
+
+size_t selscan_batch_item_bytes(int64_t m, int32_t mode)
+{
+    if (m < 1 || (mode != SELSCAN_MODE_IHS && mode != SELSCAN_MODE_XPEHH)) return 0;
+    return item_bytes_layout(m, mode, nullptr);
+}
+
+size_t selscan_batch_workspace_bytes(int32_t max_n_total, int64_t max_ld, int32_t max_scans,
+                                     int32_t max_units)
+{
+    if (max_n_total < 2 || max_ld < 1 || max_scans < 1 || max_units < 1) return 0;
+    // slots for the most warps an SM can hold, independent of the launch shape
+    return batch_layout(max_scans, max_units, device_sms() * 64, scratch_per_warp(max_n_total)).total;
+}
+
+int selscan_batch_prepare(const selscan_scan *s, void *stream)
+{
+    if (!scan_ok(s)) return SELSCAN_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const BatchDesc d = make_desc(s);
+    size_t off_ihh = 0;
+    const size_t ib = item_bytes_layout(s->m, s->mode, &off_ihh);
+    if (cudaMemsetAsync(s->items, 0, ib, st) != cudaSuccess) return SELSCAN_ERR_CUDA;
+    if (cudaMemsetAsync(s->error, 0, sizeof(int32_t), st) != cudaSuccess) return SELSCAN_ERR_CUDA;
+    if (launch_validate((const long long *)s->pos_bp, s->gmap, s->m, s->error, st) != cudaSuccess)
+        return SELSCAN_ERR_CUDA;
+    if (launch_core_select(d.a, d.sk.mode, s->params.maf_num, s->params.maf_den,
+                           s->params.xpehh_maf_filter, s->n1, s->status, st) != cudaSuccess)
+        return SELSCAN_ERR_CUDA;
+    return SELSCAN_OK;
+}
+
+int selscan_batch_run(const selscan_scan *scans, int32_t nscans, const int32_t *unit_scan,
+                      const int64_t *unit_c0, const int64_t *unit_c1, int32_t nunits,
+                      int32_t max_n_total, int64_t max_ld, void *workspace, size_t ws_bytes,
+                      void *stream)
+{
+    if (!scans || nscans < 1 || !unit_scan || !unit_c0 || !unit_c1 || nunits < 0 || !workspace)
+        return SELSCAN_ERR_INVALID_ARG;
+    if (nunits == 0) return SELSCAN_OK;
+    BatchPlan plan = batch_plan(max_n_total, max_ld);
+    const BatchLayout l = batch_layout(nscans, nunits, plan.nslots, plan.sc.per_warp);
+    if (ws_bytes < l.total || ((uintptr_t)workspace & 255)) return SELSCAN_ERR_WORKSPACE;
+    BatchDesc *hd = new BatchDesc[nscans];
+    BatchUnit *hu = new BatchUnit[nunits];
+    int rc = SELSCAN_OK;
+    for (int i = 0; i < nscans && rc == SELSCAN_OK; ++i) {
+        const selscan_scan *s = scans + i;
+        const int nB = s->mode == SELSCAN_MODE_XPEHH ? s->nB : 0;
+        if (!scan_ok(s) || s->nA + nB > max_n_total || s->ld > max_ld) rc = SELSCAN_ERR_INVALID_ARG;
+        else {
+            hd[i] = make_desc(s);
+            int R = (plan.sc.rowcap - 16) / (int)(s->ld * 8);
+            hd[i].R = R < 2 ? 2 : (R > 64 ? 64 : R);
+        }
+    }
+    for (int u = 0; u < nunits && rc == SELSCAN_OK; ++u) {
+        const int si = unit_scan[u];
+        if (si < 0 || si >= nscans || unit_c0[u] < 0 || unit_c1[u] < unit_c0[u] || unit_c1[u] > scans[si].m)
+            rc = SELSCAN_ERR_INVALID_ARG;
+        hu[u].scan = si;
+        hu[u].pad = 0;
+        hu[u].c0 = unit_c0[u];
+        hu[u].c1 = unit_c1[u];
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned char *ws = (unsigned char *)workspace;
+    if (rc == SELSCAN_OK) {
+        plan.sc.base = ws + l.scratch;
+        if (cudaMemsetAsync(ws + l.head, 0, 256, st) != cudaSuccess ||
+            cudaMemcpyAsync(ws + l.descs, hd, sizeof(BatchDesc) * (size_t)nscans,
+                            cudaMemcpyHostToDevice, st) != cudaSuccess ||
+            cudaMemcpyAsync(ws + l.units, hu, sizeof(BatchUnit) * (size_t)nunits,
+                            cudaMemcpyHostToDevice, st) != cudaSuccess)
+            rc = SELSCAN_ERR_CUDA;
+    }
+    if (rc == SELSCAN_OK) {
+        if (cudaFuncSetAttribute(walk_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)plan.smem) != cudaSuccess ||
+            cudaFuncSetAttribute(walk_batch_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 100) != cudaSuccess)
+            rc = SELSCAN_ERR_CUDA;
+    }
+    if (rc == SELSCAN_OK) {
+        walk_batch_kernel<<<plan.ctas, plan.wpc * 32, plan.smem, st>>>(
+            (const BatchDesc *)(ws + l.descs), (const BatchUnit *)(ws + l.units), nunits, plan.sc,
+            (unsigned long long *)(ws + l.head));
+        if (cudaGetLastError() != cudaSuccess) rc = SELSCAN_ERR_CUDA;
+    }
+    // the pageable copies above are complete when cudaMemcpyAsync returns
+    delete[] hd;
+    delete[] hu;
+    return rc;
+}
+
+int selscan_batch_finalize(const selscan_scan *s, void *stream)
+{
+    if (!scan_ok(s)) return SELSCAN_ERR_INVALID_ARG;
+    const BatchDesc d = make_desc(s);
+    cudaError_t e;
+    if (s->mode == SELSCAN_MODE_XPEHH)
+        e = launch_finalize_xpehh(d.sk, s->m, s->ihh_a, s->ihh_b, s->lnratio, s->status,
+                                  (cudaStream_t)stream);
+    else
+        e = launch_finalize_ihs(d.sk, s->m, s->ihh_a, s->ihh_b, s->lnratio, s->status,
+                                (cudaStream_t)stream);
+    return e == cudaSuccess ? SELSCAN_OK : SELSCAN_ERR_CUDA;
+}
+
+}  // extern "C"
