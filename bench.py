@@ -179,7 +179,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="ihs1m", choices=list(WORKLOADS))
-    ap.add_argument("--schedule", type=int, default=1)
+    ap.add_argument("--schedule", type=int, default=-1,
+                    help="-1: autotuned launch shape; 0/1/2: fixed schedule with defaults")
+    ap.add_argument("--tune-cache", action="store_true")
+    ap.add_argument("--served", type=int, default=200, help="requests in the served mix (0: skip)")
+    ap.add_argument("--load", type=float, default=0.7, help="served arrival rate / capacity")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--ref-budget", type=float, default=15.0)
@@ -213,6 +217,17 @@ def main():
     hap, pos, gmap = sg.to_device(d.rows, d.pos, d.gmap, dev)
     params = sg.selscan_default_params()
     K, Wm = args.steps, args.warmup
+    from paper_1403_6854_gb300.tune import Autotuner
+    if args.schedule >= 0:
+        launch_fields, shape = dict(schedule=args.schedule), {"schedule": args.schedule,
+                                                              "source": "--schedule"}
+    else:
+        tuner = Autotuner(cache_path=os.path.join(ROOT, "_build_tune.json") if args.tune_cache else None)
+        _, shape = tuner.launch_for(hap, pos, gmap, "ihs", n)
+        launch_fields = {f: shape.get(f, 0) for f in ("schedule", "warps_per_cta", "smem_entries",
+                                                     "window_rows", "cores_per_fetch",
+                                                     "probe_steps")}
+        shape = dict(shape, source="autotuner on the first 65,536 markers")
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(K)]
     for a, b in ev:                      # create the events before handing them out
@@ -222,14 +237,14 @@ def main():
     out = None
     for _ in range(Wm):
         out = sg.selscan_ihs(hap, n, pos, gmap, params=params,
-                             launch=sg.make_launch(args.schedule), workspace=ws, out=out)
+                             launch=sg.make_launch(**launch_fields), workspace=ws, out=out)
         ws = out["_workspace"]
     torch.cuda.synchronize()
     sg.check(out)
 
     gpu_id = str(torch.cuda.get_device_properties(dev).uuid)
     gpu_id = gpu_id if gpu_id.startswith("GPU-") else "GPU-" + gpu_id
-    launches_per_step = {0: 8, 1: 5, 2: 5}[args.schedule]
+    launches_per_step = {0: 8, 1: 4, 2: 4}[launch_fields.get("schedule", 1)]
     with ClockSampler(gpu_id) as clk:
         if world > 1:
             dist.barrier()
@@ -239,7 +254,7 @@ def main():
         t0.record()
         for k in range(K):
             out = sg.selscan_ihs(hap, n, pos, gmap, params=params,
-                                 launch=sg.make_launch(args.schedule, events=ev[k]),
+                                 launch=sg.make_launch(events=ev[k], **launch_fields),
                                  workspace=ws, out=out)
         t1.record()
         torch.cuda.synchronize()
@@ -296,6 +311,9 @@ def main():
     if rank == 0 and world == 1 and not args.no_extras:
         extras = run_extras(sg, torch, synth, d, hap, pos, gmap, n, ws)
 
+    if rank == 0 and world == 1 and args.served > 0 and not args.no_extras:
+        extras["served"] = run_served(args, torch, synth)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(d)
@@ -312,7 +330,8 @@ def main():
             "config": {"workload": WORKLOADS[args.workload], "n_haplotypes": n, "n_snps": spec.m,
                        "core_loci_per_gpu": cores, "walk_steps_per_scan": steps_total,
                        "schedule": ["persistent longest-first", "persistent in-order",
-                                    "plain one-CTA-per-core"][args.schedule],
+                                    "plain one-CTA-per-core"][launch_fields.get("schedule", 1)],
+                       "launch_shape": shape,
                        "l2": "inputs larger than L2 (packed matrix 632 MB), no flush",
                        "parallelism": f"weak: one chromosome (seed = rank) per GPU x{world}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
@@ -363,6 +382,44 @@ def run_extras(sg, torch, synth, d, hap, pos, gmap, n, ws):
     ex["xpehh"] = {"workload": "XPEHH: pop A 204 / pop B 210 haplotypes x 22,147 SNPs",
                    "value": x.spec.m / (ms / 1e3), "unit": "core loci/s", "ms_per_scan": ms}
     return ex
+
+
+def run_served(args, torch, synth):
+    """Served mix: Poisson arrivals at `load` x the server's measured capacity;
+    continuous batching vs one plain launch per scan, same arrivals."""
+    from paper_1403_6854_gb300.serve import GpuExecutor, Request, run_plain, serve, summarize
+    t_gen = time.perf_counter()
+    reqs = []
+    for i in range(args.served):
+        sp = synth.served_request(i)
+        d = synth.generate(sp)
+        reqs.append(Request(i, sp.mode, d.rows, d.pos, d.gmap, sp.pops[0].n,
+                            sp.pops[1].n if sp.mode == "xpehh" else 0))
+    t_gen = time.perf_counter() - t_gen
+    total_cores = sum(r.m for r in reqs)
+    free, _ = torch.cuda.mem_get_info()
+    budget = int(min(0.5 * free, 64 << 30))
+    ex = GpuExecutor()
+    # capacity: the whole mix with every request present at t = 0
+    serve(reqs[:8], ex, budget, realtime=False)              # warm-up
+    _, _, mk = serve(reqs, ex, budget, realtime=False)
+    capacity = total_cores / mk                              # markers per second
+    rate = args.load * capacity / (total_cores / len(reqs))  # requests per second
+    rng = np.random.Generator(np.random.PCG64(2024))
+    t = np.cumsum(rng.exponential(1.0 / rate, size=len(reqs)))
+    for r, a in zip(reqs, t):
+        r.arrival = float(a)
+    _, lat_s, mk_s = serve(reqs, ex, budget)
+    _, lat_p, mk_p = run_plain(reqs)
+    return {"requests": len(reqs), "mix": "70% iHS / 30% XPEHH, haplotypes log-U(100, 5000), "
+                                          "SNPs log-U(10k, 500k), seed 1000 + i",
+            "arrival_rate_per_s": rate, "load": args.load,
+            "capacity_markers_per_s": capacity, "hbm_budget_bytes": budget,
+            "generation_s": t_gen,
+            "continuous_batching": summarize(lat_s, total_cores, mk_s),
+            "plain_launches": summarize(lat_p, total_cores, mk_p),
+            "note": "latency = results on host - arrival; core_loci_per_s counts every marker "
+                    "(MAF-filtered cores included) over the makespan"}
 
 
 if __name__ == "__main__":

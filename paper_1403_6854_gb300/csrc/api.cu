@@ -28,6 +28,7 @@ struct Plan {
     int cap_s, tcap_s;
     int probe;
     int R, rowcap, poscap;
+    int fetch;
 };
 
 inline size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -48,7 +49,9 @@ Plan make_plan(int mode, long long ld, const selscan_launch *L)
     p.cap_s = (p.cap_s + 31) & ~31;
     p.tcap_s = ((p.cap_s / 4) + 31) & ~31;
     p.probe = (L && L->probe_steps > 0) ? L->probe_steps : kDefaultProbeSteps;
-    p.R = window_rows(ld);
+    p.R = (L && L->window_rows > 0) ? (L->window_rows < 2 ? 2 : (L->window_rows > 64 ? 64 : L->window_rows))
+                                     : window_rows(ld);
+    p.fetch = (L && L->cores_per_fetch > 0) ? (L->cores_per_fetch > 1024 ? 1024 : L->cores_per_fetch) : 1;
     p.rowcap = win_rowcap(p.R, ld);
     p.poscap = win_poscap(p.R);
     const int sms = device_sms();
@@ -193,7 +196,8 @@ int run_scan(int mode, const uint64_t *hap, int64_t ld, int32_t nA, int32_t nB, 
     if (launch && launch->walk_begin_event &&
         cudaEventRecord((cudaEvent_t)launch->walk_begin_event, s) != cudaSuccess)
         return SELSCAN_ERR_CUDA;
-    if (launch_walk(a, sk, sc, plan.schedule, plan.wpc, ctas_or_slots, plan.probe, m, s) != cudaSuccess)
+    if (launch_walk(a, sk, sc, plan.schedule, plan.wpc, ctas_or_slots, plan.probe, plan.fetch, m, s) !=
+        cudaSuccess)
         return SELSCAN_ERR_CUDA;
     if (launch && launch->walk_end_event &&
         cudaEventRecord((cudaEvent_t)launch->walk_end_event, s) != cudaSuccess)

@@ -82,7 +82,7 @@ cudaError_t launch_validate(const long long *pos, const double *gmap, long long 
 cudaError_t launch_core_select(const ScanArgs &a, int mode, unsigned maf_num, unsigned maf_den,
                                int maf_filter, int32_t *n1, int8_t *core_status, cudaStream_t s);
 cudaError_t launch_walk(const ScanArgs &a, const ItemSink &sink, const Scratch &sc,
-                        int schedule, int warps_per_cta, int ctas, int probe_steps,
+                        int schedule, int warps_per_cta, int ctas, int probe_steps, int fetch,
                         long long n_items, cudaStream_t s);
 cudaError_t launch_finalize_ihs(const ItemSink &sink, long long m, double *ihh1, double *ihh0,
                                 double *lnratio, int8_t *status, cudaStream_t s);

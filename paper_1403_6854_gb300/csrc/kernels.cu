@@ -77,7 +77,7 @@ cudaError_t launch_core_select(const ScanArgs &a, int mode, unsigned maf_num, un
 template <int NPOP>
 __global__ void __launch_bounds__(256, 2) walk_persistent_kernel(ScanArgs a, ItemSink sk, Scratch sc,
                                                               long long n_cores, int pass,
-                                                              int max_steps)
+                                                              int max_steps, int fetch)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31;
@@ -90,17 +90,21 @@ __global__ void __launch_bounds__(256, 2) walk_persistent_kernel(ScanArgs a, Ite
     unsigned wpar[2] = {0u, 0u};
     const int ipc = NPOP == 2 ? 2 : 4;
     const unsigned long long total = pass == 2 ? sk.q->n2 : (unsigned long long)n_cores;
+    const unsigned long long step = pass == 2 ? 1ull : (unsigned long long)fetch;
     for (;;) {
         unsigned long long idx = 0;
-        if (lane == 0) idx = atomicAdd(&sk.q->head, 1ull);
+        if (lane == 0) idx = atomicAdd(&sk.q->head, step);
         idx = __shfl_sync(FULLMASK, idx, 0);
         if (idx >= total) break;
         if (pass == 2) {
             run_item<NPOP>(a, sk, b, sk.sorted2[idx], 0, wpar);
-        } else {
-            if (sk.core_status[idx] == (int8_t)SELSCAN_LOCUS_MAF_FILTERED) continue;
+            continue;
+        }
+        const unsigned long long end = idx + step < total ? idx + step : total;
+        for (unsigned long long c = idx; c < end; ++c) {
+            if (sk.core_status[c] == (int8_t)SELSCAN_LOCUS_MAF_FILTERED) continue;
             for (int q = 0; q < ipc; ++q)
-                run_item<NPOP>(a, sk, b, (uint32_t)(idx * ipc + q), max_steps, wpar);
+                run_item<NPOP>(a, sk, b, (uint32_t)(c * ipc + q), max_steps, wpar);
         }
     }
 }
@@ -236,8 +240,8 @@ static int carveout_pct(size_t smem_per_cta, int ctas)
 
 template <int NPOP>
 static cudaError_t walk_impl(const ScanArgs &a, const ItemSink &sk, const Scratch &sc,
-                             int schedule, int wpc, int ctas, int probe, long long n_cores,
-                             cudaStream_t s)
+                             int schedule, int wpc, int ctas, int probe, int fetch,
+                             long long n_cores, cudaStream_t s)
 {
     const size_t smem = slice_bytes(sc) * (size_t)wpc;
     cudaError_t e;
@@ -260,24 +264,25 @@ static cudaError_t walk_impl(const ScanArgs &a, const ItemSink &sk, const Scratc
                              cudaFuncAttributePreferredSharedMemoryCarveout, carveout_pct(smem, ctas));
     if (e != cudaSuccess) return e;
     const int cap = schedule == SELSCAN_SCHED_LONGEST_FIRST ? probe : 0;
-    walk_persistent_kernel<NPOP><<<ctas, wpc * 32, smem, s>>>(a, sk, sc, n_cores, 1, cap);
+    walk_persistent_kernel<NPOP><<<ctas, wpc * 32, smem, s>>>(a, sk, sc, n_cores, 1, cap,
+                                                               cap > 0 ? 1 : fetch);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (schedule == SELSCAN_SCHED_LONGEST_FIRST && probe > 0) {
         bucket_hist_kernel<<<2 * sm_count(), 256, 0, s>>>(sk);
         bucket_scan_kernel<<<1, NBUCKET, 0, s>>>(sk);
         bucket_scatter_kernel<<<2 * sm_count(), 256, 0, s>>>(sk);
-        walk_persistent_kernel<NPOP><<<ctas, wpc * 32, smem, s>>>(a, sk, sc, n_cores, 2, 0);
+        walk_persistent_kernel<NPOP><<<ctas, wpc * 32, smem, s>>>(a, sk, sc, n_cores, 2, 0, 1);
     }
     return cudaGetLastError();
 }
 
 cudaError_t launch_walk(const ScanArgs &a, const ItemSink &sink, const Scratch &sc,
-                        int schedule, int warps_per_cta, int ctas, int probe_steps,
+                        int schedule, int warps_per_cta, int ctas, int probe_steps, int fetch,
                         long long n_cores, cudaStream_t s)
 {
     if (sink.mode == 1)
-        return walk_impl<2>(a, sink, sc, schedule, warps_per_cta, ctas, probe_steps, n_cores, s);
-    return walk_impl<1>(a, sink, sc, schedule, warps_per_cta, ctas, probe_steps, n_cores, s);
+        return walk_impl<2>(a, sink, sc, schedule, warps_per_cta, ctas, probe_steps, fetch, n_cores, s);
+    return walk_impl<1>(a, sink, sc, schedule, warps_per_cta, ctas, probe_steps, fetch, n_cores, s);
 }
 
 // ------------------------------------------------------------ finalize

@@ -73,7 +73,7 @@ class Active:
 class Scheduler:
     """Admission by HBM footprint (FIFO) and round-robin tick composition."""
 
-    def __init__(self, hbm_budget: int, tick_cores: int = 65536, unit_cores: int = 256,
+    def __init__(self, hbm_budget: int, tick_cores: int = 32768, unit_cores: int = 4,
                  max_active: int = 64):
         self.budget = int(hbm_budget)
         self.tick_cores = int(tick_cores)
@@ -102,32 +102,32 @@ class Scheduler:
             new.append(a)
         return new
 
-    def compose_tick(self) -> Tuple[List[Active], List[Tuple[int, int, int]]]:
-        """Core ranges for the next tick: equal quanta from every resident scan
-        (round-robin), units of unit_cores cores.  Returns the scans of the
-        tick and units (index into that list, c0, c1)."""
-        live = [a for a in self.active if a.remaining > 0]
+    def compose_tick(self) -> Tuple[List[Active], np.ndarray]:
+        """Core ranges for the next tick.  The tick's core budget goes to the
+        resident scans with the least remaining work first (shortest remaining
+        work first: a small request finishes within a tick or two of its
+        admission), split into units of unit_cores cores that are interleaved
+        across scans.  Returns the tick's scans and an int64 array of units
+        (index into that list, c0, c1)."""
+        live = sorted((a for a in self.active if a.remaining > 0), key=lambda a: a.remaining)
         if not live:
-            return [], []
-        quantum = max(self.unit_cores, self.tick_cores // len(live))
-        per_scan = []
+            return [], np.zeros((0, 3), np.int64)
+        budget = self.tick_cores
+        parts = []
         for i, a in enumerate(live):
-            take = min(quantum, a.remaining)
-            c = a.next_core
-            end = c + take
-            lst = []
-            while c < end:
-                lst.append((i, c, min(c + self.unit_cores, end)))
-                c = min(c + self.unit_cores, end)
-            a.next_core = end
-            per_scan.append(lst)
-        # interleave the scans' ranges so that every scan starts early in the tick
-        units = []
-        for k in range(max(len(x) for x in per_scan)):
-            for lst in per_scan:
-                if k < len(lst):
-                    units.append(lst[k])
-        return live, units
+            if budget <= 0:
+                live = live[:i]
+                break
+            take = min(budget, a.remaining)
+            c0 = np.arange(a.next_core, a.next_core + take, self.unit_cores, dtype=np.int64)
+            c1 = np.minimum(c0 + self.unit_cores, a.next_core + take)
+            k = np.arange(c0.size, dtype=np.int64)
+            parts.append(np.stack([k, np.full(c0.size, i, np.int64), c0, c1], 1))
+            a.next_core += take
+            budget -= take
+        u = np.concatenate(parts)
+        u = u[np.lexsort((u[:, 1], u[:, 0]))]      # interleave: unit k of every scan, then k + 1
+        return live, u[:, 1:]
 
     def finished(self) -> List[Active]:
         done = [a for a in self.active if a.remaining == 0]
@@ -146,16 +146,21 @@ def summarize(latencies: Dict[int, float], cores: int, makespan: float) -> Dict:
 
 
 class GpuExecutor:
-    """Runs the scheduler's ticks on the GPU through the batch C ABI."""
+    """Runs the scheduler's ticks on the GPU through the batch C ABI.  Ticks
+    alternate between two streams so that one tick's tail overlaps the next
+    tick's start; a scan is finalised after every tick that touched it."""
 
-    def __init__(self, device="cuda", stream=None):
+    def __init__(self, device="cuda"):
         import torch
         import paper_1403_6854_gb300 as sg
         self.torch, self.sg = torch, sg
         self.device = torch.device(device)
-        self.stream = stream
-        self.ws = None
-        self.ws_key = None
+        self.streams = [torch.cuda.Stream(self.device), torch.cuda.Stream(self.device)]
+        self.events = [None, None]
+        self.ws = [None, None]
+        self._ws_raw = [None, None]
+        self.k = 0
+        self.last_tick = {}
 
     def upload(self, req: Request):
         torch, sg = self.torch, self.sg
@@ -164,19 +169,21 @@ class GpuExecutor:
         m = req.m
         ipc = 4 if req.mode == "ihs" else 2
         ndig = 4 if req.mode == "ihs" else 6
-        t = dict(hap=torch.from_numpy(np.ascontiguousarray(req.rows).view(np.int64)).to(dev, non_blocking=True),
-                 pos=torch.from_numpy(np.ascontiguousarray(req.pos)).to(dev, non_blocking=True),
-                 gmap=torch.from_numpy(np.ascontiguousarray(req.gmap)).to(dev, non_blocking=True),
-                 status=torch.empty(m, dtype=torch.int8, device=dev),
-                 n1=torch.empty(m, dtype=torch.int32, device=dev),
-                 ihh_a=torch.empty(m, dtype=torch.float64, device=dev),
-                 ihh_b=torch.empty(m, dtype=torch.float64, device=dev),
-                 lnratio=torch.empty(m, dtype=torch.float64, device=dev),
-                 stop=torch.empty((m, ipc), dtype=torch.int32, device=dev),
-                 digest=torch.empty((m, ndig), dtype=torch.int64, device=dev),
-                 error=torch.zeros(1, dtype=torch.int32, device=dev))
-        nb = sg.selscan_batch_item_bytes(m, mode)
-        raw = torch.empty(nb + 256, dtype=torch.uint8, device=dev)
+        st = self.streams[self.k % 2]
+        with torch.cuda.stream(st):
+            t = dict(hap=torch.from_numpy(np.ascontiguousarray(req.rows).view(np.int64)).to(dev),
+                     pos=torch.from_numpy(np.ascontiguousarray(req.pos)).to(dev),
+                     gmap=torch.from_numpy(np.ascontiguousarray(req.gmap)).to(dev),
+                     status=torch.empty(m, dtype=torch.int8, device=dev),
+                     n1=torch.empty(m, dtype=torch.int32, device=dev),
+                     ihh_a=torch.empty(m, dtype=torch.float64, device=dev),
+                     ihh_b=torch.empty(m, dtype=torch.float64, device=dev),
+                     lnratio=torch.empty(m, dtype=torch.float64, device=dev),
+                     stop=torch.empty((m, ipc), dtype=torch.int32, device=dev),
+                     digest=torch.empty((m, ndig), dtype=torch.int64, device=dev),
+                     error=torch.zeros(1, dtype=torch.int32, device=dev))
+            nb = sg.selscan_batch_item_bytes(m, mode)
+            raw = torch.empty(nb + 256, dtype=torch.uint8, device=dev)
         off = (-raw.data_ptr()) % 256
         t["items"] = raw[off:off + nb]
         t["_raw"] = raw
@@ -187,38 +194,56 @@ class GpuExecutor:
         s.hap, s.pos_bp, s.gmap = t["hap"].data_ptr(), t["pos"].data_ptr(), t["gmap"].data_ptr()
         for f in ("status", "n1", "ihh_a", "ihh_b", "lnratio", "stop", "digest", "error", "items"):
             setattr(s, f, t[f].data_ptr())
-        sg.selscan_batch_prepare(s, self.stream)
+        sg.selscan_batch_prepare(s, st)
+        # both streams must see the prepared scan before any tick uses it
+        ev = torch.cuda.Event()
+        ev.record(st)
+        self.streams[(self.k + 1) % 2].wait_event(ev)
         return (s, t)
 
     def run_tick(self, live: List[Active], units) -> None:
         sg, torch = self.sg, self.torch
+        i = self.k % 2
+        st = self.streams[i]
         scans = [a.handle[0] for a in live]
         max_n = max(a.req.n_total for a in live)
         max_ld = max(a.req.ld for a in live)
         need = sg.selscan_batch_workspace_bytes(max_n, max_ld, len(scans), max(1, len(units)))
-        if self.ws is None or self.ws.numel() < need:
-            raw = torch.empty(need + 256, dtype=torch.uint8, device=self.device)
+        if self.ws[i] is None or self.ws[i].numel() < need:
+            with torch.cuda.stream(st):
+                raw = torch.empty(need + 256, dtype=torch.uint8, device=self.device)
             off = (-raw.data_ptr()) % 256
-            self.ws = raw[off:off + need]
-            self._ws_raw = raw
-        us = [u[0] for u in units]
-        c0 = [u[1] for u in units]
-        c1 = [u[2] for u in units]
-        sg.selscan_batch_run(scans, us, c0, c1, max_n, max_ld, self.ws, self.stream)
+            self.ws[i] = raw[off:off + need]
+            self._ws_raw[i] = raw
+        sg.selscan_batch_run(scans, units[:, 0], units[:, 1], units[:, 2], max_n, max_ld,
+                             self.ws[i], st)
+        ev = torch.cuda.Event()
+        ev.record(st)
+        self.events[i] = ev
+        for a in live:
+            self.last_tick[a.req.rid] = self.k
+        self.k += 1
 
     def finish(self, a: Active) -> Dict[str, np.ndarray]:
+        torch = self.torch
         s, t = a.handle
-        self.sg.selscan_batch_finalize(s, self.stream)
+        st = self.streams[self.last_tick.get(a.req.rid, self.k) % 2]
+        other = self.events[(self.last_tick.get(a.req.rid, self.k) + 1) % 2]
+        if other is not None:
+            st.wait_event(other)
+        self.sg.selscan_batch_finalize(s, st)
+        st.synchronize()
         out = {f: t[f].cpu().numpy() for f in ("status", "n1", "ihh_a", "ihh_b", "lnratio", "stop",
                                                "digest", "error")}
         out["digest"] = out["digest"].view(np.uint64)
         if int(out["error"][0]) != 0:
             raise self.sg.SelscanError(int(out["error"][0]), f"request {a.req.rid}")
+        self.last_tick.pop(a.req.rid, None)
         return out
 
 
-def serve(requests: List[Request], executor, hbm_budget: int, tick_cores: int = 65536,
-          unit_cores: int = 256, clock: Callable[[], float] = time.perf_counter,
+def serve(requests: List[Request], executor, hbm_budget: int, tick_cores: int = 32768,
+          unit_cores: int = 4, clock: Callable[[], float] = time.perf_counter,
           realtime: bool = True) -> Tuple[Dict[int, Dict], Dict[int, float], float]:
     """Serve requests (sorted by arrival).  Returns results, latencies, makespan."""
     sch = Scheduler(hbm_budget, tick_cores, unit_cores)
@@ -232,13 +257,13 @@ def serve(requests: List[Request], executor, hbm_budget: int, tick_cores: int = 
         for a in sch.admit():
             a.handle = executor.upload(a.req)
         live, units = sch.compose_tick()
-        if units:
+        if len(units):
             executor.run_tick(live, units)
         for a in sch.finished():
             results[a.req.rid] = executor.finish(a)
             latency[a.req.rid] = (clock() - t0) - a.req.arrival
             sch.release(a)
-        if not units and not sch.finished() and pending and realtime:
+        if not len(units) and not sch.finished() and pending and realtime:
             wait = pending[0].arrival - (clock() - t0)
             if wait > 0:
                 time.sleep(min(wait, 0.05))

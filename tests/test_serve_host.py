@@ -31,7 +31,7 @@ def test_oversized_request_rejected():
         Scheduler(hbm_budget=100).submit(req(0))
 
 
-def test_ticks_cover_every_core_once_round_robin():
+def test_ticks_cover_every_core_once_smallest_first():
     sch = Scheduler(hbm_budget=1 << 40, tick_cores=1000, unit_cores=64)
     rs = [req(i, m=m) for i, m in enumerate((700, 2500, 90))]
     for r in rs:
@@ -41,16 +41,17 @@ def test_ticks_cover_every_core_once_round_robin():
     ticks = 0
     while True:
         live, units = sch.compose_tick()
-        if not units:
+        if not len(units):
             break
         ticks += 1
         per = {}
-        for i, c0, c1 in units:
+        for i, c0, c1 in units.tolist():
             assert 0 <= c0 < c1 <= live[i].req.m and c1 - c0 <= 64
             seen[live[i].req.rid][c0:c1] += 1
             per[i] = per.get(i, 0) + c1 - c0
-        # equal quanta (up to what a scan has left)
-        assert max(per.values()) <= max(64, 1000 // len(live))
+        # the tick budget is respected and the smallest remaining scan comes first
+        assert sum(per.values()) <= 1000
+        assert live == sorted(live, key=lambda a: a.remaining + per.get(live.index(a), 0))
         for a in sch.finished():
             sch.release(a)
     assert all((v == 1).all() for v in seen.values())
@@ -65,9 +66,9 @@ class FakeExecutor:
         return {"cores": np.zeros(r.m, int)}
 
     def run_tick(self, live, units):
-        self.ticks.append(len({live[u[0]].req.rid for u in units}))
+        self.ticks.append(len({live[int(u[0])].req.rid for u in units}))
         for i, c0, c1 in units:
-            live[i].handle["cores"][c0:c1] += 1
+            live[int(i)].handle["cores"][c0:c1] += 1
 
     def finish(self, a):
         return a.handle["cores"].copy()
