@@ -148,6 +148,26 @@ def cpu_baseline(data, budget_s=20.0, seed=1234):
                       f"costs the string-enumeration oracle minutes"}
 
 
+def rank_spec(workload: str, rank: int):
+    """Weak scaling: rank r scans its own chromosome (seed r) of the same shape."""
+    import synth
+    return synth.spec(workload, seed=rank)
+
+
+def aggregate(ms: float, cores: int, world: int, device):
+    """Whole-job numbers: the slowest rank's time and the core loci of all ranks
+    (one all-reduce of two scalars; nothing on the data path is exchanged)."""
+    if world <= 1:
+        return ms, float(cores)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms, float(cores)], dtype=torch.float64, device=device)
+    a, b = t[:1].clone(), t[1:].clone()
+    dist.all_reduce(a, op=dist.ReduceOp.MAX)
+    dist.all_reduce(b, op=dist.ReduceOp.SUM)
+    return float(a[0]), float(b[0])
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -209,8 +229,7 @@ def main():
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
 
-    # weak scaling: rank r scans its own chromosome (seed r) of the same shape
-    spec = synth.spec(args.workload, seed=rank)
+    spec = rank_spec(args.workload, rank)
     d = synth.generate(spec)
     n = spec.pops[0].n
     W = spec.W
@@ -224,9 +243,8 @@ def main():
     else:
         tuner = Autotuner(cache_path=os.path.join(ROOT, "_build_tune.json") if args.tune_cache else None)
         _, shape = tuner.launch_for(hap, pos, gmap, "ihs", n)
-        launch_fields = {f: shape.get(f, 0) for f in ("schedule", "warps_per_cta", "smem_entries",
-                                                     "window_rows", "cores_per_fetch",
-                                                     "probe_steps")}
+        from paper_1403_6854_gb300.tune import SHAPE_FIELDS
+        launch_fields = {f: shape.get(f, 0) for f in SHAPE_FIELDS}
         shape = dict(shape, source="autotuner on the first 65,536 markers")
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(K)]
@@ -271,14 +289,7 @@ def main():
     steps_total = int(lens.sum())
     walk_bytes = steps_total * 8 * W + int(np.maximum(lens - 1, 0).sum()) * 16
 
-    t = torch.tensor([ms, float(cores)], dtype=torch.float64, device=dev)
-    if world > 1:
-        tm = t.clone()
-        dist.all_reduce(tm[:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(tm[1:], op=dist.ReduceOp.SUM)
-        ms_max, cores_all = float(tm[0]), float(tm[1])
-    else:
-        ms_max, cores_all = ms, float(cores)
+    ms_max, cores_all = aggregate(ms, cores, world, dev)
     value = cores_all * K / (ms_max / 1e3)
 
     # end to end: host buffers, H2D of the inputs and D2H of the scores every step

@@ -102,7 +102,7 @@ typedef struct {
     int32_t probe_steps;    /* first-pass step cap of the longest-first schedule (0 = default) */
     int32_t window_rows;    /* rows per TMA window buffer, 2..64 (0 = about 1 KB of rows) */
     int32_t cores_per_fetch;/* cores a warp takes per queue fetch, in-order schedule (0 = 1) */
-    int32_t reserved;
+    int32_t min_ctas_per_sm;/* persistent build: 2 (default, 128 registers) or 3 (85 registers) */
     void *walk_begin_event; /* optional cudaEvent_t, recorded on the stream before the first walk kernel */
     void *walk_end_event;   /* optional cudaEvent_t, recorded after the last walk kernel */
 } selscan_launch;

@@ -29,6 +29,7 @@ struct Plan {
     int probe;
     int R, rowcap, poscap;
     int fetch;
+    int minb;
 };
 
 inline size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -52,6 +53,7 @@ Plan make_plan(int mode, long long ld, const selscan_launch *L)
     p.R = (L && L->window_rows > 0) ? (L->window_rows < 2 ? 2 : (L->window_rows > 64 ? 64 : L->window_rows))
                                      : window_rows(ld);
     p.fetch = (L && L->cores_per_fetch > 0) ? (L->cores_per_fetch > 1024 ? 1024 : L->cores_per_fetch) : 1;
+    p.minb = (L && L->min_ctas_per_sm == 3) ? 3 : 2;
     p.rowcap = win_rowcap(p.R, ld);
     p.poscap = win_poscap(p.R);
     const int sms = device_sms();
@@ -64,18 +66,17 @@ Plan make_plan(int mode, long long ld, const selscan_launch *L)
     }
     const int ipc = mode == SELSCAN_MODE_XPEHH ? 2 : 4;
     if (p.schedule == SELSCAN_SCHED_PLAIN) {
+        // one scratch slot per warp an SM can ever hold (64): a resident warp
+        // always finds a free slot, whatever the kernel's occupancy
         p.wpc = ipc;
-        const size_t smem = smem_per_warp(p.cap_s, p.tcap_s, p.rowcap, p.poscap) * (size_t)ipc;
-        int per_sm = max_ctas_per_sm(p.schedule, ipc, smem);
-        if (per_sm < 1) per_sm = 64 / ipc;                 // no device: the architectural maximum
         p.ctas = 0;
-        p.nslots = sms * per_sm * ipc;
+        p.nslots = sms * 64;
         return p;
     }
     p.wpc = (L && L->warps_per_cta > 0) ? L->warps_per_cta : kDefaultWarpsPerCta;
     if (p.wpc > 8) p.wpc = 8;
     const size_t smem = smem_per_warp(p.cap_s, p.tcap_s, p.rowcap, p.poscap) * (size_t)p.wpc;
-    int per_sm = max_ctas_per_sm(p.schedule, p.wpc, smem);
+    int per_sm = max_ctas_per_sm(p.schedule, p.wpc, smem, p.minb);
     if (per_sm < 1) per_sm = 64 / p.wpc > 0 ? 64 / p.wpc : 1;
     int want = (L && L->ctas_per_sm > 0) ? L->ctas_per_sm : per_sm;
     if (want > per_sm) want = per_sm;
@@ -196,8 +197,8 @@ int run_scan(int mode, const uint64_t *hap, int64_t ld, int32_t nA, int32_t nB, 
     if (launch && launch->walk_begin_event &&
         cudaEventRecord((cudaEvent_t)launch->walk_begin_event, s) != cudaSuccess)
         return SELSCAN_ERR_CUDA;
-    if (launch_walk(a, sk, sc, plan.schedule, plan.wpc, ctas_or_slots, plan.probe, plan.fetch, m, s) !=
-        cudaSuccess)
+    if (launch_walk(a, sk, sc, plan.schedule, plan.wpc, ctas_or_slots, plan.probe, plan.fetch, plan.minb,
+                    m, s) != cudaSuccess)
         return SELSCAN_ERR_CUDA;
     if (launch && launch->walk_end_event &&
         cudaEventRecord((cudaEvent_t)launch->walk_end_event, s) != cudaSuccess)

@@ -12,7 +12,7 @@
 
 namespace selscan {
 int device_sms();
-int max_ctas_per_sm(int schedule, int warps_per_cta, size_t smem_bytes);
+int max_ctas_per_sm(int schedule, int warps_per_cta, size_t smem_bytes, int minb);
 }
 
 using namespace selscan;
@@ -58,7 +58,7 @@ BatchPlan batch_plan(int max_n_total, long long max_ld)
     p.sc.err = nullptr;
     p.sc.base = nullptr;
     p.smem = smem_per_warp(p.sc.cap_s, p.sc.tcap_s, p.sc.rowcap, p.sc.poscap) * (size_t)p.wpc;
-    int per_sm = max_ctas_per_sm(SELSCAN_SCHED_IN_ORDER, p.wpc, p.smem);
+    int per_sm = max_ctas_per_sm(SELSCAN_SCHED_IN_ORDER, p.wpc, p.smem, 2);
     if (per_sm < 1) per_sm = 64 / p.wpc;
     p.ctas = device_sms() * per_sm;
     p.nslots = p.ctas * p.wpc;

@@ -83,7 +83,7 @@ cudaError_t launch_core_select(const ScanArgs &a, int mode, unsigned maf_num, un
                                int maf_filter, int32_t *n1, int8_t *core_status, cudaStream_t s);
 cudaError_t launch_walk(const ScanArgs &a, const ItemSink &sink, const Scratch &sc,
                         int schedule, int warps_per_cta, int ctas, int probe_steps, int fetch,
-                        long long n_items, cudaStream_t s);
+                        int minb, long long n_items, cudaStream_t s);
 cudaError_t launch_finalize_ihs(const ItemSink &sink, long long m, double *ihh1, double *ihh0,
                                 double *lnratio, int8_t *status, cudaStream_t s);
 cudaError_t launch_finalize_xpehh(const ItemSink &sink, long long m, double *ihhA,
@@ -93,6 +93,6 @@ cudaError_t launch_ehh(const ScanArgs &a, long long locus, const Scratch &sc,
                        int8_t *status, double *ihh, unsigned long long *denom, cudaStream_t s);
 cudaError_t launch_pack(const uint8_t *hap01, int n, long long m, int hap_major,
                         unsigned long long *rows, long long ld, cudaStream_t s);
-int max_ctas_per_sm(int schedule, int warps_per_cta, size_t smem_bytes);
+int max_ctas_per_sm(int schedule, int warps_per_cta, size_t smem_bytes, int minb);
 
 }  // namespace selscan

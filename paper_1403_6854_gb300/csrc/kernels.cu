@@ -74,8 +74,10 @@ cudaError_t launch_core_select(const ScanArgs &a, int mode, unsigned maf_num, un
 // Persistent walk kernel.  pass 1: items in core order (a warp takes one
 // core's items per queue fetch), optionally capped at max_steps; pass 2:
 // the sorted list of walks the first pass left unfinished, one per fetch.
-template <int NPOP>
-__global__ void __launch_bounds__(256, 2) walk_persistent_kernel(ScanArgs a, ItemSink sk, Scratch sc,
+// MINB: resident 8-warp CTAs per SM the build is compiled for (register cap
+// 65536 / (256 * MINB)): 2 (128 registers) or 3 (85 registers)
+template <int NPOP, int MINB>
+__global__ void __launch_bounds__(256, MINB) walk_persistent_kernel(ScanArgs a, ItemSink sk, Scratch sc,
                                                               long long n_cores, int pass,
                                                               int max_steps, int fetch)
 {
@@ -132,7 +134,10 @@ __global__ void __launch_bounds__(128) walk_plain_kernel(ScanArgs a, ItemSink sk
     }
     slot = __shfl_sync(FULLMASK, slot, 0);
     if (slot < 0) {                       // cannot happen: nslots >= resident warps
-        if (lane == 0) sk.item_status[core * (NPOP == 2 ? 2 : 4) + warp] = (int8_t)W_UNFINISHED;
+        if (lane == 0) {
+            sk.item_status[core * (NPOP == 2 ? 2 : 4) + warp] = (int8_t)W_UNFINISHED;
+            atomicExch(sc.err, SELSCAN_ERR_INTERNAL);
+        }
         return;
     }
     WarpBufs b = make_bufs(smem + (size_t)warp * slice_bytes(sc),
@@ -196,34 +201,37 @@ static int sm_count()
     return g_sms;
 }
 
-int max_ctas_per_sm(int schedule, int warps_per_cta, size_t smem_bytes)
+template <typename K>
+static int occupancy_of(K kernel, int warps_per_cta, size_t smem_bytes, bool carve)
 {
     int nb = 0;
-    cudaError_t e;
-    if (schedule == SELSCAN_SCHED_PLAIN) {
-        cudaFuncSetAttribute(walk_plain_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem_bytes);
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, walk_plain_kernel<1>,
-                                                          warps_per_cta * 32, smem_bytes);
-    } else {
-        cudaFuncSetAttribute(walk_persistent_kernel<1>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
-        cudaFuncSetAttribute(walk_persistent_kernel<1>,
-                             cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, walk_persistent_kernel<1>,
-                                                          warps_per_cta * 32, smem_bytes);
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+    if (carve) cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, warps_per_cta * 32, smem_bytes) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return -1;
     }
-    if (e != cudaSuccess || nb < 1) { cudaGetLastError(); return -1; }
-    int nb2 = 0;
-    if (schedule == SELSCAN_SCHED_PLAIN)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb2, walk_plain_kernel<2>,
-                                                          warps_per_cta * 32, smem_bytes);
-    else
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb2, walk_persistent_kernel<2>,
-                                                          warps_per_cta * 32, smem_bytes);
-    if (e == cudaSuccess && nb2 > nb) nb = nb2;
-    cudaGetLastError();
     return nb;
+}
+
+int max_ctas_per_sm(int schedule, int warps_per_cta, size_t smem_bytes, int minb)
+{
+    int a, b;
+    if (schedule == SELSCAN_SCHED_PLAIN) {
+        a = occupancy_of(walk_plain_kernel<1>, warps_per_cta, smem_bytes, false);
+        b = occupancy_of(walk_plain_kernel<2>, warps_per_cta, smem_bytes, false);
+    } else if (minb == 3) {
+        a = occupancy_of(walk_persistent_kernel<1, 3>, warps_per_cta, smem_bytes, true);
+        b = occupancy_of(walk_persistent_kernel<2, 3>, warps_per_cta, smem_bytes, true);
+    } else {
+        a = occupancy_of(walk_persistent_kernel<1, 2>, warps_per_cta, smem_bytes, true);
+        b = occupancy_of(walk_persistent_kernel<2, 2>, warps_per_cta, smem_bytes, true);
+    }
+    // the smaller of the two builds: a plan must fit either population count
+    if (a < 1) return b;
+    if (b < 1) return a;
+    return a < b ? a : b;
 }
 
 int device_sms() { return sm_count(); }
@@ -238,51 +246,62 @@ static int carveout_pct(size_t smem_per_cta, int ctas)
     return pct > 100 ? 100 : (pct < 10 ? 10 : pct);
 }
 
-template <int NPOP>
-static cudaError_t walk_impl(const ScanArgs &a, const ItemSink &sk, const Scratch &sc,
-                             int schedule, int wpc, int ctas, int probe, int fetch,
-                             long long n_cores, cudaStream_t s)
+template <int NPOP, int MINB>
+static cudaError_t persistent_impl(const ScanArgs &a, const ItemSink &sk, const Scratch &sc,
+                                   int schedule, int wpc, int ctas, int probe, int fetch,
+                                   long long n_cores, cudaStream_t s)
 {
     const size_t smem = slice_bytes(sc) * (size_t)wpc;
-    cudaError_t e;
+    cudaError_t e = cudaFuncSetAttribute(walk_persistent_kernel<NPOP, MINB>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    // shared memory as large as the resident CTAs need; the rest stays L1
+    e = cudaFuncSetAttribute(walk_persistent_kernel<NPOP, MINB>,
+                             cudaFuncAttributePreferredSharedMemoryCarveout, carveout_pct(smem, ctas));
+    if (e != cudaSuccess) return e;
+    const int cap = schedule == SELSCAN_SCHED_LONGEST_FIRST ? probe : 0;
+    walk_persistent_kernel<NPOP, MINB><<<ctas, wpc * 32, smem, s>>>(a, sk, sc, n_cores, 1, cap,
+                                                                     cap > 0 ? 1 : fetch);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (schedule == SELSCAN_SCHED_LONGEST_FIRST && probe > 0) {
+        bucket_hist_kernel<<<2 * sm_count(), 256, 0, s>>>(sk);
+        bucket_scan_kernel<<<1, NBUCKET, 0, s>>>(sk);
+        bucket_scatter_kernel<<<2 * sm_count(), 256, 0, s>>>(sk);
+        walk_persistent_kernel<NPOP, MINB><<<ctas, wpc * 32, smem, s>>>(a, sk, sc, n_cores, 2, 0, 1);
+    }
+    return cudaGetLastError();
+}
+
+template <int NPOP>
+static cudaError_t walk_impl(const ScanArgs &a, const ItemSink &sk, const Scratch &sc,
+                             int schedule, int wpc, int ctas, int probe, int fetch, int minb,
+                             long long n_cores, cudaStream_t s)
+{
     if (schedule == SELSCAN_SCHED_PLAIN) {
         const int ipc = NPOP == 2 ? 2 : 4;
         const size_t smem_p = slice_bytes(sc) * (size_t)ipc;
-        e = cudaFuncSetAttribute(walk_plain_kernel<NPOP>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p);
+        cudaError_t e = cudaFuncSetAttribute(walk_plain_kernel<NPOP>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p);
         if (e != cudaSuccess) return e;
         // `ctas` carries the number of scratch slots; the bitmap was reset by the caller
         walk_plain_kernel<NPOP><<<(unsigned)n_cores, ipc * 32, smem_p, s>>>(a, sk, sc, sk.slotmap,
                                                                             ctas);
         return cudaGetLastError();
     }
-    e = cudaFuncSetAttribute(walk_persistent_kernel<NPOP>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    // shared memory as large as the resident CTAs need; the rest stays L1
-    e = cudaFuncSetAttribute(walk_persistent_kernel<NPOP>,
-                             cudaFuncAttributePreferredSharedMemoryCarveout, carveout_pct(smem, ctas));
-    if (e != cudaSuccess) return e;
-    const int cap = schedule == SELSCAN_SCHED_LONGEST_FIRST ? probe : 0;
-    walk_persistent_kernel<NPOP><<<ctas, wpc * 32, smem, s>>>(a, sk, sc, n_cores, 1, cap,
-                                                               cap > 0 ? 1 : fetch);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if (schedule == SELSCAN_SCHED_LONGEST_FIRST && probe > 0) {
-        bucket_hist_kernel<<<2 * sm_count(), 256, 0, s>>>(sk);
-        bucket_scan_kernel<<<1, NBUCKET, 0, s>>>(sk);
-        bucket_scatter_kernel<<<2 * sm_count(), 256, 0, s>>>(sk);
-        walk_persistent_kernel<NPOP><<<ctas, wpc * 32, smem, s>>>(a, sk, sc, n_cores, 2, 0, 1);
-    }
-    return cudaGetLastError();
+    if (minb == 3)
+        return persistent_impl<NPOP, 3>(a, sk, sc, schedule, wpc, ctas, probe, fetch, n_cores, s);
+    return persistent_impl<NPOP, 2>(a, sk, sc, schedule, wpc, ctas, probe, fetch, n_cores, s);
 }
 
 cudaError_t launch_walk(const ScanArgs &a, const ItemSink &sink, const Scratch &sc,
                         int schedule, int warps_per_cta, int ctas, int probe_steps, int fetch,
-                        long long n_cores, cudaStream_t s)
+                        int minb, long long n_cores, cudaStream_t s)
 {
     if (sink.mode == 1)
-        return walk_impl<2>(a, sink, sc, schedule, warps_per_cta, ctas, probe_steps, fetch, n_cores, s);
-    return walk_impl<1>(a, sink, sc, schedule, warps_per_cta, ctas, probe_steps, fetch, n_cores, s);
+        return walk_impl<2>(a, sink, sc, schedule, warps_per_cta, ctas, probe_steps, fetch, minb,
+                            n_cores, s);
+    return walk_impl<1>(a, sink, sc, schedule, warps_per_cta, ctas, probe_steps, fetch, minb,
+                        n_cores, s);
 }
 
 // ------------------------------------------------------------ finalize

@@ -16,7 +16,7 @@ import os
 from typing import Callable, Dict, List, Optional
 
 SHAPE_FIELDS = ("schedule", "warps_per_cta", "smem_entries", "window_rows", "cores_per_fetch",
-                "probe_steps")
+                "probe_steps", "min_ctas_per_sm")
 
 DEFAULT_CANDIDATES: List[Dict] = [
     dict(schedule=1, warps_per_cta=8, smem_entries=512, window_rows=0, cores_per_fetch=1),
@@ -27,6 +27,10 @@ DEFAULT_CANDIDATES: List[Dict] = [
     dict(schedule=1, warps_per_cta=8, smem_entries=512, window_rows=16, cores_per_fetch=1),
     dict(schedule=1, warps_per_cta=8, smem_entries=512, window_rows=0, cores_per_fetch=4),
     dict(schedule=1, warps_per_cta=8, smem_entries=512, window_rows=0, cores_per_fetch=16),
+    dict(schedule=1, warps_per_cta=8, smem_entries=256, window_rows=4, cores_per_fetch=1,
+         min_ctas_per_sm=3),
+    dict(schedule=1, warps_per_cta=8, smem_entries=384, window_rows=0, cores_per_fetch=1,
+         min_ctas_per_sm=3),
     dict(schedule=0, warps_per_cta=8, smem_entries=512, window_rows=0, cores_per_fetch=1,
          probe_steps=64),
 ]

@@ -81,7 +81,8 @@ def test_schedules_and_capacities_bitwise_equal(sg, chr22):
                 sg.make_launch(sg.SCHED_IN_ORDER, smem_entries=8),       # spills to global
                 sg.make_launch(sg.SCHED_IN_ORDER, smem_entries=2048, warps_per_cta=4),
                 sg.make_launch(sg.SCHED_IN_ORDER, window_rows=2, cores_per_fetch=7),
-                sg.make_launch(sg.SCHED_IN_ORDER, window_rows=64, cores_per_fetch=64)]
+                sg.make_launch(sg.SCHED_IN_ORDER, window_rows=64, cores_per_fetch=64),
+                sg.make_launch(sg.SCHED_IN_ORDER, min_ctas_per_sm=3, smem_entries=256)]
     for L in variants:
         assert_bitwise_equal(base, run_ihs(sg, chr22.rows, 204, chr22.pos, chr22.gmap, launch=L))
 
