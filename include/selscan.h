@@ -105,6 +105,8 @@ typedef struct {
     int32_t min_ctas_per_sm;/* persistent build: 2 (default, 128 registers) or 3 (85 registers) */
     void *walk_begin_event; /* optional cudaEvent_t, recorded on the stream before the first walk kernel */
     void *walk_end_event;   /* optional cudaEvent_t, recorded after the last walk kernel */
+    int32_t big_group_entries; /* groups with at least this many 32-bit words are split by the
+                                  whole warp, smaller ones one lane each (0 = 32) */
 } selscan_launch;
 
 /* iHS outputs: device arrays of length m (one record per marker). */

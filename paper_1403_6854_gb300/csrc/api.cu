@@ -17,6 +17,7 @@ namespace {
 constexpr int kDefaultWarpsPerCta = 8;
 constexpr int kDefaultSmemEntries = 512;
 constexpr int kDefaultProbeSteps = 48;
+constexpr int kDefaultBigGroup = 32;
 constexpr int kMaxHaplotypes = 65000;
 constexpr size_t kMaxSmemPerCta = 227 * 1024;
 
@@ -30,6 +31,7 @@ struct Plan {
     int R, rowcap, poscap;
     int fetch;
     int minb;
+    int bigt;
 };
 
 inline size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -54,6 +56,7 @@ Plan make_plan(int mode, long long ld, const selscan_launch *L)
                                      : window_rows(ld);
     p.fetch = (L && L->cores_per_fetch > 0) ? (L->cores_per_fetch > 1024 ? 1024 : L->cores_per_fetch) : 1;
     p.minb = (L && L->min_ctas_per_sm == 3) ? 3 : 2;
+    p.bigt = (L && L->big_group_entries > 0) ? L->big_group_entries : kDefaultBigGroup;
     p.rowcap = win_rowcap(p.R, ld);
     p.poscap = win_poscap(p.R);
     const int sms = device_sms();
@@ -149,6 +152,7 @@ Scratch make_scratch(unsigned char *ws, const Layout &l, int n_total, const Plan
     sc.R = p.R;
     sc.rowcap = p.rowcap;
     sc.poscap = p.poscap;
+    sc.bigt = p.bigt;
     return sc;
 }
 

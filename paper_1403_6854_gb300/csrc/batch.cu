@@ -55,6 +55,7 @@ BatchPlan batch_plan(int max_n_total, long long max_ld)
     p.sc.rowcap = win_rowcap(p.sc.R, max_ld);   // >= 2 rows of the widest scan
     p.sc.poscap = win_poscap(64);               // narrower scans use up to 64 rows
     p.sc.per_warp = scratch_per_warp(max_n_total);
+    p.sc.bigt = 32;
     p.sc.err = nullptr;
     p.sc.base = nullptr;
     p.smem = smem_per_warp(p.sc.cap_s, p.sc.tcap_s, p.sc.rowcap, p.sc.poscap) * (size_t)p.wpc;

@@ -27,6 +27,7 @@ __device__ __forceinline__ WarpBufs make_bufs(unsigned char *sm, unsigned char *
     b.wgm[1] = (double *)w; w += sc.poscap;
     b.bar = (unsigned long long *)w;
     b.R = sc.R;
+    b.bigt = sc.bigt;
     return b;
 }
 

@@ -42,6 +42,7 @@ struct Scratch {
     int cap_s, tcap_s;            // on-chip tier sizes (multiples of 32)
     int R;                        // marker-window rows per buffer
     int rowcap, poscap;           // window buffer bytes (rows; positions or map values)
+    int bigt;                     // whole-warp group threshold (entries)
     int *err;                     // device error word
 };
 

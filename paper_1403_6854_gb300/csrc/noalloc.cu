@@ -105,6 +105,7 @@ extern "C" int selscan_ehh_noalloc(const uint64_t *hap, int64_t ld, int32_t n, i
     sc.R = window_rows(ld);
     sc.rowcap = win_rowcap(sc.R, ld);
     sc.poscap = win_poscap(sc.R);
+    sc.bigt = 32;
     sc.err = out->error;
 
     cudaStream_t s = (cudaStream_t)stream;

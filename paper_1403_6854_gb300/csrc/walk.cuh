@@ -39,7 +39,6 @@ enum : int {
     W_OK = 0, W_UNDEFINED = 2, W_EDGE = 3, W_GAP = 4, W_UNFINISHED = 5
 };
 
-constexpr int kBig = 32;   // groups with at least this many entries are processed by the whole warp
 
 struct ScanArgs {
     const unsigned long long *hap;  // rows, row k at hap + k * ld (64-bit words)
@@ -73,6 +72,7 @@ struct WarpBufs {
     double *wgm[2];
     unsigned long long *bar;      // one mbarrier per buffer
     int R;
+    int bigt;                     // groups with at least this many entries use the whole warp
 };
 
 struct WalkOut {
@@ -139,6 +139,18 @@ __device__ __forceinline__ unsigned lds32(unsigned addr)
     asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr));
     return v;
 }
+__device__ __forceinline__ long long lds64(unsigned addr)
+{
+    long long v;
+    asm volatile("ld.shared.s64 %0, [%1];" : "=l"(v) : "r"(addr));
+    return v;
+}
+__device__ __forceinline__ double ldsf64(unsigned addr)
+{
+    double v;
+    asm volatile("ld.shared.f64 %0, [%1];" : "=d"(v) : "r"(addr));
+    return v;
+}
 
 __device__ __forceinline__ unsigned long long mkent(unsigned int mask, unsigned int w)
 {
@@ -194,28 +206,6 @@ struct WinBuf {
     unsigned parity;
 };
 
-// Stage `bytes` (a multiple of 8) from src into the shared buffer dst: one
-// bulk copy of the 16-byte-aligned span around it when that span stays
-// inside [base, end), else plain loads by the warp.  Returns the byte offset
-// of the data in dst; adds the bulk bytes to tx.
-__device__ __forceinline__ int stage(unsigned char *dst, const unsigned char *src, unsigned bytes,
-                                     const unsigned char *base, const unsigned char *end,
-                                     unsigned long long *bar, unsigned &tx, bool issue)
-{
-    const int lane = threadIdx.x & 31;
-    const int off = (int)((uintptr_t)src & 15u);
-    const unsigned char *s0 = src - off;
-    const unsigned len = (bytes + (unsigned)off + 15u) & ~15u;
-    if (s0 >= base && s0 + len <= end) {
-        if (issue && lane == 0) bulk_g2s(dst, s0, len, bar);
-        tx += len;
-    } else if (issue) {
-        for (unsigned k = (unsigned)lane; k < bytes / 8u; k += 32u)
-            ((unsigned long long *)(dst + off))[k] = ((const unsigned long long *)src)[k];
-    }
-    return off;
-}
-
 // Fill buffer bi with the rows of steps [s, s + R) from `core` in direction dir.
 __device__ __forceinline__ void win_issue(const ScanArgs &a, const WarpBufs &b, WinBuf &w, int bi,
                                           long long core, int dir, long long s)
@@ -231,24 +221,44 @@ __device__ __forceinline__ void win_issue(const ScanArgs &a, const WarpBufs &b, 
     w.plo = (int)plo;
     __syncwarp();
     fence_proxy_async();                      // earlier reads of this buffer precede the copies
-    const unsigned char *hb = (const unsigned char *)a.hap;
-    const unsigned char *he = hb + (size_t)a.m * (size_t)a.ld * 8u;
-    const unsigned char *pb = (const unsigned char *)a.pos, *pe = pb + (size_t)a.m * 8u;
-    const unsigned char *gb = (const unsigned char *)a.gmap, *ge = gb + (size_t)a.m * 8u;
-    const unsigned rbytes = (unsigned)((hi - lo + 1) * a.ld * 8);
-    const unsigned pbytes = (unsigned)((phi - plo + 1) * 8);
-    const unsigned char *rs = hb + (size_t)lo * (size_t)a.ld * 8u;
-    const unsigned char *ps = pb + (size_t)plo * 8u, *gs = gb + (size_t)plo * 8u;
+    const unsigned char *src[3] = {
+        (const unsigned char *)a.hap + (size_t)lo * (size_t)a.ld * 8u,
+        (const unsigned char *)a.pos + (size_t)plo * 8u,
+        (const unsigned char *)a.gmap + (size_t)plo * 8u};
+    const unsigned char *base[3] = {(const unsigned char *)a.hap, (const unsigned char *)a.pos,
+                                    (const unsigned char *)a.gmap};
+    const size_t total[3] = {(size_t)a.m * (size_t)a.ld * 8u, (size_t)a.m * 8u, (size_t)a.m * 8u};
+    unsigned char *dst[3] = {b.wrow[bi], (unsigned char *)b.wpos[bi], (unsigned char *)b.wgm[bi]};
+    const unsigned bytes[3] = {(unsigned)((hi - lo + 1) * a.ld * 8), (unsigned)((phi - plo + 1) * 8),
+                               (unsigned)((phi - plo + 1) * 8)};
+    int off[3];
+    unsigned len[3];
+    bool bulk[3];
     unsigned tx = 0u;
-    // first pass sizes the transaction, second pass issues it after expect_tx
-    stage(b.wrow[bi], rs, rbytes, hb, he, b.bar + bi, tx, false);
-    stage((unsigned char *)b.wpos[bi], ps, pbytes, pb, pe, b.bar + bi, tx, false);
-    stage((unsigned char *)b.wgm[bi], gs, pbytes, gb, ge, b.bar + bi, tx, false);
-    if (tx && (threadIdx.x & 31) == 0) mbar_expect_tx(b.bar + bi, tx);
-    unsigned tx2 = 0u;
-    w.roff = stage(b.wrow[bi], rs, rbytes, hb, he, b.bar + bi, tx2, true);
-    w.poff = stage((unsigned char *)b.wpos[bi], ps, pbytes, pb, pe, b.bar + bi, tx2, true) / 8;
-    w.goff = stage((unsigned char *)b.wgm[bi], gs, pbytes, gb, ge, b.bar + bi, tx2, true) / 8;
+    // a bulk copy of the 16-byte-aligned span around each piece when that span
+    // stays inside its array, else plain loads by the warp
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        off[q] = (int)((uintptr_t)src[q] & 15u);
+        len[q] = (bytes[q] + (unsigned)off[q] + 15u) & ~15u;
+        bulk[q] = src[q] - off[q] >= base[q] && src[q] - off[q] + len[q] <= base[q] + total[q];
+        if (bulk[q]) tx += len[q];
+    }
+    const int lane = threadIdx.x & 31;
+    if (lane == 0) {
+        if (tx) mbar_expect_tx(b.bar + bi, tx);
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+            if (bulk[q]) bulk_g2s(dst[q], src[q] - off[q], len[q], b.bar + bi);
+    }
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+        if (!bulk[q])
+            for (unsigned k = (unsigned)lane; k < bytes[q] / 8u; k += 32u)
+                ((unsigned long long *)(dst[q] + off[q]))[k] = ((const unsigned long long *)src[q])[k];
+    w.roff = off[0];
+    w.poff = off[1] / 8;
+    w.goff = off[2] / 8;
     w.pending = tx != 0u;
     __syncwarp();
 }
@@ -401,7 +411,7 @@ __device__ __forceinline__ void split_step(const ScanArgs &a, unsigned row_sa, c
         unsigned long long t = 0ull;
         if (r < G0) t = *trow(b, r);
         const unsigned st = tab_st(t), ln = tab_ln(t), sz = tab_sz(t);
-        const bool isbig = ln >= (unsigned)kBig;
+        const bool isbig = ln >= (unsigned)b.bigt;
         const unsigned bb = __ballot_sync(FULLMASK, isbig);
         if (isbig) b.big[nbig + __popc(bb & ltm)] = (unsigned short)r;
         nbig += __popc(bb);
@@ -626,11 +636,14 @@ __device__ WalkOut walk(const ScanArgs &a, long long core, int dir, int sel, con
     unsigned long long p0 = S0, p1 = S1;
     const long long step = dir ? 1 : -1;
     const int R = b.R;
+    const unsigned rowbytes = (unsigned)a.ld * 8u;
     WinBuf wb[2];
     wb[0].parity = win_parity[0];
     wb[1].parity = win_parity[1];
     win_issue(a, b, wb[0], 0, core, dir, 1);
     win_issue(a, b, wb[1], 1, core, dir, 1 + R);
+    int bi = 1, left = 0;                         // current buffer, steps left in it
+    unsigned row_sa = 0u, pos_sa = 0u, gm_sa = 0u; // shared addresses of the current x
     for (long long i = 1;; ++i) {
         const long long x = core + step * i;
         if (x < 0 || x >= a.m) { o.status = W_EDGE; o.stop = (int)i; break; }
@@ -640,30 +653,36 @@ __device__ WalkOut walk(const ScanArgs &a, long long core, int dir, int sel, con
             o.key = (float)((double)(NPOP == 2 ? SP : S0) / (double)Dstop);
             break;
         }
-        const int bi = (int)(((i - 1) / R) & 1);
-        if ((i - 1) % R == 0) {
-            if (i > 1) {                          // the other buffer is done: refill it
-                if (bi) win_issue(a, b, wb[0], 0, core, dir, i + R);
-                else win_issue(a, b, wb[1], 1, core, dir, i + R);
+        if (left == 0) {                          // enter the next buffer
+            if (i > 1) {                          // the buffer just used is done: refill it
+                if (bi) win_issue(a, b, wb[1], 1, core, dir, i + R);
+                else win_issue(a, b, wb[0], 0, core, dir, i + R);
             }
+            bi ^= 1;
+            left = R;
             if (!(bi ? win_wait(b, wb[1], 1) : win_wait(b, wb[0], 0))) {
                 o.status = W_UNDEFINED;
                 o.stop = (int)i;
                 break;
             }
+            const WinBuf &w = bi ? wb[1] : wb[0];
+            row_sa = smem_u32(b.wrow[bi] + w.roff) + (unsigned)(x - w.lo) * rowbytes;
+            pos_sa = smem_u32(b.wpos[bi]) + 8u * (unsigned)(w.poff + (int)(x - w.plo));
+            gm_sa = smem_u32(b.wgm[bi]) + 8u * (unsigned)(w.goff + (int)(x - w.plo));
         }
-        const WinBuf &w = bi ? wb[1] : wb[0];
-        const long long *wp = b.wpos[bi] + (w.poff - w.plo);
-        const double *wg = b.wgm[bi] + (w.goff - w.plo);
-        const long long xp = x - step;
-        const long long lo = dir ? xp : x, hi = dir ? x : xp;
-        const long long bp = wp[hi] - wp[lo];
+        --left;
+        // positions / map of x and of the previous marker (one slot away in the window)
+        const unsigned prev_off = dir ? (unsigned)-8 : 8u;
+        const long long bp = dir ? lds64(pos_sa) - lds64(pos_sa + prev_off)
+                                 : lds64(pos_sa + prev_off) - lds64(pos_sa);
         if (bp > a.max_gap) { o.status = W_GAP; o.stop = (int)i; break; }
-        double g = wg[hi] - wg[lo];
+        double g = dir ? ldsf64(gm_sa) - ldsf64(gm_sa + prev_off) : ldsf64(gm_sa + prev_off) - ldsf64(gm_sa);
         if (bp > a.gap_scale) g = g * ((double)a.gap_scale / (double)bp);
 
-        split_step<NPOP>(a, smem_u32(b.wrow[bi] + w.roff + (size_t)(x - w.lo) * (size_t)a.ld * 8u),
-                         b, L, dS);
+        split_step<NPOP>(a, row_sa, b, L, dS);
+        // advance to the next marker inside the buffer
+        if (dir) { row_sa += rowbytes; pos_sa += 8u; gm_sa += 8u; }
+        else { row_sa -= rowbytes; pos_sa -= 8u; gm_sa -= 8u; }
         S0 -= dS[0];
         if (NPOP == 2) { S1 -= dS[1]; SP -= dS[2]; }
         const unsigned long long ii = (unsigned long long)(i + 1);
@@ -675,8 +694,10 @@ __device__ WalkOut walk(const ScanArgs &a, long long core, int dir, int sel, con
         if (stop && !a.crossing) { o.stop = (int)i; break; }
         // trapezoid (Eq. 4 / Eq. 5): (EHH(i-1) + EHH(i)) / 2 * g, with the
         // common 1 / (2 C(N,2)) applied once at the end
-        acc0 += (double)(p0 + S0) * g;
-        if (NPOP == 2) acc1 += (double)(p1 + S1) * g;
+        if (lane == 0) {                      // one lane keeps the FP64 sums
+            acc0 += (double)(p0 + S0) * g;
+            if (NPOP == 2) acc1 += (double)(p1 + S1) * g;
+        }
         if (stop) { o.stop = (int)i; break; }
         p0 = S0;
         p1 = S1;

@@ -16,7 +16,7 @@ import os
 from typing import Callable, Dict, List, Optional
 
 SHAPE_FIELDS = ("schedule", "warps_per_cta", "smem_entries", "window_rows", "cores_per_fetch",
-                "probe_steps", "min_ctas_per_sm")
+                "probe_steps", "min_ctas_per_sm", "big_group_entries")
 
 DEFAULT_CANDIDATES: List[Dict] = [
     dict(schedule=1, warps_per_cta=8, smem_entries=512, window_rows=0, cores_per_fetch=1),
