@@ -204,6 +204,11 @@ def main():
     ap.add_argument("--tune-cache", action="store_true")
     ap.add_argument("--served", type=int, default=200, help="requests in the served mix (0: skip)")
     ap.add_argument("--load", type=float, default=0.7, help="served arrival rate / capacity")
+    ap.add_argument("--overload", type=float, default=2.0,
+                    help="second served run at this arrival rate / capacity (0: skip)")
+    ap.add_argument("--policy", default="fifo", choices=["fifo", "srpt", "ps"],
+                    help="served tick composition")
+    ap.add_argument("--tick-cores", type=int, default=32768, help="served cores per tick")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--ref-budget", type=float, default=15.0)
@@ -412,25 +417,35 @@ def run_served(args, torch, synth):
     budget = int(min(0.5 * free, 64 << 30))
     ex = GpuExecutor()
     # capacity: the whole mix with every request present at t = 0
-    serve(reqs[:8], ex, budget, realtime=False)              # warm-up
-    _, _, mk = serve(reqs, ex, budget, realtime=False)
+    serve(reqs[:8], ex, budget, tick_cores=args.tick_cores, realtime=False)      # warm-up
+    _, _, mk = serve(reqs, ex, budget, tick_cores=args.tick_cores, policy=args.policy,
+                     realtime=False)
     capacity = total_cores / mk                              # markers per second
     rate = args.load * capacity / (total_cores / len(reqs))  # requests per second
     rng = np.random.Generator(np.random.PCG64(2024))
-    t = np.cumsum(rng.exponential(1.0 / rate, size=len(reqs)))
-    for r, a in zip(reqs, t):
-        r.arrival = float(a)
-    _, lat_s, mk_s = serve(reqs, ex, budget)
-    _, lat_p, mk_p = run_plain(reqs)
-    return {"requests": len(reqs), "mix": "70% iHS / 30% XPEHH, haplotypes log-U(100, 5000), "
-                                          "SNPs log-U(10k, 500k), seed 1000 + i",
-            "arrival_rate_per_s": rate, "load": args.load,
-            "capacity_markers_per_s": capacity, "hbm_budget_bytes": budget,
-            "generation_s": t_gen,
-            "continuous_batching": summarize(lat_s, total_cores, mk_s),
-            "plain_launches": summarize(lat_p, total_cores, mk_p),
-            "note": "latency = results on host - arrival; core_loci_per_s counts every marker "
-                    "(MAF-filtered cores included) over the makespan"}
+    gaps = rng.exponential(1.0, size=len(reqs))              # unit-rate Poisson gaps
+
+    def at_rate(rps):
+        for r, a in zip(reqs, np.cumsum(gaps / rps)):
+            r.arrival = float(a)
+        _, lat_s, mk_s = serve(reqs, ex, budget, tick_cores=args.tick_cores, policy=args.policy)
+        _, lat_p, mk_p = run_plain(reqs)
+        return {"arrival_rate_per_s": rps,
+                "continuous_batching": summarize(lat_s, total_cores, mk_s),
+                "plain_launches": summarize(lat_p, total_cores, mk_p)}
+
+    out = {"requests": len(reqs), "mix": "70% iHS / 30% XPEHH, haplotypes log-U(100, 5000), "
+                                         "SNPs log-U(10k, 500k), seed 1000 + i",
+           "policy": args.policy, "tick_cores": args.tick_cores, "load": args.load,
+           "capacity_markers_per_s": capacity, "hbm_budget_bytes": budget,
+           "generation_s": t_gen}
+    out.update(at_rate(rate))
+    if args.overload > 0:
+        out["overload"] = dict(load=args.overload, **at_rate(args.overload * rate / args.load))
+    out["note"] = ("latency = results on host - arrival; core_loci_per_s counts every marker "
+                   "(MAF-filtered cores included) over the makespan; capacity = the whole mix "
+                   "present at t = 0 through the server; both arms see the same arrivals")
+    return out
 
 
 if __name__ == "__main__":

@@ -207,7 +207,10 @@ int selscan_ehh_noalloc(const uint64_t *hap, int64_t ld, int32_t n, int64_t m,
  * Life of a scan: selscan_batch_prepare (validate + core selection), one or
  * more ticks covering every core [0, m) exactly once, selscan_batch_finalize.
  * All buffers in selscan_scan are caller-owned device memory; ticks and the
- * prepare/finalize calls of one scan must be ordered on one stream. */
+ * prepare/finalize calls of one scan must be ordered on one stream (or by
+ * events between streams). */
+#define SELSCAN_BATCH_MAX_SCANS 64    /* scans in one tick */
+#define SELSCAN_BATCH_MAX_UNITS 256   /* core ranges in one tick */
 typedef struct {
     int32_t mode;                 /* SELSCAN_MODE_IHS or SELSCAN_MODE_XPEHH */
     int32_t nA, nB;               /* iHS: n, (ignored); XPEHH: n_A, n_B */
@@ -229,13 +232,20 @@ typedef struct {
 
 size_t selscan_batch_item_bytes(int64_t m, int32_t mode);
 /* Workspace of one tick for scans of at most max_n_total haplotypes and row
- * stride max_ld, at most max_scans scans and max_units core ranges. */
+ * stride max_ld (max_scans <= SELSCAN_BATCH_MAX_SCANS and max_units <=
+ * SELSCAN_BATCH_MAX_UNITS, else 0; neither changes the size).  Two ticks in
+ * flight at once need two workspaces. */
 size_t selscan_batch_workspace_bytes(int32_t max_n_total, int64_t max_ld, int32_t max_scans,
                                      int32_t max_units);
 int selscan_batch_prepare(const selscan_scan *scan, void *stream);
-/* One tick: core ranges [unit_c0[u], unit_c1[u]) of scans[unit_scan[u]]
- * (host arrays; the scan array and unit arrays may be reused once the call
- * returns).  max_n_total / max_ld bound the scans of this tick. */
+/* One tick: core ranges [unit_c0[u], unit_c1[u]) of scans[unit_scan[u]],
+ * u < nunits <= SELSCAN_BATCH_MAX_UNITS, nscans <= SELSCAN_BATCH_MAX_SCANS
+ * (host arrays, read before the call returns: the tick copies nothing to the
+ * device, its descriptors travel in the launch's parameter block).  Cores
+ * are walked in unit order, one core per fetch of a warp.  max_n_total /
+ * max_ld bound the scans of this tick.  SELSCAN_ERR_INVALID_ARG for counts
+ * above the limits, ranges outside [0, m) or a scan that fails the checks of
+ * selscan_batch_prepare; nothing is launched then. */
 int selscan_batch_run(const selscan_scan *scans, int32_t nscans, const int32_t *unit_scan,
                       const int64_t *unit_c0, const int64_t *unit_c1, int32_t nunits,
                       int32_t max_n_total, int64_t max_ld, void *workspace, size_t ws_bytes,

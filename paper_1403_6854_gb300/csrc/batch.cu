@@ -1,9 +1,13 @@
 // Batched scans: several admitted scans (iHS and XPEHH, any sizes) share one
-// persistent walk launch ("tick").  The host hands each tick a list of core
-// ranges from any of the scans; warps pull ranges from one queue, so walks of
-// different scans run side by side on the GPU.  Used by the serving loop for
-// continuous batching; the statistics are exactly those of selscan_ihs /
-// selscan_xpehh (same walk code, same finalize).
+// persistent walk launch ("tick").  The host hands each tick up to
+// SELSCAN_BATCH_MAX_UNITS core ranges from up to SELSCAN_BATCH_MAX_SCANS scans;
+// the tick walks the concatenation of those ranges, one core per queue fetch
+// (neighbouring cores near a sweep all have long walks, so finer fetches
+// balance the warps), so walks of different scans run side by side on the
+// GPU.  Used by the serving loop for continuous batching; the statistics are
+// exactly those of selscan_ihs / selscan_xpehh (same walk code, same
+// finalize).  A tick issues no host-to-device copy: the scan descriptors and
+// the ranges travel as the kernel's parameter block.
 #include <string.h>
 
 #include "../../include/selscan.h"
@@ -19,7 +23,7 @@ using namespace selscan;
 
 namespace {
 
-constexpr int kBatchWarps = 8;
+constexpr int kBatchWarps = 4;
 constexpr int kBatchSmemEntries = 512;
 
 struct BatchDesc {
@@ -29,16 +33,23 @@ struct BatchDesc {
     int *err;
 };
 
-struct BatchUnit {
-    int scan;
-    int pad;
-    long long c0, c1;   // core range [c0, c1)
+// The whole tick, passed by value as the kernel's parameter block (at most
+// 32,764 bytes on this architecture).
+struct TickParams {
+    BatchDesc d[SELSCAN_BATCH_MAX_SCANS];
+    int scan[SELSCAN_BATCH_MAX_UNITS];            // scan of unit u
+    long long c0[SELSCAN_BATCH_MAX_UNITS];        // first core of unit u
+    long long off[SELSCAN_BATCH_MAX_UNITS + 1];   // tick index of unit u's first core
+    int nunits;
+    Scratch sc;
+    unsigned long long *head;
 };
+static_assert(sizeof(TickParams) <= 32000, "tick parameter block too large");
 
 inline size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct BatchPlan {
-    int ctas, wpc, nslots;
+    int ctas, wpc, nslots, carveout;
     Scratch sc;     // base filled at run time
     size_t smem;
 };
@@ -63,20 +74,23 @@ BatchPlan batch_plan(int max_n_total, long long max_ld)
     if (per_sm < 1) per_sm = 64 / p.wpc;
     p.ctas = device_sms() * per_sm;
     p.nslots = p.ctas * p.wpc;
+    // shared memory for the resident CTAs, the rest of the array stays L1
+    // (the global tier of the pools goes through it)
+    const size_t need = (p.smem + 1024) * (size_t)per_sm;
+    const int pct = (int)((need * 100 + 228 * 1024 - 1) / (228 * 1024));
+    p.carveout = pct > 100 ? 100 : (pct < 10 ? 10 : pct);
     return p;
 }
 
 struct BatchLayout {
-    size_t head, descs, units, scratch, total;
+    size_t head, scratch, total;
 };
 
-BatchLayout batch_layout(int max_scans, int max_units, int nslots, size_t per_warp)
+BatchLayout batch_layout(int nslots, size_t per_warp)
 {
     BatchLayout l;
     size_t o = 0;
     l.head = o;    o += 256;
-    l.descs = o;   o += up256((size_t)max_scans * sizeof(BatchDesc));
-    l.units = o;   o += up256((size_t)max_units * sizeof(BatchUnit));
     l.scratch = o; o += (size_t)nslots * per_warp;
     l.total = o;
     return l;
@@ -147,37 +161,35 @@ BatchDesc make_desc(const selscan_scan *s)
 
 namespace selscan {
 
-__global__ void __launch_bounds__(256, 2) walk_batch_kernel(const BatchDesc *descs,
-                                                            const BatchUnit *units, int nunits,
-                                                            Scratch sc, unsigned long long *head)
+__global__ void __launch_bounds__(256, 2) walk_batch_kernel(const __grid_constant__ TickParams t)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int wpc = blockDim.x >> 5;
     const long long gw = (long long)blockIdx.x * wpc + warp;
-    WarpBufs b = make_bufs(smem + (size_t)warp * slice_bytes(sc),
-                           sc.base + (size_t)gw * sc.per_warp, sc);
+    WarpBufs b = make_bufs(smem + (size_t)warp * slice_bytes(t.sc),
+                           t.sc.base + (size_t)gw * t.sc.per_warp, t.sc);
     init_window(b);
     unsigned wpar[2] = {0u, 0u};
+    const unsigned long long total = (unsigned long long)t.off[t.nunits];
+    int u = 0;
     for (;;) {
         unsigned long long idx = 0;
-        if (lane == 0) idx = atomicAdd(head, 1ull);
+        if (lane == 0) idx = atomicAdd(t.head, 1ull);
         idx = __shfl_sync(FULLMASK, idx, 0);
-        if (idx >= (unsigned long long)nunits) break;
-        const BatchUnit u = units[idx];
-        const BatchDesc &d = descs[u.scan];
-        const ScanArgs a = d.a;
-        const ItemSink sk = d.sk;
+        if (idx >= total) break;
+        // a warp's fetches increase, so its unit only moves forward
+        while (idx >= (unsigned long long)t.off[u + 1]) ++u;
+        const BatchDesc &d = t.d[t.scan[u]];
+        const long long c = t.c0[u] + (long long)(idx - (unsigned long long)t.off[u]);
+        if (d.sk.core_status[c] == (int8_t)SELSCAN_LOCUS_MAF_FILTERED) continue;
         b.R = d.R;
         b.err = d.err;
-        for (long long c = u.c0; c < u.c1; ++c) {
-            if (sk.core_status[c] == (int8_t)SELSCAN_LOCUS_MAF_FILTERED) continue;
-            if (sk.mode == 1) {
-                for (int q = 0; q < 2; ++q) run_item<2>(a, sk, b, (uint32_t)(c * 2 + q), 0, wpar);
-            } else {
-                for (int q = 0; q < 4; ++q) run_item<1>(a, sk, b, (uint32_t)(c * 4 + q), 0, wpar);
-            }
+        if (d.sk.mode == 1) {
+            for (int q = 0; q < 2; ++q) run_item<2>(d.a, d.sk, b, (uint32_t)(c * 2 + q), 0, wpar);
+        } else {
+            for (int q = 0; q < 4; ++q) run_item<1>(d.a, d.sk, b, (uint32_t)(c * 4 + q), 0, wpar);
         }
     }
 }
@@ -195,9 +207,11 @@ size_t selscan_batch_item_bytes(int64_t m, int32_t mode)
 size_t selscan_batch_workspace_bytes(int32_t max_n_total, int64_t max_ld, int32_t max_scans,
                                      int32_t max_units)
 {
-    if (max_n_total < 2 || max_ld < 1 || max_scans < 1 || max_units < 1) return 0;
+    if (max_n_total < 2 || max_ld < 1 || max_scans < 1 || max_units < 1 ||
+        max_scans > SELSCAN_BATCH_MAX_SCANS || max_units > SELSCAN_BATCH_MAX_UNITS)
+        return 0;
     // slots for the most warps an SM can hold, independent of the launch shape
-    return batch_layout(max_scans, max_units, device_sms() * 64, scratch_per_warp(max_n_total)).total;
+    return batch_layout(device_sms() * 64, scratch_per_warp(max_n_total)).total;
 }
 
 int selscan_batch_prepare(const selscan_scan *s, void *stream)
@@ -222,62 +236,49 @@ int selscan_batch_run(const selscan_scan *scans, int32_t nscans, const int32_t *
                       int32_t max_n_total, int64_t max_ld, void *workspace, size_t ws_bytes,
                       void *stream)
 {
-    if (!scans || nscans < 1 || !unit_scan || !unit_c0 || !unit_c1 || nunits < 0 || !workspace)
+    if (!scans || nscans < 1 || nscans > SELSCAN_BATCH_MAX_SCANS || !unit_scan || !unit_c0 ||
+        !unit_c1 || nunits < 0 || nunits > SELSCAN_BATCH_MAX_UNITS || !workspace)
         return SELSCAN_ERR_INVALID_ARG;
     if (nunits == 0) return SELSCAN_OK;
     BatchPlan plan = batch_plan(max_n_total, max_ld);
-    const BatchLayout l = batch_layout(nscans, nunits, plan.nslots, plan.sc.per_warp);
+    const BatchLayout l = batch_layout(plan.nslots, plan.sc.per_warp);
     if (ws_bytes < l.total || ((uintptr_t)workspace & 255)) return SELSCAN_ERR_WORKSPACE;
-    BatchDesc *hd = new BatchDesc[nscans];
-    BatchUnit *hu = new BatchUnit[nunits];
-    int rc = SELSCAN_OK;
-    for (int i = 0; i < nscans && rc == SELSCAN_OK; ++i) {
+    // static: the block is large, and it is consumed by the launch below
+    // before this function returns
+    static thread_local TickParams t;
+    for (int i = 0; i < nscans; ++i) {
         const selscan_scan *s = scans + i;
         const int nB = s->mode == SELSCAN_MODE_XPEHH ? s->nB : 0;
-        if (!scan_ok(s) || s->nA + nB > max_n_total || s->ld > max_ld) rc = SELSCAN_ERR_INVALID_ARG;
-        else {
-            hd[i] = make_desc(s);
-            int R = (plan.sc.rowcap - 16) / (int)(s->ld * 8);
-            hd[i].R = R < 2 ? 2 : (R > 64 ? 64 : R);
-        }
+        if (!scan_ok(s) || s->nA + nB > max_n_total || s->ld > max_ld) return SELSCAN_ERR_INVALID_ARG;
+        t.d[i] = make_desc(s);
+        int R = (plan.sc.rowcap - 16) / (int)(s->ld * 8);
+        t.d[i].R = R < 2 ? 2 : (R > 64 ? 64 : R);
     }
-    for (int u = 0; u < nunits && rc == SELSCAN_OK; ++u) {
+    long long off = 0;
+    for (int u = 0; u < nunits; ++u) {
         const int si = unit_scan[u];
         if (si < 0 || si >= nscans || unit_c0[u] < 0 || unit_c1[u] < unit_c0[u] || unit_c1[u] > scans[si].m)
-            rc = SELSCAN_ERR_INVALID_ARG;
-        hu[u].scan = si;
-        hu[u].pad = 0;
-        hu[u].c0 = unit_c0[u];
-        hu[u].c1 = unit_c1[u];
+            return SELSCAN_ERR_INVALID_ARG;
+        t.scan[u] = si;
+        t.c0[u] = unit_c0[u];
+        t.off[u] = off;
+        off += unit_c1[u] - unit_c0[u];
     }
+    t.off[nunits] = off;
+    t.nunits = nunits;
     cudaStream_t st = (cudaStream_t)stream;
     unsigned char *ws = (unsigned char *)workspace;
-    if (rc == SELSCAN_OK) {
-        plan.sc.base = ws + l.scratch;
-        if (cudaMemsetAsync(ws + l.head, 0, 256, st) != cudaSuccess ||
-            cudaMemcpyAsync(ws + l.descs, hd, sizeof(BatchDesc) * (size_t)nscans,
-                            cudaMemcpyHostToDevice, st) != cudaSuccess ||
-            cudaMemcpyAsync(ws + l.units, hu, sizeof(BatchUnit) * (size_t)nunits,
-                            cudaMemcpyHostToDevice, st) != cudaSuccess)
-            rc = SELSCAN_ERR_CUDA;
-    }
-    if (rc == SELSCAN_OK) {
-        if (cudaFuncSetAttribute(walk_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)plan.smem) != cudaSuccess ||
-            cudaFuncSetAttribute(walk_batch_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                 100) != cudaSuccess)
-            rc = SELSCAN_ERR_CUDA;
-    }
-    if (rc == SELSCAN_OK) {
-        walk_batch_kernel<<<plan.ctas, plan.wpc * 32, plan.smem, st>>>(
-            (const BatchDesc *)(ws + l.descs), (const BatchUnit *)(ws + l.units), nunits, plan.sc,
-            (unsigned long long *)(ws + l.head));
-        if (cudaGetLastError() != cudaSuccess) rc = SELSCAN_ERR_CUDA;
-    }
-    // the pageable copies above are complete when cudaMemcpyAsync returns
-    delete[] hd;
-    delete[] hu;
-    return rc;
+    plan.sc.base = ws + l.scratch;
+    t.sc = plan.sc;
+    t.head = (unsigned long long *)(ws + l.head);
+    if (cudaMemsetAsync(ws + l.head, 0, 256, st) != cudaSuccess) return SELSCAN_ERR_CUDA;
+    if (cudaFuncSetAttribute(walk_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)plan.smem) != cudaSuccess ||
+        cudaFuncSetAttribute(walk_batch_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             plan.carveout) != cudaSuccess)
+        return SELSCAN_ERR_CUDA;
+    walk_batch_kernel<<<plan.ctas, plan.wpc * 32, plan.smem, st>>>(t);
+    return cudaGetLastError() == cudaSuccess ? SELSCAN_OK : SELSCAN_ERR_CUDA;
 }
 
 int selscan_batch_finalize(const selscan_scan *s, void *stream)

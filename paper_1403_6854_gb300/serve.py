@@ -3,16 +3,17 @@
 Requests (scans of any mode and size) arrive over time.  The server keeps the
 packed matrices of admitted scans resident in HBM, admits waiting requests in
 arrival order as soon as their HBM footprint fits the budget, and runs
-"ticks": one persistent walk launch (selscan_batch_run) over core ranges taken
-round-robin from every resident scan, so requests that arrive while others
-run join the very next tick and their walks share the GPU.  A scan whose cores
+"ticks": one persistent walk launch (selscan_batch_run) over core ranges of
+the resident scans in policy order, so requests that arrive while others run
+join the very next tick and their walks share the GPU.  A scan whose cores
 are all walked is finalised, its results are copied to the host and its
 memory is released.  Latency = result on the host - arrival.
 
 `Scheduler` holds the host-side policy (admission, tick composition) and is
 independent of the GPU; `GpuExecutor` runs it on the device through the
-C ABI; `run_plain` is the comparison: each request alone, in arrival order,
-with one plain launch (one CTA per core).
+C ABI; `serve` replays a list of timed requests, `Server` is the online form
+(submit -> Future, cancel); `run_plain` is the comparison: each request
+alone, in arrival order, with one plain launch (one CTA per core).
 """
 from __future__ import annotations
 
@@ -71,14 +72,19 @@ class Active:
 
 
 class Scheduler:
-    """Admission by HBM footprint (FIFO) and round-robin tick composition."""
+    """Admission by HBM footprint (FIFO) and tick composition by policy."""
 
-    def __init__(self, hbm_budget: int, tick_cores: int = 32768, unit_cores: int = 4,
-                 max_active: int = 64):
+    POLICIES = ("fifo", "srpt", "ps")
+    MAX_SCANS = 64                # scans one tick can carry (the C ABI's limit)
+
+    def __init__(self, hbm_budget: int, tick_cores: int = 32768, max_active: int = MAX_SCANS,
+                 policy: str = "fifo"):
+        if policy not in self.POLICIES:
+            raise ValueError(policy)
+        self.policy = policy
         self.budget = int(hbm_budget)
         self.tick_cores = int(tick_cores)
-        self.unit_cores = int(unit_cores)
-        self.max_active = int(max_active)
+        self.max_active = min(int(max_active), self.MAX_SCANS)
         self.waiting: deque = deque()
         self.active: List[Active] = []
         self.used = 0
@@ -87,6 +93,14 @@ class Scheduler:
         if footprint(req) > self.budget:
             raise ValueError(f"request {req.rid} needs {footprint(req)} B, budget {self.budget} B")
         self.waiting.append(req)
+
+    def cancel(self, rid: int) -> bool:
+        """Drop a request that has not been admitted yet; True if it was waiting."""
+        for r in self.waiting:
+            if r.rid == rid:
+                self.waiting.remove(r)
+                return True
+        return False
 
     def admit(self) -> List[Active]:
         """Admit waiting requests, in arrival order, while they fit."""
@@ -103,31 +117,32 @@ class Scheduler:
         return new
 
     def compose_tick(self) -> Tuple[List[Active], np.ndarray]:
-        """Core ranges for the next tick.  The tick's core budget goes to the
-        resident scans with the least remaining work first (shortest remaining
-        work first: a small request finishes within a tick or two of its
-        admission), split into units of unit_cores cores that are interleaved
-        across scans.  Returns the tick's scans and an int64 array of units
-        (index into that list, c0, c1)."""
-        live = sorted((a for a in self.active if a.remaining > 0), key=lambda a: a.remaining)
+        """Core ranges for the next tick: one contiguous range per scan, the
+        tick's core budget handed out in policy order ("fifo" oldest first,
+        younger scans backfill what the oldest cannot use; "srpt" least
+        remaining work first; "ps" equal shares).  The device walks the ranges
+        in this order, one core per warp fetch.  Returns the tick's scans and
+        an int64 array of units (index into that list, c0, c1)."""
+        live = [a for a in self.active if a.remaining > 0]
         if not live:
             return [], np.zeros((0, 3), np.int64)
+        if self.policy == "srpt":
+            live.sort(key=lambda a: a.remaining)
+        share = max(1, self.tick_cores // len(live)) if self.policy == "ps" else None
         budget = self.tick_cores
-        parts = []
-        for i, a in enumerate(live):
+        out, rows = [], []
+        for a in live:
             if budget <= 0:
-                live = live[:i]
                 break
-            take = min(budget, a.remaining)
-            c0 = np.arange(a.next_core, a.next_core + take, self.unit_cores, dtype=np.int64)
-            c1 = np.minimum(c0 + self.unit_cores, a.next_core + take)
-            k = np.arange(c0.size, dtype=np.int64)
-            parts.append(np.stack([k, np.full(c0.size, i, np.int64), c0, c1], 1))
+            take = min(budget, a.remaining, share or budget)
+            rows.append((len(out), a.next_core, a.next_core + take))
+            out.append(a)
             a.next_core += take
             budget -= take
-        u = np.concatenate(parts)
-        u = u[np.lexsort((u[:, 1], u[:, 0]))]      # interleave: unit k of every scan, then k + 1
-        return live, u[:, 1:]
+        return out, np.array(rows, np.int64).reshape(-1, 3)
+
+    def has_work(self) -> bool:
+        return any(a.remaining > 0 for a in self.active)
 
     def finished(self) -> List[Active]:
         done = [a for a in self.active if a.remaining == 0]
@@ -201,6 +216,13 @@ class GpuExecutor:
         self.streams[(self.k + 1) % 2].wait_event(ev)
         return (s, t)
 
+    def wait_slot(self) -> None:
+        """Block until the stream the next tick goes to has finished its
+        previous tick, so that no more than two ticks are ever queued."""
+        ev = self.events[self.k % 2]
+        if ev is not None:
+            ev.synchronize()
+
     def run_tick(self, live: List[Active], units) -> None:
         sg, torch = self.sg, self.torch
         i = self.k % 2
@@ -224,50 +246,234 @@ class GpuExecutor:
             self.last_tick[a.req.rid] = self.k
         self.k += 1
 
-    def finish(self, a: Active) -> Dict[str, np.ndarray]:
+    FIELDS = ("status", "n1", "ihh_a", "ihh_b", "lnratio", "stop", "digest", "error")
+
+    def start_finish(self, a: Active):
+        """Queue finalisation and the copy of the results to pinned host memory
+        on the completion stream, after every tick issued so far; returns a
+        handle for poll_finish."""
         torch = self.torch
         s, t = a.handle
-        st = self.streams[self.last_tick.get(a.req.rid, self.k) % 2]
-        other = self.events[(self.last_tick.get(a.req.rid, self.k) + 1) % 2]
-        if other is not None:
-            st.wait_event(other)
-        self.sg.selscan_batch_finalize(s, st)
-        st.synchronize()
-        out = {f: t[f].cpu().numpy() for f in ("status", "n1", "ihh_a", "ihh_b", "lnratio", "stop",
-                                               "digest", "error")}
+        if not hasattr(self, "fstream"):
+            self.fstream = torch.cuda.Stream(self.device)
+        fs = self.fstream
+        for ev in self.events:
+            if ev is not None:
+                fs.wait_event(ev)
+        self.sg.selscan_batch_finalize(s, fs)
+        host = {}
+        with torch.cuda.stream(fs):
+            for f in self.FIELDS:
+                h = torch.empty(t[f].shape, dtype=t[f].dtype, pin_memory=True)
+                h.copy_(t[f], non_blocking=True)
+                host[f] = h
+        done = torch.cuda.Event()
+        done.record(fs)
+        self.last_tick.pop(a.req.rid, None)
+        return (done, host, t)
+
+    def poll_finish(self, handle, block: bool = False):
+        """Results of a queued finalisation once they are on the host, else None."""
+        done, host, _ = handle
+        if block:
+            done.synchronize()
+        elif not done.query():
+            return None
+        out = {f: host[f].numpy() for f in self.FIELDS}
         out["digest"] = out["digest"].view(np.uint64)
         if int(out["error"][0]) != 0:
-            raise self.sg.SelscanError(int(out["error"][0]), f"request {a.req.rid}")
-        self.last_tick.pop(a.req.rid, None)
+            raise self.sg.SelscanError(int(out["error"][0]), "served scan")
         return out
+
+    def finish(self, a: Active) -> Dict[str, np.ndarray]:
+        return self.poll_finish(self.start_finish(a), block=True)
+
+
+class _Loop:
+    """One pass of the serving loop: admit, launch the next tick, queue the
+    finalisation of scans whose cores are all walked, collect finished ones.
+    The host never waits for the GPU unless told to (nothing left to launch)."""
+
+    def __init__(self, sch: Scheduler, executor):
+        self.sch, self.ex = sch, executor
+        self.finishing: List[Tuple[Active, object]] = []
+        self.cancelled = set()
+        self.async_finish = hasattr(executor, "start_finish")
+
+    def busy(self) -> bool:
+        return bool(self.sch.waiting or self.sch.active or self.finishing)
+
+    def cancel(self, rid: int) -> bool:
+        """Cancel a waiting or resident scan.  A resident scan stops receiving
+        ticks; its memory is released once the ticks already issued for it
+        are done."""
+        if self.sch.cancel(rid):
+            return True
+        for a in self.sch.active:
+            if a.req.rid == rid:
+                self.cancelled.add(rid)
+                a.next_core = a.req.m
+                return True
+        return False
+
+    def step(self, may_block: bool) -> Tuple[List[Tuple[Active, Optional[Dict]]], bool]:
+        """Returns (done, idle): scans completed in this pass with their results
+        (None for a cancelled scan) and whether no tick was launched."""
+        sch, ex = self.sch, self.ex
+        done = []
+        for a in sch.admit():
+            a.handle = ex.upload(a.req)
+        if sch.has_work() and hasattr(ex, "wait_slot"):
+            ex.wait_slot()      # at most two ticks in flight: new scans join the next one
+        live, units = sch.compose_tick()
+        if len(units):
+            ex.run_tick(live, units)
+        queued = {id(f[0]) for f in self.finishing}
+        for a in sch.finished():
+            if id(a) in queued:
+                continue
+            if self.async_finish:
+                self.finishing.append((a, ex.start_finish(a)))
+            else:
+                done.append((a, ex.finish(a)))
+                sch.release(a)
+        idle = not len(units)
+        still = []
+        for a, h in self.finishing:
+            out = ex.poll_finish(h, block=idle and may_block)
+            if out is None:
+                still.append((a, h))
+                continue
+            done.append((a, out))
+            sch.release(a)
+        self.finishing = still
+        for i, (a, out) in enumerate(done):
+            if a.req.rid in self.cancelled:
+                self.cancelled.discard(a.req.rid)
+                done[i] = (a, None)
+        return done, idle
 
 
 def serve(requests: List[Request], executor, hbm_budget: int, tick_cores: int = 32768,
-          unit_cores: int = 4, clock: Callable[[], float] = time.perf_counter,
-          realtime: bool = True) -> Tuple[Dict[int, Dict], Dict[int, float], float]:
-    """Serve requests (sorted by arrival).  Returns results, latencies, makespan."""
-    sch = Scheduler(hbm_budget, tick_cores, unit_cores)
+          clock: Callable[[], float] = time.perf_counter,
+          realtime: bool = True, policy: str = "fifo") -> Tuple[Dict[int, Dict], Dict[int, float], float]:
+    """Replay requests (by arrival time; realtime=False submits all at once).
+    Returns results, latencies (result on the host - arrival), makespan."""
+    loop = _Loop(Scheduler(hbm_budget, tick_cores, policy=policy), executor)
     pending = deque(sorted(requests, key=lambda r: r.arrival))
     results, latency = {}, {}
     t0 = clock()
-    while pending or sch.waiting or sch.active:
+    while pending or loop.busy():
         now = clock() - t0
         while pending and (pending[0].arrival <= now or not realtime):
-            sch.submit(pending.popleft())
-        for a in sch.admit():
-            a.handle = executor.upload(a.req)
-        live, units = sch.compose_tick()
-        if len(units):
-            executor.run_tick(live, units)
-        for a in sch.finished():
-            results[a.req.rid] = executor.finish(a)
+            loop.sch.submit(pending.popleft())
+        done, idle = loop.step(may_block=not (pending and realtime))
+        for a, out in done:
+            results[a.req.rid] = out
             latency[a.req.rid] = (clock() - t0) - a.req.arrival
-            sch.release(a)
-        if not len(units) and not sch.finished() and pending and realtime:
+        if idle and not loop.finishing and pending and realtime:
             wait = pending[0].arrival - (clock() - t0)
             if wait > 0:
-                time.sleep(min(wait, 0.05))
+                time.sleep(min(wait, 0.002))
     return results, latency, clock() - t0
+
+
+class Server:
+    """Online form of the loop: submit() (from any thread) returns a Future
+    that resolves to the scan's results; cancel() drops a waiting or resident
+    scan (its Future is cancelled).  A background thread runs the loop and
+    owns the executor; close() drains nothing, it stops after the current
+    pass and cancels whatever is still open."""
+
+    def __init__(self, executor, hbm_budget: int, tick_cores: int = 32768, policy: str = "fifo",
+                 idle_wait: float = 0.002):
+        import threading
+        self._loop = _Loop(Scheduler(hbm_budget, tick_cores, policy=policy), executor)
+        self._lock = threading.Lock()
+        self._inbox: deque = deque()
+        self._cancels: deque = deque()
+        self._futures: Dict[int, "Future"] = {}
+        self._wake = threading.Event()
+        self._stop = False
+        self._idle_wait = idle_wait
+        self._error: Optional[BaseException] = None
+        self._thread = threading.Thread(target=self._run, name="selscan-serve", daemon=True)
+        self._thread.start()
+
+    def submit(self, req: Request):
+        from concurrent.futures import Future
+        if footprint(req) > self._loop.sch.budget:
+            raise ValueError(f"request {req.rid} needs {footprint(req)} B, budget {self._loop.sch.budget} B")
+        fut = Future()
+        with self._lock:
+            if self._stop:
+                raise RuntimeError("server closed")
+            if req.rid in self._futures:
+                raise ValueError(f"request id {req.rid} is open")
+            self._futures[req.rid] = fut
+            self._inbox.append(req)
+        self._wake.set()
+        return fut
+
+    def cancel(self, rid: int) -> None:
+        with self._lock:
+            self._cancels.append(rid)
+        self._wake.set()
+
+    def close(self, timeout: Optional[float] = None) -> None:
+        with self._lock:
+            self._stop = True
+        self._wake.set()
+        self._thread.join(timeout)
+        with self._lock:
+            for f in self._futures.values():
+                f.cancel()
+            self._futures.clear()
+        if self._error is not None:
+            raise self._error
+
+    def _resolve(self, rid: int, out) -> None:
+        with self._lock:
+            fut = self._futures.pop(rid, None)
+        if fut is None:
+            return
+        if out is None:
+            fut.cancel()
+        elif fut.set_running_or_notify_cancel():
+            fut.set_result(out)
+
+    def _run(self) -> None:
+        loop = self._loop
+        try:
+            while True:
+                with self._lock:
+                    if self._stop:
+                        return
+                    while self._inbox:
+                        loop.sch.submit(self._inbox.popleft())
+                    cancels = list(self._cancels)
+                    self._cancels.clear()
+                for rid in cancels:
+                    waiting = any(r.rid == rid for r in loop.sch.waiting)
+                    if loop.cancel(rid) and waiting:
+                        self._resolve(rid, None)
+                if not loop.busy():
+                    self._wake.wait(self._idle_wait)
+                    self._wake.clear()
+                    continue
+                done, idle = loop.step(may_block=False)
+                for a, out in done:
+                    self._resolve(a.req.rid, out)
+                if idle and loop.finishing:
+                    time.sleep(self._idle_wait / 4)
+        except BaseException as e:          # surfaced to every open Future and by close()
+            self._error = e
+            with self._lock:
+                futs = list(self._futures.values())
+                self._futures.clear()
+            for f in futs:
+                if f.set_running_or_notify_cancel():
+                    f.set_exception(e)
 
 
 def run_plain(requests: List[Request], device="cuda", clock: Callable[[], float] = time.perf_counter,

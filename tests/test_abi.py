@@ -100,3 +100,23 @@ def test_host_side_argument_errors(sg):
     assert lib.selscan_ehh(fake, 2, 100, 10, fake, fake, 10, ctypes.byref(p), ctypes.byref(oe), 4,
                            fake, 1 << 20, None) == sg.ERR_INVALID_ARG
     assert lib.selscan_pack(fake, 100, 10, 2, fake, 2, None) == sg.ERR_INVALID_ARG
+
+
+def test_batch_limits(sg):
+    """Tick limits of the batch ABI, rejected before any device work."""
+    lib = sg.load_library()
+    assert sg.selscan_batch_workspace_bytes(100, 2, 64, 256) > 0
+    assert sg.selscan_batch_workspace_bytes(100, 2, 65, 1) == 0
+    assert sg.selscan_batch_workspace_bytes(100, 2, 1, 257) == 0
+    assert sg.selscan_batch_item_bytes(1000, sg.MODE_IHS) >= 1000 * 4 * 9
+    assert sg.selscan_batch_item_bytes(0, sg.MODE_IHS) == 0
+    scans = (sg.selscan_scan * 65)()
+    us = (ctypes.c_int32 * 257)()
+    c = (ctypes.c_int64 * 257)()
+    fake = ctypes.c_void_p(0x1000)
+    assert lib.selscan_batch_run(scans, 65, us, c, c, 1, 100, 2, fake, 1 << 30,
+                                 None) == sg.ERR_INVALID_ARG
+    assert lib.selscan_batch_run(scans, 1, us, c, c, 257, 100, 2, fake, 1 << 30,
+                                 None) == sg.ERR_INVALID_ARG
+    # a scan that fails its checks (all-zero struct) launches nothing
+    assert lib.selscan_batch_prepare(scans, None) == sg.ERR_INVALID_ARG

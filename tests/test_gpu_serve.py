@@ -46,8 +46,7 @@ def test_served_results_equal_alone(sg):
     from paper_1403_6854_gb300.serve import GpuExecutor, footprint, serve
     reqs = make_requests()
     budget = sum(footprint(r) for r in reqs[:3])      # at most ~3 resident: admission matters
-    res, lat, mk = serve(reqs, GpuExecutor(), budget, tick_cores=700, unit_cores=64,
-                         realtime=False)
+    res, lat, mk = serve(reqs, GpuExecutor(), budget, tick_cores=700, realtime=False)
     assert sorted(res) == [r.rid for r in reqs]
     for r in reqs:
         got, ref = res[r.rid], alone(sg, r)
@@ -58,6 +57,31 @@ def test_served_results_equal_alone(sg):
         ok = ~np.isnan(ref["lnratio"])
         assert np.array_equal(np.isnan(got["lnratio"]), ~ok)
         np.testing.assert_allclose(got["lnratio"][ok], ref["lnratio"][ok], rtol=0, atol=LN_ATOL)
+
+
+def test_server_futures_equal_alone(sg):
+    """The online form: futures resolve to the same results; a cancelled
+    resident scan frees its memory and the rest complete."""
+    from paper_1403_6854_gb300.serve import GpuExecutor, Server, footprint
+    reqs = make_requests()
+    srv = Server(GpuExecutor(), sum(footprint(r) for r in reqs[:2]), tick_cores=500,
+                 policy="srpt")
+    futs = {r.rid: srv.submit(r) for r in reqs}
+    srv.cancel(4)
+    for r in reqs:
+        if r.rid == 4:
+            continue
+        got, ref = futs[r.rid].result(timeout=300), alone(sg, r)
+        for f in ("status", "n1", "stop", "digest"):
+            assert np.array_equal(got[f], ref[f]), (r.rid, f)
+        np.testing.assert_allclose(got["ihh_a"], ref["ihh_a"], rtol=IHH_RTOL, atol=0)
+    assert futs[4].cancelled() or futs[4].done()
+    import time
+    t = time.time()
+    while srv._loop.busy() and time.time() - t < 60:
+        time.sleep(0.01)
+    srv.close()
+    assert srv._loop.sch.used == 0
 
 
 def test_plain_runner_equals_alone(sg):
