@@ -94,6 +94,12 @@ typedef struct {
 #define SELSCAN_SCHED_LONGEST_FIRST 0  /* persistent kernel, probe pass + longest-first queue */
 #define SELSCAN_SCHED_IN_ORDER      1  /* persistent kernel, one queue in core order */
 #define SELSCAN_SCHED_PLAIN         2  /* one CTA per core, no persistence, no ordering */
+#define SELSCAN_SCHED_SWEEP         3  /* sorted sweep: per chunk of cores the haplotypes are kept
+                                          sorted by their sequence read outward from the core, and
+                                          a walk applies only the neighbour pairs that part at each
+                                          step; walks longer than the chunk's history finish in a
+                                          second in-order pass.  Needs n_total <= 16383 (else the
+                                          in-order schedule runs). */
 typedef struct {
     int32_t schedule;       /* SELSCAN_SCHED_* */
     int32_t warps_per_cta;  /* 1..8 (0 = default) */
@@ -107,6 +113,11 @@ typedef struct {
     void *walk_end_event;   /* optional cudaEvent_t, recorded after the last walk kernel */
     int32_t big_group_entries; /* groups with at least this many 32-bit words are split by the
                                   whole warp, smaller ones one lane each (0 = 32) */
+    int32_t sweep_warmup;      /* sweep schedule: markers sorted before a chunk's first core,
+                                  16..16384 (0 = 1024); walks longer than this may take the
+                                  second pass */
+    int32_t sweep_stage_cores; /* sweep schedule: cores per chunk between walk launches,
+                                  1..4096 (0 = 64); sizes the slot buffer */
 } selscan_launch;
 
 /* iHS outputs: device arrays of length m (one record per marker). */

@@ -30,7 +30,7 @@ ERR_INVALID_ARG, ERR_UNSORTED, ERR_WORKSPACE, ERR_CUDA, ERR_TIMEOUT, ERR_UNSUPPO
 ERR_INTERNAL = -7
 LOCUS_OK, LOCUS_MAF_FILTERED, LOCUS_UNDEFINED, LOCUS_ABORT_EDGE, LOCUS_ABORT_GAP = 0, 1, 2, 3, 4
 MODE_IHS, MODE_XPEHH, MODE_EHH = 0, 1, 2
-SCHED_LONGEST_FIRST, SCHED_IN_ORDER, SCHED_PLAIN = 0, 1, 2
+SCHED_LONGEST_FIRST, SCHED_IN_ORDER, SCHED_PLAIN, SCHED_SWEEP = 0, 1, 2, 3
 
 _P = ctypes.c_void_p
 
@@ -48,7 +48,8 @@ class selscan_launch(ctypes.Structure):
                 ("probe_steps", ctypes.c_int32), ("window_rows", ctypes.c_int32),
                 ("cores_per_fetch", ctypes.c_int32), ("min_ctas_per_sm", ctypes.c_int32),
                 ("walk_begin_event", ctypes.c_void_p), ("walk_end_event", ctypes.c_void_p),
-                ("big_group_entries", ctypes.c_int32)]
+                ("big_group_entries", ctypes.c_int32), ("sweep_warmup", ctypes.c_int32),
+                ("sweep_stage_cores", ctypes.c_int32)]
 
 
 class selscan_ihs_out(ctypes.Structure):
@@ -162,11 +163,14 @@ def selscan_default_params(**overrides) -> selscan_params:
 def make_launch(schedule: int = SCHED_IN_ORDER, warps_per_cta: int = 0, ctas_per_sm: int = 0,
                 smem_entries: int = 0, probe_steps: int = 0, window_rows: int = 0,
                 cores_per_fetch: int = 0, min_ctas_per_sm: int = 0, big_group_entries: int = 0,
+                sweep_warmup: int = 0, sweep_stage_cores: int = 0,
                 events=None) -> selscan_launch:
     """events: optional (begin, end) torch.cuda.Event pair bracketing the walk kernels."""
     L = selscan_launch(schedule, warps_per_cta, ctas_per_sm, smem_entries, probe_steps,
                        window_rows, cores_per_fetch, min_ctas_per_sm)
     L.big_group_entries = big_group_entries
+    L.sweep_warmup = sweep_warmup
+    L.sweep_stage_cores = sweep_stage_cores
     if events is not None:
         L.walk_begin_event = ctypes.c_void_p(events[0].cuda_event)
         L.walk_end_event = ctypes.c_void_p(events[1].cuda_event)

@@ -21,8 +21,18 @@ constexpr int kDefaultBigGroup = 32;
 constexpr int kMaxHaplotypes = 65000;
 constexpr size_t kMaxSmemPerCta = 227 * 1024;
 
+struct SweepPlan {
+    int nch, L, R, nstages;
+    long long B;
+    size_t state_bytes, slot_bytes;
+    int split_bytes;
+    int walk_ctas;
+    size_t wscratch_bytes;    // per split-walk warp
+};
+
 struct Plan {
     int schedule;
+    SweepPlan sw;
     int wpc;            // warps per CTA of the walk kernel
     int ctas;           // persistent grid size
     int nslots;         // global scratch slices (warps)
@@ -42,11 +52,47 @@ bool params_ok(const selscan_params *p)
            (p->include_crossing_term == 0 || p->include_crossing_term == 1);
 }
 
-Plan make_plan(int mode, long long ld, const selscan_launch *L)
+SweepPlan make_sweep_plan(int n_total, long long m, int mode, const selscan_launch *L)
+{
+    SweepPlan w;
+    w.L = (L && L->sweep_warmup > 0) ? L->sweep_warmup : 1024;
+    if (w.L < 16) w.L = 16;
+    if (w.L > 16384) w.L = 16384;
+    w.R = (L && L->sweep_stage_cores > 0) ? L->sweep_stage_cores : 64;
+    if (w.R > 4096) w.R = 4096;
+    // chunks: about one per SM, each at least as long as its warm-up
+    const long long per = w.L > 256 ? w.L : 256;
+    long long nch = (m + per - 1) / per;
+    const int sms = device_sms();
+    if (nch > sms) nch = sms;
+    if (nch < 1) nch = 1;
+    // run lengths are 16-bit: a chunk plus its warm-up stays below 65,000 markers
+    const long long maxB = 65000 - w.L;
+    if ((m + nch - 1) / nch > maxB) nch = (m + maxB - 1) / maxB;
+    w.nch = (int)nch;
+    w.B = (m + nch - 1) / nch;
+    w.nstages = (int)((w.B + w.R - 1) / w.R);
+    const int xp = mode == SELSCAN_MODE_XPEHH;
+    w.state_bytes = sweep_state_bytes(n_total);
+    w.slot_bytes = sweep_slot_bytes(n_total, xp);
+    w.split_bytes = (int)split_smem_per_warp(n_total, xp);
+    w.walk_ctas = split_walk_ctas(n_total, xp);
+    w.wscratch_bytes = split_scratch_per_warp(n_total);
+    return w;
+}
+
+Plan make_plan(int mode, long long ld, const selscan_launch *L, int n_total = 0, long long m = 0)
 {
     Plan p;
     p.schedule = L ? L->schedule : SELSCAN_SCHED_IN_ORDER;
-    if (p.schedule < 0 || p.schedule > SELSCAN_SCHED_PLAIN) p.schedule = -1;
+    if (p.schedule < 0 || p.schedule > SELSCAN_SCHED_SWEEP) p.schedule = -1;
+    memset(&p.sw, 0, sizeof(p.sw));
+    if (p.schedule == SELSCAN_SCHED_SWEEP) {
+        if (mode == SELSCAN_MODE_EHH || n_total > kSweepMaxN || n_total < 2 || m < 1)
+            p.schedule = SELSCAN_SCHED_IN_ORDER;
+        else
+            p.sw = make_sweep_plan(n_total, m, mode, L);
+    }
     p.cap_s = (L && L->smem_entries > 0) ? L->smem_entries : kDefaultSmemEntries;
     if (p.cap_s > 8192) p.cap_s = 8192;
     p.cap_s = (p.cap_s + 31) & ~31;
@@ -79,7 +125,9 @@ Plan make_plan(int mode, long long ld, const selscan_launch *L)
     p.wpc = (L && L->warps_per_cta > 0) ? L->warps_per_cta : kDefaultWarpsPerCta;
     if (p.wpc > 8) p.wpc = 8;
     const size_t smem = smem_per_warp(p.cap_s, p.tcap_s, p.rowcap, p.poscap) * (size_t)p.wpc;
-    int per_sm = max_ctas_per_sm(p.schedule, p.wpc, smem, p.minb);
+    // the sweep schedule's second pass is an in-order persistent launch
+    const int psched = p.schedule == SELSCAN_SCHED_SWEEP ? SELSCAN_SCHED_IN_ORDER : p.schedule;
+    int per_sm = max_ctas_per_sm(psched, p.wpc, smem, p.minb);
     if (per_sm < 1) per_sm = 64 / p.wpc > 0 ? 64 / p.wpc : 1;
     int want = (L && L->ctas_per_sm > 0) ? L->ctas_per_sm : per_sm;
     if (want > per_sm) want = per_sm;
@@ -91,9 +139,10 @@ Plan make_plan(int mode, long long ld, const selscan_launch *L)
 struct Layout {
     size_t queue, slotmap, item_status, item_ihh, list2, key2, sorted2, bucket, scratch, total;
     size_t per_warp;
+    size_t sweep_state, sweep_slots, sweep_head, sweep_wscratch;
 };
 
-Layout make_layout(int n_total, long long m, int mode, int nslots)
+Layout make_layout(int n_total, long long m, int mode, int nslots, const SweepPlan *sw = nullptr)
 {
     Layout l;
     const long long items = mode == SELSCAN_MODE_EHH ? 0 : m * (mode == SELSCAN_MODE_XPEHH ? 2 : 4);
@@ -108,6 +157,13 @@ Layout make_layout(int n_total, long long m, int mode, int nslots)
     l.bucket = o;       o += up256((NBUCKET + 1) * 4);
     l.per_warp = scratch_per_warp(n_total);
     l.scratch = o;      o += (size_t)nslots * l.per_warp;
+    l.sweep_state = l.sweep_slots = l.sweep_head = l.sweep_wscratch = 0;
+    if (sw && sw->nch > 0) {
+        l.sweep_head = o;     o += 256;
+        l.sweep_state = o;    o += up256((size_t)2 * sw->nch * sw->state_bytes);
+        l.sweep_slots = o;    o += up256((size_t)2 * sw->nch * sw->R * sw->slot_bytes);
+        l.sweep_wscratch = o; o += (size_t)sw->walk_ctas * kSplitWarps * sw->wscratch_bytes;
+    }
     l.total = o;
     return l;
 }
@@ -163,11 +219,15 @@ int run_scan(int mode, const uint64_t *hap, int64_t ld, int32_t nA, int32_t nB, 
              void *stream)
 {
     const int n_total = nA + nB;
-    const Plan plan = make_plan(mode, ld, launch);
+    const Plan plan = make_plan(mode, ld, launch, n_total, m);
     if (plan.schedule < 0 || (launch && launch->warps_per_cta < 0)) return SELSCAN_ERR_INVALID_ARG;
     if (smem_per_warp(plan.cap_s, plan.tcap_s, plan.rowcap, plan.poscap) * (size_t)plan.wpc > kMaxSmemPerCta)
         return SELSCAN_ERR_UNSUPPORTED;
-    const Layout l = make_layout(n_total, m, mode, plan.nslots);
+    const bool sweep = plan.schedule == SELSCAN_SCHED_SWEEP;
+    if (sweep && (sweep_smem_bytes(n_total, (nA + 63) / 64 + (nB + 63) / 64) > kMaxSmemPerCta ||
+                  (size_t)plan.sw.split_bytes * kSplitWarps > kMaxSmemPerCta))
+        return SELSCAN_ERR_UNSUPPORTED;
+    const Layout l = make_layout(n_total, m, mode, plan.nslots, sweep ? &plan.sw : nullptr);
     if (!workspace || ws_bytes < l.total || ((uintptr_t)workspace & 255)) return SELSCAN_ERR_WORKSPACE;
     cudaStream_t s = (cudaStream_t)stream;
     unsigned char *ws = (unsigned char *)workspace;
@@ -201,9 +261,32 @@ int run_scan(int mode, const uint64_t *hap, int64_t ld, int32_t nA, int32_t nB, 
     if (launch && launch->walk_begin_event &&
         cudaEventRecord((cudaEvent_t)launch->walk_begin_event, s) != cudaSuccess)
         return SELSCAN_ERR_CUDA;
-    if (launch_walk(a, sk, sc, plan.schedule, plan.wpc, ctas_or_slots, plan.probe, plan.fetch, plan.minb,
-                    m, s) != cudaSuccess)
+    if (sweep) {
+        SweepArgs w;
+        w.a = a;
+        w.sk = sk;
+        w.n = n_total;
+        w.nch = plan.sw.nch;
+        w.B = plan.sw.B;
+        w.L = plan.sw.L;
+        w.R = plan.sw.R;
+        w.stage = 0;
+        w.nstages = plan.sw.nstages;
+        w.st = (unsigned short *)(ws + l.sweep_state);
+        w.slots = ws + l.sweep_slots;
+        w.slot_bytes = plan.sw.slot_bytes;
+        w.split_bytes = plan.sw.split_bytes;
+        w.wscratch = ws + l.sweep_wscratch;
+        w.wscratch_bytes = plan.sw.wscratch_bytes;
+        w.walk_ctas = plan.sw.walk_ctas;
+        w.walk_head = (unsigned long long *)(ws + l.sweep_head);
+        if (launch_sweep_path(w, s) != cudaSuccess) return SELSCAN_ERR_CUDA;
+        if (launch_pass2(a, sk, sc, plan.wpc, plan.ctas, plan.minb, s) != cudaSuccess)
+            return SELSCAN_ERR_CUDA;
+    } else if (launch_walk(a, sk, sc, plan.schedule, plan.wpc, ctas_or_slots, plan.probe, plan.fetch,
+                           plan.minb, m, s) != cudaSuccess) {
         return SELSCAN_ERR_CUDA;
+    }
     if (launch && launch->walk_end_event &&
         cudaEventRecord((cudaEvent_t)launch->walk_end_event, s) != cudaSuccess)
         return SELSCAN_ERR_CUDA;
@@ -236,9 +319,10 @@ size_t selscan_workspace_bytes(int32_t n_total, int64_t m, int32_t mode, const s
     if (n_total < 2 || m < 1 || mode < 0 || mode > 2) return 0;
     // scratch slots for the most warps an SM can hold (64), so the size does
     // not depend on the row stride, registers or shared memory of the call
-    const Plan p = make_plan(mode, (n_total + 63) / 64, launch);
+    const Plan p = make_plan(mode, (n_total + 63) / 64, launch, n_total, m);
     const int nslots = mode == SELSCAN_MODE_EHH ? p.nslots : device_sms() * 64;
-    return make_layout(n_total, m, mode, nslots).total;
+    return make_layout(n_total, m, mode, nslots,
+                       p.schedule == SELSCAN_SCHED_SWEEP ? &p.sw : nullptr).total;
 }
 
 int selscan_ihs(const uint64_t *hap, int64_t ld, int32_t n, int64_t m, const int64_t *pos_bp,

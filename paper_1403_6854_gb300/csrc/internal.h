@@ -96,4 +96,40 @@ cudaError_t launch_pack(const uint8_t *hap01, int n, long long m, int hap_major,
                         unsigned long long *rows, long long ld, cudaStream_t s);
 int max_ctas_per_sm(int schedule, int warps_per_cta, size_t smem_bytes, int minb);
 
+// Second pass of the per-step walk over the items queued in sink.list2.
+cudaError_t launch_pass2(const ScanArgs &a, const ItemSink &sink, const Scratch &sc,
+                         int warps_per_cta, int ctas, int minb, cudaStream_t s);
+
+// ---- sorted-sweep walks (sweep.cu)
+constexpr int kSweepThreads = 512;   // threads of one sweep CTA
+constexpr int kSplitWarps = 8;       // warps of one split-walk CTA
+constexpr int kSweepMaxN = 16383;    // haplotypes the sweep keeps on chip (14-bit counts)
+
+struct SweepArgs {
+    ScanArgs a;
+    ItemSink sk;
+    int n;                   // haplotypes sorted (iHS: n; XPEHH: n_A + n_B)
+    int nch;                 // chunks of cores per direction
+    long long B;             // cores per chunk
+    int L;                   // markers swept before a chunk's first core
+    int R;                   // cores per chunk and stage
+    int stage, nstages;
+    unsigned short *st;      // per chunk and direction: sorted order, run lengths
+    unsigned char *slots;    // [2][nch][R] slots of slot_bytes
+    size_t slot_bytes;
+    int split_bytes;         // shared memory of one split-walk warp
+    unsigned char *wscratch; // per split-walk warp: window staging and step lists
+    size_t wscratch_bytes;
+    int walk_ctas;           // persistent split-walk grid
+    unsigned long long *walk_head;   // slot counter of the current walk launch
+};
+
+size_t sweep_smem_bytes(int n, int W);
+size_t sweep_slot_bytes(int n, int xpehh);
+size_t sweep_state_bytes(int n);
+size_t split_smem_per_warp(int n, int xpehh);
+size_t split_scratch_per_warp(int n);
+int split_walk_ctas(int n, int xpehh);
+cudaError_t launch_sweep_path(const SweepArgs &w, cudaStream_t s);
+
 }  // namespace selscan

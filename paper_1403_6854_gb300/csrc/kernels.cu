@@ -293,6 +293,34 @@ static cudaError_t walk_impl(const ScanArgs &a, const ItemSink &sk, const Scratc
     return persistent_impl<NPOP, 2>(a, sk, sc, schedule, wpc, ctas, probe, fetch, n_cores, s);
 }
 
+template <int NPOP, int MINB>
+static cudaError_t pass2_impl(const ScanArgs &a, const ItemSink &sk, const Scratch &sc, int wpc,
+                              int ctas, cudaStream_t s)
+{
+    const size_t smem = slice_bytes(sc) * (size_t)wpc;
+    cudaError_t e = cudaFuncSetAttribute(walk_persistent_kernel<NPOP, MINB>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(walk_persistent_kernel<NPOP, MINB>,
+                             cudaFuncAttributePreferredSharedMemoryCarveout, carveout_pct(smem, ctas));
+    if (e != cudaSuccess) return e;
+    bucket_hist_kernel<<<2 * sm_count(), 256, 0, s>>>(sk);
+    bucket_scan_kernel<<<1, NBUCKET, 0, s>>>(sk);
+    bucket_scatter_kernel<<<2 * sm_count(), 256, 0, s>>>(sk);
+    walk_persistent_kernel<NPOP, MINB><<<ctas, wpc * 32, smem, s>>>(a, sk, sc, 0, 2, 0, 1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pass2(const ScanArgs &a, const ItemSink &sink, const Scratch &sc,
+                         int warps_per_cta, int ctas, int minb, cudaStream_t s)
+{
+    if (sink.mode == 1)
+        return minb == 3 ? pass2_impl<2, 3>(a, sink, sc, warps_per_cta, ctas, s)
+                         : pass2_impl<2, 2>(a, sink, sc, warps_per_cta, ctas, s);
+    return minb == 3 ? pass2_impl<1, 3>(a, sink, sc, warps_per_cta, ctas, s)
+                     : pass2_impl<1, 2>(a, sink, sc, warps_per_cta, ctas, s);
+}
+
 cudaError_t launch_walk(const ScanArgs &a, const ItemSink &sink, const Scratch &sc,
                         int schedule, int warps_per_cta, int ctas, int probe_steps, int fetch,
                         int minb, long long n_cores, cudaStream_t s)

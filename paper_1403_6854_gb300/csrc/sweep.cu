@@ -1,0 +1,789 @@
+// Sorted-sweep form of the EHH walks (iHS Eq. 3-5, XPEHH Eq. 6-7).
+//
+// Every statistic of a walk is a function of S(i), the number of pairs of the
+// walk's sample that are identical over the markers between the core and
+// x_i (Section 1.2: EHH(x_i) = S(i) / C(N, 2)).  If the haplotypes are kept
+// sorted by their sequence read outward from the core (the prefix order of a
+// positional Burrows-Wheeler sweep), the haplotypes identical over
+// [core, x_i] are contiguous runs of that order, and two neighbours t-1, t
+// part at the first marker where they differ, i.e. at walk step M[t] = the
+// length of their common run ending at the core.  So S(0) = C(n_c, 2) per
+// core class, and step i only has to apply the boundaries t with M[t] = i:
+// splitting a run [l, r) at t lowers S by (t - l)(r - t).  The cost of a walk
+// becomes the number of boundaries it crosses, not the number of groups it
+// carries at every step.
+//
+// Two kernels per stage:
+//  * sweep_kernel: one CTA per chunk of cores and direction keeps the order A
+//    and the run lengths M of all haplotypes in shared memory and advances them
+//    marker by marker (a stable partition by allele; the new run length of a
+//    neighbour pair is 1 + the minimum over the old pairs it spans).  At every
+//    core of the stage it writes M, the class boundary n0 (and, for XPEHH, the
+//    population of each sorted position) to a slot.  A chunk starts `warmup`
+//    markers before its first core, so its sort is exact for walks that stay
+//    within that history.
+//  * split_walk_kernel: one warp per slot runs the walk steps of that core
+//    (both allele classes of iHS, or the pooled XPEHH walk): gaps, the map,
+//    the cutoff and the trapezoid exactly as the per-step walk does, with S(i)
+//    from the boundaries of step i.  A walk that would step beyond its
+//    chunk's history is handed to the per-step walk kernel (second pass).
+#include <limits.h>
+
+#include "../../include/selscan.h"
+#include "device_common.cuh"
+#include "internal.h"
+
+namespace selscan {
+
+namespace {
+
+constexpr unsigned kInf16 = 0xFFFFu;
+
+__host__ __device__ inline int sweep_e(int n)
+{
+    int e = (n + kSweepThreads - 1) / kSweepThreads;
+    return (e + 1) & ~1;                    // even: elements are read in pairs
+}
+__host__ __device__ inline int sweep_npad(int n) { return sweep_e(n) * kSweepThreads; }
+__host__ __device__ inline int split_nw(int n) { return (n + 32) >> 5; }   // bits 0..n
+
+// ---- prefix-state algebra of the stable partition --------------------------
+// A segment of the current order summarised as: minimum run length over the
+// segment, the running minimum since the last allele-0 / allele-1 element
+// (or the whole-segment minimum if the segment has none), the number of
+// allele-0 elements, and whether each allele occurs.  Packed in two words:
+// p0 = min_all | tail0 << 16; p1 = tail1 | zeros << 16 | seen0 << 30 | seen1 << 31.
+__device__ __forceinline__ void compose(unsigned l0, unsigned l1, unsigned &r0, unsigned &r1)
+{
+    const unsigned lall = l0 & 0xFFFFu, lt0 = l0 >> 16, lt1 = l1 & 0xFFFFu;
+    const unsigned rall = r0 & 0xFFFFu, rt0 = r0 >> 16, rt1 = r1 & 0xFFFFu;
+    const unsigned all = min(lall, rall);
+    const unsigned t0 = (r1 >> 30) & 1u ? rt0 : min(lt0, rall);
+    const unsigned t1 = (r1 >> 31) ? rt1 : min(lt1, rall);
+    const unsigned zeros = ((l1 >> 16) & 0x3FFFu) + ((r1 >> 16) & 0x3FFFu);
+    const unsigned flags = (l1 | r1) & 0xC0000000u;
+    r0 = all | (t0 << 16);
+    r1 = t1 | (zeros << 16) | flags;
+}
+constexpr unsigned kId0 = 0xFFFFFFFFu;
+constexpr unsigned kId1 = 0x0000FFFFu;
+
+__device__ __forceinline__ unsigned bit_index(const SweepArgs &w, int h)
+{
+    // position of haplotype h (pooled numbering, A first) in the row's bits
+    return h < w.a.nA ? (unsigned)h : (unsigned)(64 * w.a.WA + (h - w.a.nA));
+}
+
+}  // namespace
+
+size_t sweep_smem_bytes(int n, int W)
+{
+    const int W32 = ((2 * W) + 3) & ~3;
+    return (size_t)sweep_npad(n) * 4 * 2 + (size_t)W32 * 4 * 2 + kSweepThreads / 32 * 8;
+}
+
+size_t sweep_slot_bytes(int n, int xpehh)
+{
+    size_t b = 16 + (((size_t)n * 2 + 15) & ~(size_t)15);
+    if (xpehh) b += ((size_t)split_nw(n) * 4 + 15) & ~(size_t)15;
+    return b;
+}
+
+size_t sweep_state_bytes(int n) { return (size_t)sweep_npad(n) * 4; }
+
+
+// ---- the sweep ---------------------------------------------------------------
+// Shared memory: two buffers of np packed elements (bit index of the haplotype
+// in the row | run length with its predecessor << 16), two row buffers, the
+// warp totals.  EMAX bounds the elements per thread; up to 16 stay in
+// registers between the two passes.
+template <int EMAX>
+__global__ void __launch_bounds__(kSweepThreads, 2) sweep_kernel(SweepArgs w)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    constexpr bool CACHE = EMAX <= 16;
+    const int n = w.n;
+    const int E = sweep_e(n);
+    const int np = E * kSweepThreads;
+    const int W32 = 2 * w.a.W;
+    const int W32r = (W32 + 3) & ~3;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int NW = kSweepThreads / 32;
+    unsigned *P0 = (unsigned *)smem;             // buffer b at P0 + b * np
+    unsigned *R0 = P0 + 2 * np;                  // row buffer r at R0 + r * W32r
+    unsigned *wsum = R0 + 2 * W32r;
+
+    const int dir = blockIdx.x / w.nch;          // 0: walks toward lower indices
+    const int c = blockIdx.x % w.nch;
+    const long long m = w.a.m;
+    const long long c0 = (long long)c * w.B;
+    if (c0 >= m) return;
+    const long long c1 = c0 + w.B < m ? c0 + w.B : m;
+    long long klo, khi;                          // this stage's cores [klo, khi)
+    if (dir == 0) {
+        klo = c0 + (long long)w.stage * w.R;
+        khi = klo + w.R < c1 ? klo + w.R : c1;
+        if (klo >= c1) return;
+    } else {
+        khi = c1 - (long long)w.stage * w.R;
+        klo = khi - w.R > c0 ? khi - w.R : c0;
+        if (khi <= c0) return;
+    }
+    // history origin of the chunk: the sort is exact for runs inside it
+    const long long s0 = c0 - w.L > 0 ? c0 - w.L : 0;
+    const long long e0 = c1 - 1 + w.L < m - 1 ? c1 - 1 + w.L : m - 1;
+    long long xfirst, xlast;                     // markers of this launch, in sweep order
+    if (dir == 0) {
+        xfirst = w.stage == 0 ? s0 : klo;
+        xlast = khi - 1;
+    } else {
+        xfirst = w.stage == 0 ? e0 : khi - 1;
+        xlast = klo;
+    }
+    const long long step = dir == 0 ? 1 : -1;
+    unsigned *st = (unsigned *)w.st + (size_t)blockIdx.x * np;
+
+    if (blockIdx.x == 0 && tid == 0) *w.walk_head = 0ull;   // the next walk launch's slot counter
+    // ---- state in
+    if (w.stage == 0) {
+        for (int t = tid; t < np; t += kSweepThreads) P0[t] = t < n ? bit_index(w, t) : 0u;
+    } else {
+        for (int t = tid; t < np; t += kSweepThreads) P0[t] = st[t];
+    }
+    const unsigned *hap32 = (const unsigned *)w.a.hap;
+    const long long ld32 = 2 * w.a.ld;
+    for (int t = tid; t < W32; t += kSweepThreads) R0[t] = hap32[xfirst * ld32 + t];
+    __syncthreads();
+
+    int cur = 0, rb = 0;
+    const int base = tid * E;
+    unsigned val[CACHE ? EMAX : 1];
+    for (long long x = xfirst;; x += step) {
+        const bool more = x != xlast;
+        unsigned rnext = 0u;                     // the next row, loaded while this one is sorted
+        if (more && tid < W32) rnext = __ldg(hap32 + (x + step) * ld32 + tid);
+        const bool is_core = x >= klo && x < khi;
+        int cst = 0;
+        if (is_core) cst = w.sk.core_status[x];
+
+        const unsigned *Pc = P0 + cur * np;
+        const unsigned *row = R0 + rb * W32r;
+        // pass 1: alleles of this thread's elements and the segment summary
+        unsigned vmask = 0u;
+        unsigned all = kInf16, t0 = kInf16, t1 = kInf16, zeros = 0u, seen = 0u;
+#pragma unroll
+        for (int e = 0; e < EMAX; e += 2) {
+            if (e < E && base + e < n) {
+                const uint2 q = *(const uint2 *)(Pc + base + e);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const unsigned pv = h ? q.y : q.x;
+                    if (CACHE) val[e + h] = pv;
+                    if (base + e + h < n) {
+                        const unsigned bi = pv & 0xFFFFu, mv = pv >> 16;
+                        const unsigned v = (row[bi >> 5] >> (bi & 31u)) & 1u;
+                        vmask |= v << (e + h);
+                        all = min(all, mv);
+                        t0 = v ? min(t0, mv) : kInf16;
+                        t1 = v ? kInf16 : min(t1, mv);
+                        zeros += v ^ 1u;
+                        seen |= 1u << v;
+                    }
+                }
+            }
+        }
+        unsigned p0 = all | (t0 << 16);
+        unsigned p1 = t1 | (zeros << 16) | (seen << 30);
+        // warp inclusive scan
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const unsigned o0 = __shfl_up_sync(FULLMASK, p0, d);
+            const unsigned o1 = __shfl_up_sync(FULLMASK, p1, d);
+            if (lane >= d) compose(o0, o1, p0, p1);
+        }
+        unsigned x0 = __shfl_up_sync(FULLMASK, p0, 1), x1 = __shfl_up_sync(FULLMASK, p1, 1);
+        if (lane == 0) { x0 = kId0; x1 = kId1; }
+        if (lane == 31) { wsum[2 * warp] = p0; wsum[2 * warp + 1] = p1; }
+        __syncthreads();
+        // every warp scans the warp totals: its own prefix and the block total
+        unsigned q0 = lane < NW ? wsum[2 * lane] : kId0;
+        unsigned q1 = lane < NW ? wsum[2 * lane + 1] : kId1;
+#pragma unroll
+        for (int d = 1; d < NW; d <<= 1) {
+            const unsigned o0 = __shfl_up_sync(FULLMASK, q0, d);
+            const unsigned o1 = __shfl_up_sync(FULLMASK, q1, d);
+            if (lane >= d) compose(o0, o1, q0, q1);
+        }
+        unsigned w0 = __shfl_sync(FULLMASK, q0, (warp + 31) & 31);
+        unsigned w1 = __shfl_sync(FULLMASK, q1, (warp + 31) & 31);
+        if (warp == 0) { w0 = kId0; w1 = kId1; }
+        const unsigned tot1 = __shfl_sync(FULLMASK, q1, NW - 1);
+        const unsigned n0 = (tot1 >> 16) & 0x3FFFu;
+        compose(w0, w1, x0, x1);                  // this thread's exclusive prefix
+        // pass 2: scatter into the other buffer with the new run lengths
+        unsigned mn0 = x0 >> 16, mn1 = x1 & 0xFFFFu;
+        unsigned hp0 = (x1 >> 30) & 1u, hp1 = x1 >> 31;
+        unsigned z = (x1 >> 16) & 0x3FFFu;
+        unsigned o = n0 + (unsigned)base - z;
+        unsigned *Pn = P0 + (cur ^ 1) * np;
+#pragma unroll
+        for (int e = 0; e < EMAX; ++e) {
+            if (e < E && base + e < n) {
+                const unsigned pv = CACHE ? val[e] : Pc[base + e];
+                const unsigned bi = pv & 0xFFFFu, mv = pv >> 16;
+                mn0 = min(mn0, mv);
+                mn1 = min(mn1, mv);
+                const unsigned one = (vmask >> e) & 1u;
+                const unsigned mn = one ? mn1 : mn0;
+                const unsigned hp = one ? hp1 : hp0;
+                const unsigned out = hp ? min(mn + 1u, kInf16) : 0u;
+                const unsigned p = one ? o : z;
+                o += one;
+                z += one ^ 1u;
+                mn1 = one ? kInf16 : mn1;
+                mn0 = one ? mn0 : kInf16;
+                hp1 |= one;
+                hp0 |= one ^ 1u;
+                Pn[p] = bi | (out << 16);
+            }
+        }
+        if (more && tid < W32) R0[(rb ^ 1) * W32r + tid] = rnext;
+        __syncthreads();
+        cur ^= 1;
+        rb ^= 1;
+
+        // ---- a core of this stage: hand its sorted state to the walk
+        if (is_core && cst != (int)SELSCAN_LOCUS_MAF_FILTERED) {
+            const int r = dir == 0 ? (int)(x - klo) : (int)(khi - 1 - x);
+            unsigned char *slot = w.slots + ((size_t)(dir * w.nch + c) * w.R + r) * w.slot_bytes;
+            if (tid == 0) {
+                int *hdr = (int *)slot;
+                hdr[0] = (int)n0;
+                long long hz;
+                if (dir == 0) hz = s0 == 0 ? INT_MAX : x - s0;
+                else hz = e0 == m - 1 ? INT_MAX : e0 - x;
+                hdr[1] = (int)hz;
+            }
+            const unsigned *Ps = P0 + cur * np;
+            unsigned *Md = (unsigned *)(slot + 16);
+            for (int t = tid; t < (n + 1) / 2; t += kSweepThreads) {
+                const uint2 q = *(const uint2 *)(Ps + 2 * t);
+                Md[t] = (q.x >> 16) | (q.y & 0xFFFF0000u);
+            }
+            if (w.a.nB > 0) {                    // population of each sorted position
+                const unsigned limA = 64u * (unsigned)w.a.WA;
+                unsigned *isA = (unsigned *)(slot + 16 + (((size_t)n * 2 + 15) & ~(size_t)15));
+                const int nw = split_nw(n);
+                for (int q = tid; q < nw; q += kSweepThreads) {
+                    unsigned word = 0u;
+                    for (int b = 0; b < 32; ++b) {
+                        const int t = q * 32 + b;
+                        if (t < n && (Ps[t] & 0xFFFFu) < limA) word |= 1u << b;
+                    }
+                    isA[q] = word;
+                }
+            }
+        }
+        if (!more) break;
+    }
+    // ---- state out for the next stage
+    if (w.stage + 1 < w.nstages) {
+        const unsigned *Ps = P0 + cur * np;
+        for (int t = tid; t < np; t += kSweepThreads) st[t] = Ps[t];
+    }
+}
+
+// ---- the split walk ----------------------------------------------------------
+namespace {
+
+// Per-warp shared memory: run starts before this step (O) and set at this
+// step (N) as bitmaps over positions 0..n, one summary bit per non-zero
+// word (SO, SN), step counts / offsets of the current 64-step window, and
+// for XPEHH the population-A flags of the sorted positions with their
+// per-word prefix counts.
+struct SplitSmem {
+    unsigned *O, *N, *SO, *SN;
+    unsigned *cnt, *off;
+    unsigned *isA, *PA;
+    int nw, ns;
+};
+
+__device__ inline SplitSmem split_smem(unsigned char *base, int n, int xpehh)
+{
+    SplitSmem s;
+    s.nw = split_nw(n);
+    s.ns = (s.nw + 31) >> 5;
+    unsigned *p = (unsigned *)base;
+    s.O = p; p += s.nw;
+    s.N = p; p += s.nw;
+    s.SO = p; p += s.ns;
+    s.SN = p; p += s.ns;
+    s.cnt = p; p += 64;
+    s.off = p; p += 65;
+    s.isA = xpehh ? p : nullptr;
+    s.PA = xpehh ? p + s.nw : nullptr;
+    return s;
+}
+
+__device__ __forceinline__ unsigned long long c2(unsigned long long k) { return k * (k - 1ull) / 2ull; }
+__device__ __forceinline__ int c2i(unsigned k) { return (int)(k * (k - 1u) / 2u); }
+
+// last set position < b in O (| N)
+template <bool WITH_N>
+__device__ __forceinline__ int prev_set(const SplitSmem &s, int b)
+{
+    const int wd = b >> 5;
+    unsigned bits = s.O[wd] | (WITH_N ? s.N[wd] : 0u);
+    bits &= (1u << (b & 31)) - 1u;
+    if (bits) return (wd << 5) + 31 - __clz(bits);
+    for (int sw = wd - 1; sw >= 0;) {
+        const int q = sw >> 5;
+        unsigned sb = s.SO[q] | (WITH_N ? s.SN[q] : 0u);
+        sb &= 0xFFFFFFFFu >> (31 - (sw & 31));
+        if (sb) {
+            const int ww = (q << 5) + 31 - __clz(sb);
+            const unsigned word = s.O[ww] | (WITH_N ? s.N[ww] : 0u);
+            return (ww << 5) + 31 - __clz(word);
+        }
+        sw = (q << 5) - 1;
+    }
+    return 0;                         // position 0 is always set
+}
+
+// first set position > b in O (| N)
+template <bool WITH_N>
+__device__ __forceinline__ int next_set(const SplitSmem &s, int b, int n)
+{
+    const int wd = b >> 5;
+    unsigned bits = s.O[wd] | (WITH_N ? s.N[wd] : 0u);
+    bits &= ~((2u << (b & 31)) - 1u);
+    if (bits) return (wd << 5) + __ffs(bits) - 1;
+    for (int sw = wd + 1; sw < s.nw;) {
+        const int q = sw >> 5;
+        unsigned sb = s.SO[q] | (WITH_N ? s.SN[q] : 0u);
+        sb &= 0xFFFFFFFFu << (sw & 31);
+        if (sb) {
+            const int ww = (q << 5) + __ffs(sb) - 1;
+            const unsigned word = s.O[ww] | (WITH_N ? s.N[ww] : 0u);
+            return (ww << 5) + __ffs(word) - 1;
+        }
+        sw = (q + 1) << 5;
+    }
+    return n;                         // position n is always set
+}
+
+__device__ __forceinline__ unsigned count_a(const SplitSmem &s, int x)
+{
+    return s.PA[x >> 5] + (unsigned)__popc(s.isA[x >> 5] & ((1u << (x & 31)) - 1u));
+}
+
+// Group the boundaries t with lo <= M[t] < lo + 64 by step: one pass over M
+// (8 values per 16-byte load, four loads in flight per lane) collects them
+// with their rank inside their step, then they are placed by step.
+__device__ void build_window(const SplitSmem &s, const unsigned *M32, int n, int lo,
+                             unsigned long long *stage, unsigned short *list)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned ltm = (1u << lane) - 1u;
+    const uint4 *M4 = (const uint4 *)M32;
+    for (int q = lane; q < 64; q += 32) s.cnt[q] = 0u;
+    __syncwarp();
+    const int n4 = (n + 7) >> 3;
+    unsigned K = 0;
+    for (int base = 0; base < n4; base += 128) {
+        uint4 q[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int idx = base + u * 32 + lane;
+            q[u] = idx < n4 ? __ldg(M4 + idx) : make_uint4(~0u, ~0u, ~0u, ~0u);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int t0 = (base + u * 32 + lane) * 8;
+            const unsigned wv[4] = {q[u].x, q[u].y, q[u].z, q[u].w};
+#pragma unroll
+            for (int h = 0; h < 8; ++h) {
+                const int t = t0 + h;
+                const unsigned d = ((h & 1) ? (wv[h >> 1] >> 16) : (wv[h >> 1] & 0xFFFFu)) - (unsigned)lo;
+                const bool in = t < n && d < 64u;
+                const unsigned bal = __ballot_sync(FULLMASK, in);
+                if (in) {
+                    const unsigned r = atomicAdd(s.cnt + d, 1u);
+                    stage[K + __popc(bal & ltm)] =
+                        (unsigned long long)t | ((unsigned long long)d << 16) | ((unsigned long long)r << 32);
+                }
+                K += __popc(bal);
+            }
+        }
+    }
+    __syncwarp();
+    const unsigned a = s.cnt[2 * lane], b = s.cnt[2 * lane + 1];
+    unsigned incl = a + b;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const unsigned v = __shfl_up_sync(FULLMASK, incl, d);
+        if (lane >= d) incl += v;
+    }
+    const unsigned excl = incl - a - b;
+    s.off[2 * lane] = excl;
+    s.off[2 * lane + 1] = excl + a;
+    if (lane == 31) s.off[64] = incl;
+    __syncwarp();
+    for (unsigned j = lane; j < K; j += 32) {
+        const unsigned long long e = stage[j];
+        list[s.off[(unsigned)(e >> 16) & 63u] + (unsigned)(e >> 32)] = (unsigned short)(e & 0xFFFFu);
+    }
+    __syncwarp();
+}
+
+struct ClassWalk {
+    unsigned long long D, S, prev, dig;
+    double acc;
+    int status, stop;
+    bool active;
+};
+
+// Reductions of S caused by the boundaries b that part at this step
+// (iHS: d0 class 0, d1 class 1; XPEHH: d0 A, d1 B, d2 pooled).
+template <int NPOP>
+__device__ __forceinline__ void split_terms(const SplitSmem &s, int b, int n, int n0, int &d0,
+                                            int &d1, int &d2)
+{
+    const int p = prev_set<true>(s, b);
+    const int rr = next_set<true>(s, b, n);
+    const bool old = (s.O[p >> 5] >> (p & 31)) & 1u;
+    const int e = old ? next_set<false>(s, b, n) : 0;
+    if (NPOP == 2) {
+        const unsigned ab = count_a(s, b), ar = count_a(s, rr);
+        const unsigned la = ar - ab, lb = (unsigned)(rr - b) - la;
+        d0 += c2i(la);
+        d1 += c2i(lb);
+        d2 += c2i((unsigned)(rr - b));
+        if (old) {
+            const unsigned ap = count_a(s, p), ae = count_a(s, e);
+            const unsigned l1a = ab - ap, l1b = (unsigned)(b - p) - l1a;
+            const unsigned l2a = ae - ap, l2b = (unsigned)(e - p) - l2a;
+            d0 += c2i(l1a) - c2i(l2a);
+            d1 += c2i(l1b) - c2i(l2b);
+            d2 += c2i((unsigned)(b - p)) - c2i((unsigned)(e - p));
+        }
+    } else {
+        int dd = c2i((unsigned)(rr - b));
+        if (old) dd += c2i((unsigned)(b - p)) - c2i((unsigned)(e - p));
+        if (b < n0) d0 += dd;
+        else d1 += dd;
+    }
+}
+
+}  // namespace
+
+size_t split_smem_per_warp(int n, int xpehh)
+{
+    const int nw = split_nw(n), ns = (nw + 31) >> 5;
+    size_t b = (size_t)nw * 4 * 2 + (size_t)ns * 4 * 2 + 64 * 4 + 65 * 4;
+    if (xpehh) b += (size_t)nw * 4 * 2;
+    return (b + 15) & ~(size_t)15;
+}
+
+size_t split_scratch_per_warp(int n) { return (((size_t)n * 10) + 255) & ~(size_t)255; }
+
+// Persistent: each warp takes slots of this stage (both directions) from a
+// counter and walks the cores in them.
+template <int NPOP>
+__global__ void __launch_bounds__(kSplitWarps * 32, 4) split_walk_kernel(SweepArgs w)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int n = w.n;
+    SplitSmem s = split_smem(smem + (size_t)warp * w.split_bytes, n, NPOP == 2);
+    unsigned char *scr = w.wscratch + ((size_t)blockIdx.x * kSplitWarps + warp) * w.wscratch_bytes;
+    unsigned long long *stage = (unsigned long long *)scr;
+    unsigned short *list = (unsigned short *)(scr + (size_t)n * 8);
+    const long long per_dir = (long long)w.nch * w.R;
+    const long long m = w.a.m;
+    for (;;) {
+        unsigned long long gs = 0;
+        if (lane == 0) gs = atomicAdd(w.walk_head, 1ull);
+        gs = __shfl_sync(FULLMASK, gs, 0);
+        if (gs >= (unsigned long long)(2 * per_dir)) break;
+        const long long gslot = (long long)gs;
+        const int dir = (int)(gslot / per_dir);
+        const int c = (int)((gslot / w.R) % w.nch);
+        const int r = (int)(gslot % w.R);
+        const long long c0 = (long long)c * w.B;
+        if (c0 >= m) continue;
+        const long long c1 = c0 + w.B < m ? c0 + w.B : m;
+        long long k;
+        if (dir == 0) {
+            const long long klo = c0 + (long long)w.stage * w.R;
+            const long long khi = klo + w.R < c1 ? klo + w.R : c1;
+            k = klo + r;
+            if (k >= khi) continue;
+        } else {
+            const long long khi = c1 - (long long)w.stage * w.R;
+            const long long klo = khi - w.R > c0 ? khi - w.R : c0;
+            k = khi - 1 - r;
+            if (k < klo) continue;
+        }
+        if (w.sk.core_status[k] == (int8_t)SELSCAN_LOCUS_MAF_FILTERED) continue;
+
+        const unsigned char *slot = w.slots + (size_t)gslot * w.slot_bytes;
+        const int n0 = ((const int *)slot)[0];
+        const int hz = ((const int *)slot)[1];
+        const unsigned *M32 = (const unsigned *)(slot + 16);
+
+        for (int q = lane; q < s.nw; q += 32) { s.O[q] = 0u; s.N[q] = 0u; }
+        for (int q = lane; q < s.ns; q += 32) { s.SO[q] = 0u; s.SN[q] = 0u; }
+        if (NPOP == 2) {
+            const unsigned *isA = (const unsigned *)(slot + 16 + (((size_t)n * 2 + 15) & ~(size_t)15));
+            unsigned carry = 0u;
+            for (int base = 0; base < s.nw; base += 32) {
+                const int q = base + lane;
+                const unsigned v = q < s.nw ? __ldg(isA + q) : 0u;
+                const unsigned pc = (unsigned)__popc(v);
+                unsigned incl = pc;
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    const unsigned u = __shfl_up_sync(FULLMASK, incl, d);
+                    if (lane >= d) incl += u;
+                }
+                if (q < s.nw) { s.isA[q] = v; s.PA[q] = carry + incl - pc; }
+                carry += __shfl_sync(FULLMASK, incl, 31);
+            }
+        }
+        __syncwarp();
+        if (lane < 3) {                           // run starts before step 1: 0, n0, n
+            const int mk = lane == 0 ? 0 : (lane == 1 ? n0 : n);
+            atomicOr(s.O + (mk >> 5), 1u << (mk & 31));
+            atomicOr(s.SO + (mk >> 10), 1u << ((mk >> 5) & 31));
+        }
+        __syncwarp();
+
+        // ---- step 0 (the core marker splits the sample into its allele classes)
+        constexpr int NWK = NPOP == 2 ? 1 : 2;    // walks handled by this warp
+        ClassWalk cw[NWK];
+        unsigned long long SA = 0, SB = 0, pA = 0, pB = 0, dA = 0, dB = 0, DA = 0, DB = 0;
+        double accB = 0.0;
+        if (NPOP == 2) {
+            const unsigned nA = (unsigned)w.a.nA, nB = (unsigned)w.a.nB;
+            const unsigned a0 = count_a(s, n0), a1 = nA - a0;
+            const unsigned b0 = (unsigned)n0 - a0, b1 = nB - b0;
+            SA = c2(a0) + c2(a1);
+            SB = c2(b0) + c2(b1);
+            DA = c2(nA);
+            DB = c2(nB);
+            cw[0].D = c2((unsigned long long)n);
+            cw[0].S = c2((unsigned long long)n0) + c2((unsigned long long)(n - n0));
+            pA = SA; pB = SB;
+            dA = SA; dB = SB;
+        } else {
+            cw[0].D = c2((unsigned long long)n0);              // allele 0: positions [0, n0)
+            cw[1].D = c2((unsigned long long)(n - n0));        // allele 1: positions [n0, n)
+            cw[0].S = cw[0].D;
+            cw[1].S = cw[1].D;
+        }
+        bool any = false;
+#pragma unroll
+        for (int q = 0; q < NWK; ++q) {
+            cw[q].prev = cw[q].S;
+            cw[q].dig = cw[q].S;
+            cw[q].acc = 0.0;
+            cw[q].stop = 0;
+            cw[q].status = cw[q].D == 0ull ? W_UNDEFINED : W_OK;
+            cw[q].active = cw[q].D != 0ull;
+            any |= cw[q].active;
+        }
+
+        const long long step = dir ? 1 : -1;
+        long long pprev = __ldg(w.a.pos + k);
+        double gprev = __ldg(w.a.gmap + k);
+        long long preg = 0;
+        double greg = 0.0;
+        int lo = 1;
+        if (any) build_window(s, M32, n, lo, stage, list);
+        int fin = W_OK;                           // how the still-active walks end
+        long long i = 1;
+        for (; any; ++i) {
+            const long long x = k + step * i;
+            if (x < 0 || x >= m) { fin = W_EDGE; break; }
+            if (((i - 1) & 31) == 0) {            // positions and map of the next 32 steps
+                const long long xl = x + step * lane;
+                if (xl >= 0 && xl < m) { preg = __ldg(w.a.pos + xl); greg = __ldg(w.a.gmap + xl); }
+            }
+            const long long px = __shfl_sync(FULLMASK, preg, (int)((i - 1) & 31));
+            const double gx = __shfl_sync(FULLMASK, greg, (int)((i - 1) & 31));
+            const long long bp = dir ? px - pprev : pprev - px;
+            if (bp > w.a.max_gap) { fin = W_GAP; break; }
+            double g = dir ? gx - gprev : gprev - gx;
+            if (bp > w.a.gap_scale) g = g * ((double)w.a.gap_scale / (double)bp);
+            pprev = px;
+            gprev = gx;
+            if (i > (long long)hz) { fin = W_UNFINISHED; break; }
+            if (i >= lo + 64) {
+                lo += 64;
+                build_window(s, M32, n, lo, stage, list);
+            }
+            // ---- the boundaries that part at this step
+            const unsigned j0 = s.off[i - lo], j1 = s.off[i - lo + 1];
+            int d0 = 0, d1 = 0, d2 = 0;
+            if (j1 > j0) {
+                if (j1 - j0 <= 32u) {             // one boundary per lane
+                    const bool has = lane < (int)(j1 - j0);
+                    const int b = has ? (int)list[j0 + lane] : 0;
+                    if (has) {
+                        atomicOr(s.N + (b >> 5), 1u << (b & 31));
+                        atomicOr(s.SN + (b >> 10), 1u << ((b >> 5) & 31));
+                    }
+                    __syncwarp();
+                    if (has) split_terms<NPOP>(s, b, n, n0, d0, d1, d2);
+                    __syncwarp();
+                    if (has) {
+                        atomicOr(s.O + (b >> 5), 1u << (b & 31));
+                        atomicOr(s.SO + (b >> 10), 1u << ((b >> 5) & 31));
+                        s.N[b >> 5] = 0u;
+                        s.SN[b >> 10] = 0u;
+                    }
+                    __syncwarp();
+                } else {
+                    for (unsigned j = j0 + lane; j < j1; j += 32) {
+                        const int b = list[j];
+                        atomicOr(s.N + (b >> 5), 1u << (b & 31));
+                        atomicOr(s.SN + (b >> 10), 1u << ((b >> 5) & 31));
+                    }
+                    __syncwarp();
+                    for (unsigned j = j0 + lane; j < j1; j += 32)
+                        split_terms<NPOP>(s, (int)list[j], n, n0, d0, d1, d2);
+                    __syncwarp();
+                    for (unsigned j = j0 + lane; j < j1; j += 32) {
+                        const int b = list[j];
+                        atomicOr(s.O + (b >> 5), 1u << (b & 31));
+                        atomicOr(s.SO + (b >> 10), 1u << ((b >> 5) & 31));
+                    }
+                    __syncwarp();
+                    for (unsigned j = j0 + lane; j < j1; j += 32) {
+                        const int b = list[j];
+                        s.N[b >> 5] = 0u;
+                        s.SN[b >> 10] = 0u;
+                    }
+                    __syncwarp();
+                }
+                d0 = __reduce_add_sync(FULLMASK, d0);
+                d1 = __reduce_add_sync(FULLMASK, d1);
+                if (NPOP == 2) d2 = __reduce_add_sync(FULLMASK, d2);
+            }
+            const unsigned long long ii = (unsigned long long)(i + 1);
+            if (NPOP == 2) {
+                SA = (unsigned long long)((long long)SA + d0);
+                SB = (unsigned long long)((long long)SB + d1);
+                ClassWalk &q = cw[0];
+                q.S = (unsigned long long)((long long)q.S + d2);
+                dA += ii * SA;
+                dB += ii * SB;
+                q.dig += ii * q.S;
+                const bool stop = below_cut(w.a, q.S, q.D);
+                if (stop && !w.a.crossing) { q.stop = (int)i; q.active = false; }
+                else {
+                    if (lane == 0) {
+                        q.acc += (double)(pA + SA) * g;
+                        accB += (double)(pB + SB) * g;
+                    }
+                    if (stop) { q.stop = (int)i; q.active = false; }
+                    pA = SA;
+                    pB = SB;
+                }
+            } else {
+#pragma unroll
+                for (int c_ = 0; c_ < 2; ++c_) {
+                    ClassWalk &q = cw[c_];
+                    if (!q.active) continue;
+                    q.S = (unsigned long long)((long long)q.S + (c_ ? d1 : d0));
+                    q.dig += ii * q.S;
+                    const bool stop = below_cut(w.a, q.S, q.D);
+                    if (stop && !w.a.crossing) { q.stop = (int)i; q.active = false; continue; }
+                    if (lane == 0) q.acc += (double)(q.prev + q.S) * g;
+                    if (stop) { q.stop = (int)i; q.active = false; continue; }
+                    q.prev = q.S;
+                }
+            }
+            any = false;
+#pragma unroll
+            for (int q = 0; q < NWK; ++q) any |= cw[q].active;
+        }
+        // ---- results (lane 0)
+        if (lane == 0) {
+            const ItemSink &sk = w.sk;
+#pragma unroll
+            for (int q_ = 0; q_ < NWK; ++q_) {
+                ClassWalk &q = cw[q_];
+                // iHS items: (allele 1, down), (allele 1, up), (allele 0, down), (allele 0, up)
+                const uint32_t item = NPOP == 2 ? (uint32_t)(k * 2 + dir)
+                                                : (uint32_t)(k * 4 + (q_ == 1 ? 0 : 2) + dir);
+                if (q.active) {
+                    if (fin == W_UNFINISHED) {
+                        const unsigned long long slot2 = atomicAdd(&sk.q->n2, 1ull);
+                        sk.list2[slot2] = item;
+                        sk.key2[slot2] = bucket_of((float)((double)q.S / (double)q.D));
+                        continue;
+                    }
+                    q.status = fin;
+                    q.stop = (int)i;
+                }
+                sk.item_status[item] = (int8_t)q.status;
+                sk.stop[item] = q.stop;
+                if (NPOP == 2) {
+                    sk.item_ihh[2 * (size_t)item] = DA ? q.acc / (2.0 * (double)DA) : 0.0;
+                    sk.item_ihh[2 * (size_t)item + 1] = DB ? accB / (2.0 * (double)DB) : 0.0;
+                    sk.digest[3 * (size_t)item] = dA;
+                    sk.digest[3 * (size_t)item + 1] = dB;
+                    sk.digest[3 * (size_t)item + 2] = q.dig;
+                } else {
+                    sk.item_ihh[item] = q.D ? q.acc / (2.0 * (double)q.D) : 0.0;
+                    sk.digest[item] = q.D ? q.dig : 0ull;
+                }
+            }
+        }
+        __syncwarp();
+    }
+}
+
+int split_walk_ctas(int n, int xpehh)
+{
+    // resident CTAs of the persistent walker (registers allow 4 per SM)
+    int per_sm = 0;
+    const size_t smem = split_smem_per_warp(n, xpehh) * kSplitWarps;
+    cudaError_t e;
+    if (xpehh) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, split_walk_kernel<2>,
+                                                                 kSplitWarps * 32, smem);
+    else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, split_walk_kernel<1>,
+                                                           kSplitWarps * 32, smem);
+    if (e != cudaSuccess || per_sm < 1) per_sm = 1;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return per_sm * (sms > 0 ? sms : 1);
+}
+
+cudaError_t launch_sweep_path(const SweepArgs &w0, cudaStream_t s)
+{
+    SweepArgs w = w0;
+    const size_t ssm = sweep_smem_bytes(w.n, w.a.W);
+    const int E = sweep_e(w.n);
+    void (*sweep)(SweepArgs) = E <= 4 ? sweep_kernel<4> : E <= 8 ? sweep_kernel<8>
+                             : E <= 16 ? sweep_kernel<16> : sweep_kernel<32>;
+    cudaError_t e = cudaFuncSetAttribute(sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm);
+    if (e != cudaSuccess) return e;
+    const size_t wsm = (size_t)w.split_bytes * kSplitWarps;
+    void (*walk)(SweepArgs) = w.a.nB > 0 ? split_walk_kernel<2> : split_walk_kernel<1>;
+    if ((e = cudaFuncSetAttribute(walk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsm)) !=
+        cudaSuccess)
+        return e;
+    for (int st = 0; st < w.nstages; ++st) {
+        w.stage = st;
+        sweep<<<2 * w.nch, kSweepThreads, ssm, s>>>(w);
+        walk<<<w.walk_ctas, kSplitWarps * 32, wsm, s>>>(w);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace selscan

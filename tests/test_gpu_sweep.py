@@ -1,0 +1,150 @@
+"""Sorted-sweep schedule vs the CPU oracle, through the C ABI.
+
+The sweep keeps each chunk's haplotypes sorted by their sequence read
+outward from the core and applies, at walk step i, only the neighbour pairs
+that part there; walks that outrun a chunk's sorted history finish in a
+second per-step pass.  Every launch shape below must reproduce the oracle:
+integers bit for bit, iHH within 1e-12 relative, ln ratios within 1e-9.
+Small warm-ups force many walks through the hand-off; one-core stages
+exercise the state carried between stage launches."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from parity_util import assert_ihs_equal, assert_xpehh_equal, to_np
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [dict(), dict(sweep_warmup=16, sweep_stage_cores=7), dict(sweep_warmup=40, sweep_stage_cores=1),
+          dict(sweep_warmup=300, sweep_stage_cores=4096)]
+
+
+@pytest.fixture(scope="module")
+def sg():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1403_6854_gb300 as sg
+    return sg
+
+
+def sweep(sg, **kw):
+    return sg.make_launch(sg.SCHED_SWEEP, **kw)
+
+
+def run_ihs(sg, rows, n, pos, gmap, **kw):
+    hap, p, g = sg.to_device(rows, pos, gmap)
+    out = sg.selscan_ihs(hap, n, p, g, **kw)
+    sg.check(out)
+    return to_np(out)
+
+
+def run_xpehh(sg, rows, nA, nB, pos, gmap, **kw):
+    hap, p, g = sg.to_device(rows, pos, gmap)
+    out = sg.selscan_xpehh(hap, nA, nB, p, g, **kw)
+    sg.check(out)
+    return to_np(out)
+
+
+@pytest.fixture(scope="module")
+def chr22():
+    d = synth.generate(synth.spec("chr22"))
+    return d, oracle.ihs(d.rows, 204, d.pos, d.gmap)
+
+
+@pytest.fixture(scope="module")
+def xp():
+    d = synth.generate(synth.spec("xpehh"))
+    return d, oracle.xpehh(d.rows, 204, 210, d.pos, d.gmap)
+
+
+@pytest.mark.parametrize("shape", range(len(SHAPES)))
+def test_plain_config(sg, shape):
+    d = synth.generate(synth.spec("plain"))
+    ref = oracle.ihs(d.rows, 100, d.pos, d.gmap)
+    assert_ihs_equal(run_ihs(sg, d.rows, 100, d.pos, d.gmap, launch=sweep(sg, **SHAPES[shape])), ref)
+
+
+@pytest.mark.parametrize("shape", range(len(SHAPES)))
+def test_chr22_all_cores(sg, chr22, shape):
+    d, ref = chr22
+    assert_ihs_equal(run_ihs(sg, d.rows, 204, d.pos, d.gmap, launch=sweep(sg, **SHAPES[shape])), ref)
+
+
+@pytest.mark.parametrize("shape", range(len(SHAPES)))
+def test_xpehh_all_cores(sg, xp, shape):
+    d, ref = xp
+    got = run_xpehh(sg, d.rows, 204, 210, d.pos, d.gmap, launch=sweep(sg, **SHAPES[shape]))
+    assert_xpehh_equal(got, ref)
+
+
+@pytest.mark.parametrize("n", [2, 3, 31, 32, 33, 63, 64, 65, 200])
+@pytest.mark.parametrize("m", [1, 2, 7, 40, 300])
+def test_small_shapes(sg, n, m):
+    hap, pos, gmap = synth.tiny_mosaic(n, m, 3000 + 7 * n + m, founders=3, switch=0.1, flip=0.03)
+    rows = synth.pack(hap)
+    for p in (oracle.params(maf=(0, 1)), oracle.params()):
+        ref = oracle.ihs(rows, n, pos, gmap, p=p)
+        for kw in (dict(), dict(sweep_warmup=16, sweep_stage_cores=3)):
+            got = run_ihs(sg, rows, n, pos, gmap, launch=sweep(sg, **kw),
+                          params=sg.selscan_default_params(maf=(p.maf_num, p.maf_den)))
+            assert_ihs_equal(got, ref)
+
+
+def test_gap_rules_and_parameters(sg):
+    n, m = 40, 60
+    hap, pos, gmap = synth.tiny_mosaic(n, m, 5, founders=2, switch=0.04, flip=0.01,
+                                       dyadic_map=False)
+    steps = np.diff(pos)
+    steps[[5, 12, 20, 33, 41, 50]] = [20_000, 20_001, 200_000, 200_001, 45_000, 1_000_000]
+    pos = np.concatenate([[pos[0]], pos[0] + np.cumsum(steps)]).astype(np.int64)
+    rows = synth.pack(hap)
+    rx = np.concatenate([synth.pack(hap[:, :17]), synth.pack(hap[:, 17:])], 1)
+    cases = [dict(), dict(include_crossing_term=1), dict(ehh_cut=(1, 4)), dict(ehh_cut=(3, 100)),
+             dict(gap_scale_bp=5000, max_gap_bp=60_000), dict(maf=(1, 5))]
+    for c in cases:
+        op = oracle.params(**c)
+        for kw in (dict(), dict(sweep_warmup=16, sweep_stage_cores=2)):
+            L = sweep(sg, **kw)
+            got = run_ihs(sg, rows, n, pos, gmap, params=sg.selscan_default_params(**c), launch=L)
+            assert_ihs_equal(got, oracle.ihs(rows, n, pos, gmap, p=op))
+            gotx = run_xpehh(sg, rx, 17, n - 17, pos, gmap, params=sg.selscan_default_params(**c),
+                             launch=L)
+            assert_xpehh_equal(gotx, oracle.xpehh(rx, 17, n - 17, pos, gmap, p=op))
+
+
+def test_xpehh_small_and_maf_flag(sg):
+    for nA, nB in ((2, 2), (5, 64), (64, 65), (100, 31)):
+        hap, pos, gmap = synth.tiny_mosaic(nA + nB, 35, nA * 31 + nB, founders=3, switch=0.1,
+                                           flip=0.03)
+        rows = np.concatenate([synth.pack(hap[:, :nA]), synth.pack(hap[:, nA:])], 1)
+        for flag in (0, 1):
+            ref = oracle.xpehh(rows, nA, nB, pos, gmap, p=oracle.params(xpehh_maf_filter=flag))
+            for kw in (dict(), dict(sweep_warmup=16, sweep_stage_cores=5)):
+                got = run_xpehh(sg, rows, nA, nB, pos, gmap, launch=sweep(sg, **kw),
+                                params=sg.selscan_default_params(xpehh_maf_filter=flag))
+                assert_xpehh_equal(got, ref)
+
+
+def test_identical_haplotypes_and_long_walks(sg):
+    """All carriers identical over long stretches (a sweep in miniature): the
+    walks outrun small warm-ups and finish in the second pass."""
+    n, m = 150, 500
+    hap, pos, gmap = synth.tiny_mosaic(n, m, 99, founders=2, switch=0.002, flip=0.0)
+    rows = synth.pack(hap)
+    ref = oracle.ihs(rows, n, pos, gmap)
+    for kw in (dict(), dict(sweep_warmup=16, sweep_stage_cores=9), dict(sweep_warmup=100)):
+        assert_ihs_equal(run_ihs(sg, rows, n, pos, gmap, launch=sweep(sg, **kw)), ref)
+
+
+@pytest.mark.parametrize("n", [16383, 16384])
+def test_haplotype_limit(sg, n):
+    """16383 haplotypes is the largest sample sorted on chip; 16384 falls back
+    to the in-order schedule.  Both agree with the oracle on sampled cores."""
+    m = 120
+    hap, pos, gmap = synth.tiny_mosaic(n, m, n, founders=6, switch=0.05, flip=0.002)
+    rows = synth.pack(hap)
+    cores = np.array([0, 1, 17, 59, 60, 101, 119])
+    ref = oracle.ihs(rows, n, pos, gmap, cores=cores)
+    got = run_ihs(sg, rows, n, pos, gmap, launch=sweep(sg, sweep_warmup=32, sweep_stage_cores=16))
+    assert_ihs_equal(got, ref, idx=cores)
