@@ -200,7 +200,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="ihs1m", choices=list(WORKLOADS))
     ap.add_argument("--schedule", type=int, default=-1,
-                    help="-1: autotuned launch shape; 0/1/2: fixed schedule with defaults")
+                    help="-1: autotuned launch shape; 0/1/2/3: fixed schedule with defaults")
     ap.add_argument("--tune-cache", action="store_true")
     ap.add_argument("--served", type=int, default=200, help="requests in the served mix (0: skip)")
     ap.add_argument("--load", type=float, default=0.7, help="served arrival rate / capacity")
@@ -250,7 +250,9 @@ def main():
         _, shape = tuner.launch_for(hap, pos, gmap, "ihs", n)
         from paper_1403_6854_gb300.tune import SHAPE_FIELDS
         launch_fields = {f: shape.get(f, 0) for f in SHAPE_FIELDS}
-        shape = dict(shape, source="autotuner on the first 65,536 markers")
+        shape = dict(shape, source=("autotuner, sorted-sweep candidates timed on the whole scan"
+                                    if shape.get("schedule") == 3 else
+                                    "autotuner on the first 65,536 markers"))
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(K)]
     for a, b in ev:                      # create the events before handing them out
@@ -267,7 +269,7 @@ def main():
 
     gpu_id = str(torch.cuda.get_device_properties(dev).uuid)
     gpu_id = gpu_id if gpu_id.startswith("GPU-") else "GPU-" + gpu_id
-    launches_per_step = {0: 8, 1: 4, 2: 4}[launch_fields.get("schedule", 1)]
+    launches_per_step = sg.selscan_launch_count(n, spec.m, sg.MODE_IHS, sg.make_launch(**launch_fields))
     with ClockSampler(gpu_id) as clk:
         if world > 1:
             dist.barrier()
@@ -313,7 +315,8 @@ def main():
             dh.copy_(h_rows, non_blocking=True)
             dp.copy_(h_pos, non_blocking=True)
             dg.copy_(h_gmap, non_blocking=True)
-            o2 = sg.selscan_ihs(dh, n, dp, dg, params=params, workspace=ws)
+            o2 = sg.selscan_ihs(dh, n, dp, dg, params=params, workspace=ws,
+                                launch=sg.make_launch(**launch_fields))
             for f in res:
                 res[f].copy_(o2[f], non_blocking=True)
             torch.cuda.synchronize()
@@ -346,13 +349,16 @@ def main():
             "config": {"workload": WORKLOADS[args.workload], "n_haplotypes": n, "n_snps": spec.m,
                        "core_loci_per_gpu": cores, "walk_steps_per_scan": steps_total,
                        "schedule": ["persistent longest-first", "persistent in-order",
-                                    "plain one-CTA-per-core"][launch_fields.get("schedule", 1)],
+                                    "plain one-CTA-per-core", "sorted sweep + split walk"][
+                                        launch_fields.get("schedule", 1)],
                        "launch_shape": shape,
                        "l2": "inputs larger than L2 (packed matrix 632 MB), no flush",
                        "parallelism": f"weak: one chromosome (seed = rank) per GPU x{world}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "traffic": None,
-                         "kernel": "walk_persistent_kernel (both passes)",
+                         "kernel": ("sweep_kernel + split_walk_kernel, all stages, and the "
+                                    "second per-step pass" if launch_fields.get("schedule") == 3
+                                    else "walk_persistent_kernel (both passes)"),
                          "walk_ms": walk_ms, "walk_bytes": walk_bytes,
                          "peak_source": f"{src} hbm_gbs (MEASURED_PEAKS.json)"},
             "gpu_launches": launches_per_step * K,
@@ -369,8 +375,21 @@ def main():
 
 
 def run_extras(sg, torch, synth, d, hap, pos, gmap, n, ws):
-    """XPEHH throughput and the plain-launch comparison on the same GPU."""
+    """XPEHH throughput and the per-step comparisons (persistent in-order,
+    plain launches) on the same GPU and matrix."""
     ex = {}
+    L = sg.make_launch(sg.SCHED_IN_ORDER, warps_per_cta=4)
+    o = sg.selscan_ihs(hap, n, pos, gmap, launch=L)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    o = sg.selscan_ihs(hap, n, pos, gmap, launch=L, workspace=o["_workspace"], out=o)
+    b.record()
+    torch.cuda.synchronize()
+    cores = int((o["status"] != sg.LOCUS_MAF_FILTERED).sum())
+    ex["per_step_in_order"] = {"value": cores / (a.elapsed_time(b) / 1e3), "unit": "core loci/s",
+                               "ms_per_scan": a.elapsed_time(b)}
+    del o
     # plain launches (one CTA per core) on the same matrix
     L = sg.make_launch(sg.SCHED_PLAIN)
     o = sg.selscan_ihs(hap, n, pos, gmap, launch=L)

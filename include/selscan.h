@@ -88,9 +88,12 @@ typedef struct {
     int32_t xpehh_maf_filter;            /* 0 (default): XPEHH at every marker */
 } selscan_params;
 
-/* Scheduling of the walk kernel.  Changes how the work runs, never the
- * results.  A NULL selscan_launch* selects the library defaults (in-order
- * persistent schedule, 8 warps per CTA, 512 on-chip group words per warp). */
+/* Scheduling of the walk kernels.  Changes how the work runs, never the
+ * results.  A NULL selscan_launch* selects the library defaults: the sorted
+ * sweep for iHS / XPEHH scans of at least 131,072 markers and up to 16383
+ * haplotypes, else the in-order persistent schedule; 8 warps per CTA and 512
+ * on-chip group words per warp for the per-step kernels. */
+#define SELSCAN_SCHED_DEFAULT      -1  /* the library's choice (as for a NULL selscan_launch*) */
 #define SELSCAN_SCHED_LONGEST_FIRST 0  /* persistent kernel, probe pass + longest-first queue */
 #define SELSCAN_SCHED_IN_ORDER      1  /* persistent kernel, one queue in core order */
 #define SELSCAN_SCHED_PLAIN         2  /* one CTA per core, no persistence, no ordering */
@@ -114,10 +117,13 @@ typedef struct {
     int32_t big_group_entries; /* groups with at least this many 32-bit words are split by the
                                   whole warp, smaller ones one lane each (0 = 32) */
     int32_t sweep_warmup;      /* sweep schedule: markers sorted before a chunk's first core,
-                                  16..16384 (0 = 1024); walks longer than this may take the
+                                  16..16384 (0 = 2048); walks longer than this may take the
                                   second pass */
     int32_t sweep_stage_cores; /* sweep schedule: cores per chunk between walk launches,
-                                  1..4096 (0 = 64); sizes the slot buffer */
+                                  1..4096 (0 = the whole chunk, capped so that the slot
+                                  buffer stays near 4 GiB); sizes the slot buffer */
+    int32_t sweep_threads;     /* sweep schedule: threads per sorting CTA, 256 or 512
+                                  (0 = 256 up to 6144 haplotypes, else 512) */
 } selscan_launch;
 
 /* iHS outputs: device arrays of length m (one record per marker). */
@@ -269,6 +275,11 @@ int selscan_batch_finalize(const selscan_scan *scan, void *stream);
  * words beyond W written as 0. */
 int selscan_pack(const uint8_t *hap01, int32_t n, int64_t m, int32_t hap_major,
                  uint64_t *rows, int64_t ld, void *stream);
+
+/* Kernel launches one selscan_ihs / selscan_xpehh call makes with this
+ * launch shape (mode SELSCAN_MODE_IHS or SELSCAN_MODE_XPEHH), or -1 for bad
+ * arguments.  Host only: no device work. */
+int32_t selscan_launch_count(int32_t n_total, int64_t m, int32_t mode, const selscan_launch *launch);
 
 /* Static description of a return or error code. */
 const char *selscan_strerror(int code);

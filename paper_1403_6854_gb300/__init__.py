@@ -30,7 +30,7 @@ ERR_INVALID_ARG, ERR_UNSORTED, ERR_WORKSPACE, ERR_CUDA, ERR_TIMEOUT, ERR_UNSUPPO
 ERR_INTERNAL = -7
 LOCUS_OK, LOCUS_MAF_FILTERED, LOCUS_UNDEFINED, LOCUS_ABORT_EDGE, LOCUS_ABORT_GAP = 0, 1, 2, 3, 4
 MODE_IHS, MODE_XPEHH, MODE_EHH = 0, 1, 2
-SCHED_LONGEST_FIRST, SCHED_IN_ORDER, SCHED_PLAIN, SCHED_SWEEP = 0, 1, 2, 3
+SCHED_DEFAULT, SCHED_LONGEST_FIRST, SCHED_IN_ORDER, SCHED_PLAIN, SCHED_SWEEP = -1, 0, 1, 2, 3
 
 _P = ctypes.c_void_p
 
@@ -49,7 +49,7 @@ class selscan_launch(ctypes.Structure):
                 ("cores_per_fetch", ctypes.c_int32), ("min_ctas_per_sm", ctypes.c_int32),
                 ("walk_begin_event", ctypes.c_void_p), ("walk_end_event", ctypes.c_void_p),
                 ("big_group_entries", ctypes.c_int32), ("sweep_warmup", ctypes.c_int32),
-                ("sweep_stage_cores", ctypes.c_int32)]
+                ("sweep_stage_cores", ctypes.c_int32), ("sweep_threads", ctypes.c_int32)]
 
 
 class selscan_ihs_out(ctypes.Structure):
@@ -77,7 +77,7 @@ class selscan_scan(ctypes.Structure):
 EXPORTS = ("selscan_default_params", "selscan_workspace_bytes", "selscan_ihs", "selscan_xpehh",
            "selscan_ehh", "selscan_ehh_noalloc", "selscan_pack", "selscan_strerror",
            "selscan_batch_item_bytes", "selscan_batch_workspace_bytes", "selscan_batch_prepare",
-           "selscan_batch_run", "selscan_batch_finalize")
+           "selscan_batch_run", "selscan_batch_finalize", "selscan_launch_count")
 EHH_NOALLOC_MAX_N = 8192
 
 _lib = None
@@ -129,6 +129,8 @@ def load_library():
     lib.selscan_batch_run.argtypes = [ctypes.POINTER(selscan_scan), ctypes.c_int32, _P, _P, _P,
                                       ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, _P,
                                       ctypes.c_size_t, _P]
+    lib.selscan_launch_count.restype = ctypes.c_int32
+    lib.selscan_launch_count.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, _P]
     lib.selscan_batch_finalize.restype = ctypes.c_int
     lib.selscan_batch_finalize.argtypes = [ctypes.POINTER(selscan_scan), _P]
     lib.selscan_strerror.restype = ctypes.c_char_p
@@ -160,10 +162,10 @@ def selscan_default_params(**overrides) -> selscan_params:
     return p
 
 
-def make_launch(schedule: int = SCHED_IN_ORDER, warps_per_cta: int = 0, ctas_per_sm: int = 0,
+def make_launch(schedule: int = SCHED_DEFAULT, warps_per_cta: int = 0, ctas_per_sm: int = 0,
                 smem_entries: int = 0, probe_steps: int = 0, window_rows: int = 0,
                 cores_per_fetch: int = 0, min_ctas_per_sm: int = 0, big_group_entries: int = 0,
-                sweep_warmup: int = 0, sweep_stage_cores: int = 0,
+                sweep_warmup: int = 0, sweep_stage_cores: int = 0, sweep_threads: int = 0,
                 events=None) -> selscan_launch:
     """events: optional (begin, end) torch.cuda.Event pair bracketing the walk kernels."""
     L = selscan_launch(schedule, warps_per_cta, ctas_per_sm, smem_entries, probe_steps,
@@ -171,10 +173,18 @@ def make_launch(schedule: int = SCHED_IN_ORDER, warps_per_cta: int = 0, ctas_per
     L.big_group_entries = big_group_entries
     L.sweep_warmup = sweep_warmup
     L.sweep_stage_cores = sweep_stage_cores
+    L.sweep_threads = sweep_threads
     if events is not None:
         L.walk_begin_event = ctypes.c_void_p(events[0].cuda_event)
         L.walk_end_event = ctypes.c_void_p(events[1].cuda_event)
     return L
+
+
+def selscan_launch_count(n_total: int, m: int, mode: int,
+                         launch: Optional[selscan_launch] = None) -> int:
+    """Kernel launches of one scan call with this launch shape."""
+    return int(load_library().selscan_launch_count(
+        n_total, m, mode, ctypes.byref(launch) if launch is not None else None))
 
 
 def selscan_workspace_bytes(n_total: int, m: int, mode: int,

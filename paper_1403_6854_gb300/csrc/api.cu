@@ -19,10 +19,12 @@ constexpr int kDefaultSmemEntries = 512;
 constexpr int kDefaultProbeSteps = 48;
 constexpr int kDefaultBigGroup = 32;
 constexpr int kMaxHaplotypes = 65000;
+constexpr int kDefaultSweepWarmup = 2048;
+constexpr size_t kSweepSlotBudget = (size_t)4 << 30;   // bytes of sweep slots per scan
 constexpr size_t kMaxSmemPerCta = 227 * 1024;
 
 struct SweepPlan {
-    int nch, L, R, nstages;
+    int nch, L, R, nstages, threads;
     long long B;
     size_t state_bytes, slot_bytes;
     int split_bytes;
@@ -55,26 +57,41 @@ bool params_ok(const selscan_params *p)
 SweepPlan make_sweep_plan(int n_total, long long m, int mode, const selscan_launch *L)
 {
     SweepPlan w;
-    w.L = (L && L->sweep_warmup > 0) ? L->sweep_warmup : 1024;
+    w.L = (L && L->sweep_warmup > 0) ? L->sweep_warmup : kDefaultSweepWarmup;
     if (w.L < 16) w.L = 16;
     if (w.L > 16384) w.L = 16384;
-    w.R = (L && L->sweep_stage_cores > 0) ? L->sweep_stage_cores : 64;
+    w.R = (L && L->sweep_stage_cores > 0) ? L->sweep_stage_cores : 0;
     if (w.R > 4096) w.R = 4096;
-    // chunks: about one per SM, each at least as long as its warm-up
+    // 256-thread CTAs (3 per SM) up to 24 elements per thread, else 512 (2 per SM)
+    const int want = L ? L->sweep_threads : 0;
+    w.threads = (want == 256 || want == 512) ? want : (n_total <= 256 * 24 ? 256 : 512);
+    if (w.threads == 256 && n_total > 256 * 64) w.threads = 512;
+    // chunks: the resident sweep CTAs split over both directions, each chunk
+    // at least as long as its warm-up
     const long long per = w.L > 256 ? w.L : 256;
     long long nch = (m + per - 1) / per;
     const int sms = device_sms();
-    if (nch > sms) nch = sms;
+    const int nmax = w.threads == 256 ? (3 * sms) / 2 : sms;
+    if (nch > nmax) nch = nmax;
     if (nch < 1) nch = 1;
     // run lengths are 16-bit: a chunk plus its warm-up stays below 65,000 markers
     const long long maxB = 65000 - w.L;
     if ((m + nch - 1) / nch > maxB) nch = (m + maxB - 1) / maxB;
     w.nch = (int)nch;
     w.B = (m + nch - 1) / nch;
-    w.nstages = (int)((w.B + w.R - 1) / w.R);
     const int xp = mode == SELSCAN_MODE_XPEHH;
-    w.state_bytes = sweep_state_bytes(n_total);
+    w.state_bytes = sweep_state_bytes(n_total, w.threads);
     w.slot_bytes = sweep_slot_bytes(n_total, xp);
+    if (w.R <= 0) {
+        // default stage: the whole chunk if its slots fit the slot budget,
+        // else as many cores as fit (fewer, longer stages launch less)
+        const long long fit = (long long)(kSweepSlotBudget / ((size_t)2 * w.nch * w.slot_bytes));
+        long long r = w.B < fit ? w.B : fit;
+        if (r > 4096) r = 4096;
+        if (r < 16) r = 16;
+        w.R = (int)r;
+    }
+    w.nstages = (int)((w.B + w.R - 1) / w.R);
     w.split_bytes = (int)split_smem_per_warp(n_total, xp);
     w.walk_ctas = split_walk_ctas(n_total, xp);
     w.wscratch_bytes = split_scratch_per_warp(n_total);
@@ -84,7 +101,12 @@ SweepPlan make_sweep_plan(int n_total, long long m, int mode, const selscan_laun
 Plan make_plan(int mode, long long ld, const selscan_launch *L, int n_total = 0, long long m = 0)
 {
     Plan p;
-    p.schedule = L ? L->schedule : SELSCAN_SCHED_IN_ORDER;
+    // default: the sorted sweep once the chromosome is long enough for its
+    // chunks' sequential sorts (each about B + warm-up markers) to cost less
+    // than walking every step; the in-order per-step schedule otherwise
+    p.schedule = (L && L->schedule != SELSCAN_SCHED_DEFAULT)
+                     ? L->schedule
+                     : (m >= 64ll * kDefaultSweepWarmup ? SELSCAN_SCHED_SWEEP : SELSCAN_SCHED_IN_ORDER);
     if (p.schedule < 0 || p.schedule > SELSCAN_SCHED_SWEEP) p.schedule = -1;
     memset(&p.sw, 0, sizeof(p.sw));
     if (p.schedule == SELSCAN_SCHED_SWEEP) {
@@ -224,7 +246,7 @@ int run_scan(int mode, const uint64_t *hap, int64_t ld, int32_t nA, int32_t nB, 
     if (smem_per_warp(plan.cap_s, plan.tcap_s, plan.rowcap, plan.poscap) * (size_t)plan.wpc > kMaxSmemPerCta)
         return SELSCAN_ERR_UNSUPPORTED;
     const bool sweep = plan.schedule == SELSCAN_SCHED_SWEEP;
-    if (sweep && (sweep_smem_bytes(n_total, (nA + 63) / 64 + (nB + 63) / 64) > kMaxSmemPerCta ||
+    if (sweep && (sweep_smem_bytes(n_total, (nA + 63) / 64 + (nB + 63) / 64, plan.sw.threads) > kMaxSmemPerCta ||
                   (size_t)plan.sw.split_bytes * kSplitWarps > kMaxSmemPerCta))
         return SELSCAN_ERR_UNSUPPORTED;
     const Layout l = make_layout(n_total, m, mode, plan.nslots, sweep ? &plan.sw : nullptr);
@@ -266,6 +288,7 @@ int run_scan(int mode, const uint64_t *hap, int64_t ld, int32_t nA, int32_t nB, 
         w.a = a;
         w.sk = sk;
         w.n = n_total;
+        w.threads = plan.sw.threads;
         w.nch = plan.sw.nch;
         w.B = plan.sw.B;
         w.L = plan.sw.L;
@@ -323,6 +346,19 @@ size_t selscan_workspace_bytes(int32_t n_total, int64_t m, int32_t mode, const s
     const int nslots = mode == SELSCAN_MODE_EHH ? p.nslots : device_sms() * 64;
     return make_layout(n_total, m, mode, nslots,
                        p.schedule == SELSCAN_SCHED_SWEEP ? &p.sw : nullptr).total;
+}
+
+int32_t selscan_launch_count(int32_t n_total, int64_t m, int32_t mode, const selscan_launch *launch)
+{
+    if (n_total < 2 || m < 1 || (mode != SELSCAN_MODE_IHS && mode != SELSCAN_MODE_XPEHH)) return -1;
+    const Plan p = make_plan(mode, (n_total + 63) / 64, launch, n_total, m);
+    switch (p.schedule) {
+    case SELSCAN_SCHED_LONGEST_FIRST: return 8;   // validate, select, probe pass, 3 bucket kernels, pass 2, finalize
+    case SELSCAN_SCHED_IN_ORDER:
+    case SELSCAN_SCHED_PLAIN: return 4;           // validate, select, walk, finalize
+    case SELSCAN_SCHED_SWEEP: return 7 + 2 * p.sw.nstages;   // + sweep and split walk per stage
+    default: return -1;
+    }
 }
 
 int selscan_ihs(const uint64_t *hap, int64_t ld, int32_t n, int64_t m, const int64_t *pos_bp,

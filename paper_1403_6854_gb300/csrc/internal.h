@@ -101,7 +101,6 @@ cudaError_t launch_pass2(const ScanArgs &a, const ItemSink &sink, const Scratch 
                          int warps_per_cta, int ctas, int minb, cudaStream_t s);
 
 // ---- sorted-sweep walks (sweep.cu)
-constexpr int kSweepThreads = 512;   // threads of one sweep CTA
 constexpr int kSplitWarps = 8;       // warps of one split-walk CTA
 constexpr int kSweepMaxN = 16383;    // haplotypes the sweep keeps on chip (14-bit counts)
 
@@ -109,6 +108,7 @@ struct SweepArgs {
     ScanArgs a;
     ItemSink sk;
     int n;                   // haplotypes sorted (iHS: n; XPEHH: n_A + n_B)
+    int threads;             // threads of one sweep CTA (256 or 512)
     int nch;                 // chunks of cores per direction
     long long B;             // cores per chunk
     int L;                   // markers swept before a chunk's first core
@@ -124,9 +124,9 @@ struct SweepArgs {
     unsigned long long *walk_head;   // slot counter of the current walk launch
 };
 
-size_t sweep_smem_bytes(int n, int W);
+size_t sweep_smem_bytes(int n, int W, int T);
 size_t sweep_slot_bytes(int n, int xpehh);
-size_t sweep_state_bytes(int n);
+size_t sweep_state_bytes(int n, int T);
 size_t split_smem_per_warp(int n, int xpehh);
 size_t split_scratch_per_warp(int n);
 int split_walk_ctas(int n, int xpehh);

@@ -39,12 +39,12 @@ namespace {
 
 constexpr unsigned kInf16 = 0xFFFFu;
 
-__host__ __device__ inline int sweep_e(int n)
+__host__ __device__ inline int sweep_e(int n, int T)
 {
-    int e = (n + kSweepThreads - 1) / kSweepThreads;
+    int e = (n + T - 1) / T;
     return (e + 1) & ~1;                    // even: elements are read in pairs
 }
-__host__ __device__ inline int sweep_npad(int n) { return sweep_e(n) * kSweepThreads; }
+__host__ __device__ inline int sweep_npad(int n, int T) { return sweep_e(n, T) * T; }
 __host__ __device__ inline int split_nw(int n) { return (n + 32) >> 5; }   // bits 0..n
 
 // ---- prefix-state algebra of the stable partition --------------------------
@@ -76,10 +76,10 @@ __device__ __forceinline__ unsigned bit_index(const SweepArgs &w, int h)
 
 }  // namespace
 
-size_t sweep_smem_bytes(int n, int W)
+size_t sweep_smem_bytes(int n, int W, int T)
 {
-    const int W32 = ((2 * W) + 3) & ~3;
-    return (size_t)sweep_npad(n) * 4 * 2 + (size_t)W32 * 4 * 2 + kSweepThreads / 32 * 8;
+    const int W32 = ((2 * W) + 4) & ~3;
+    return (size_t)sweep_npad(n, T) * 4 * 2 + (size_t)W32 * 4 * 2 + T / 32 * 8;
 }
 
 size_t sweep_slot_bytes(int n, int xpehh)
@@ -89,26 +89,30 @@ size_t sweep_slot_bytes(int n, int xpehh)
     return b;
 }
 
-size_t sweep_state_bytes(int n) { return (size_t)sweep_npad(n) * 4; }
+size_t sweep_state_bytes(int n, int T) { return (size_t)sweep_npad(n, T) * 4; }
 
 
 // ---- the sweep ---------------------------------------------------------------
 // Shared memory: two buffers of np packed elements (bit index of the haplotype
-// in the row | run length with its predecessor << 16), two row buffers, the
-// warp totals.  EMAX bounds the elements per thread; up to 16 stay in
-// registers between the two passes.
-template <int EMAX>
-__global__ void __launch_bounds__(kSweepThreads, 2) sweep_kernel(SweepArgs w)
+// in the row | run length with its predecessor << 16), two row buffers with
+// one extra all-ones word, the warp totals.  Positions n..np-1 hold padding
+// elements whose allele is that all-ones word: they sort after every real
+// haplotype and never touch a real element's run length.  T threads; EMAX
+// bounds the elements per thread, up to 24 stay in registers between the
+// two passes.
+template <int T, int EMAX>
+__global__ void __launch_bounds__(T, T == 512 ? 2 : 3) sweep_kernel(SweepArgs w)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    constexpr bool CACHE = EMAX <= 16;
+    constexpr bool CACHE = EMAX <= 24;
     const int n = w.n;
-    const int E = sweep_e(n);
-    const int np = E * kSweepThreads;
+    const int E = sweep_e(n, T);
+    const int np = E * T;
     const int W32 = 2 * w.a.W;
-    const int W32r = (W32 + 3) & ~3;
+    const int W32r = (W32 + 4) & ~3;             // >= W32 + 1
+    const unsigned pad_bi = 32u * (unsigned)W32; // bit index of the padding elements
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    constexpr int NW = kSweepThreads / 32;
+    constexpr int NW = T / 32;
     unsigned *P0 = (unsigned *)smem;             // buffer b at P0 + b * np
     unsigned *R0 = P0 + 2 * np;                  // row buffer r at R0 + r * W32r
     unsigned *wsum = R0 + 2 * W32r;
@@ -146,13 +150,17 @@ __global__ void __launch_bounds__(kSweepThreads, 2) sweep_kernel(SweepArgs w)
     if (blockIdx.x == 0 && tid == 0) *w.walk_head = 0ull;   // the next walk launch's slot counter
     // ---- state in
     if (w.stage == 0) {
-        for (int t = tid; t < np; t += kSweepThreads) P0[t] = t < n ? bit_index(w, t) : 0u;
+        for (int t = tid; t < np; t += T) P0[t] = t < n ? bit_index(w, t) : pad_bi;
     } else {
-        for (int t = tid; t < np; t += kSweepThreads) P0[t] = st[t];
+        for (int t = tid; t < np; t += T) P0[t] = st[t];
     }
     const unsigned *hap32 = (const unsigned *)w.a.hap;
     const long long ld32 = 2 * w.a.ld;
-    for (int t = tid; t < W32; t += kSweepThreads) R0[t] = hap32[xfirst * ld32 + t];
+    for (int t = tid; t < W32; t += T) R0[t] = hap32[xfirst * ld32 + t];
+    if (tid < W32r - W32) {
+        R0[W32 + tid] = 0xFFFFFFFFu;
+        R0[W32r + W32 + tid] = 0xFFFFFFFFu;
+    }
     __syncthreads();
 
     int cur = 0, rb = 0;
@@ -160,40 +168,51 @@ __global__ void __launch_bounds__(kSweepThreads, 2) sweep_kernel(SweepArgs w)
     unsigned val[CACHE ? EMAX : 1];
     for (long long x = xfirst;; x += step) {
         const bool more = x != xlast;
-        unsigned rnext = 0u;                     // the next row, loaded while this one is sorted
-        if (more && tid < W32) rnext = __ldg(hap32 + (x + step) * ld32 + tid);
+        unsigned rnext[3];                       // the next row, loaded while this one is sorted
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            rnext[j] = more && tid + j * T < W32 ? __ldg(hap32 + (x + step) * ld32 + tid + j * T) : 0u;
         const bool is_core = x >= klo && x < khi;
         int cst = 0;
         if (is_core) cst = w.sk.core_status[x];
 
         const unsigned *Pc = P0 + cur * np;
         const unsigned *row = R0 + rb * W32r;
-        // pass 1: alleles of this thread's elements and the segment summary
-        unsigned vmask = 0u;
-        unsigned all = kInf16, t0 = kInf16, t1 = kInf16, zeros = 0u, seen = 0u;
+        // pass 1: alleles, the new run lengths as far as this segment decides
+        // them, and the segment summary
+        unsigned vmask = 0u, all = kInf16, mn0 = kInf16, mn1 = kInf16, hp0 = 0u, hp1 = 0u;
+        unsigned f0min = kInf16, f1min = kInf16, f0bi = 0u, f1bi = 0u;
 #pragma unroll
         for (int e = 0; e < EMAX; e += 2) {
-            if (e < E && base + e < n) {
+            if (e < E) {
                 const uint2 q = *(const uint2 *)(Pc + base + e);
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     const unsigned pv = h ? q.y : q.x;
-                    if (CACHE) val[e + h] = pv;
-                    if (base + e + h < n) {
-                        const unsigned bi = pv & 0xFFFFu, mv = pv >> 16;
-                        const unsigned v = (row[bi >> 5] >> (bi & 31u)) & 1u;
-                        vmask |= v << (e + h);
-                        all = min(all, mv);
-                        t0 = v ? min(t0, mv) : kInf16;
-                        t1 = v ? kInf16 : min(t1, mv);
-                        zeros += v ^ 1u;
-                        seen |= 1u << v;
+                    const unsigned bi = pv & 0xFFFFu, mv = pv >> 16;
+                    const unsigned v = (row[bi >> 5] >> (bi & 31u)) & 1u;
+                    vmask |= v << (e + h);
+                    all = min(all, mv);
+                    mn0 = min(mn0, mv);
+                    mn1 = min(mn1, mv);
+                    const unsigned mnv = v ? mn1 : mn0;
+                    const unsigned hpv = v ? hp1 : hp0;
+                    if (!hpv) {                  // first of its allele in the segment
+                        if (v) { f1min = mnv; f1bi = bi; }
+                        else { f0min = mnv; f0bi = bi; }
                     }
+                    const unsigned out = min(mnv + 1u, kInf16);
+                    if (CACHE) val[e + h] = bi | (out << 16);
+                    mn1 = v ? kInf16 : mn1;
+                    mn0 = v ? mn0 : kInf16;
+                    hp1 |= v;
+                    hp0 |= v ^ 1u;
                 }
             }
         }
-        unsigned p0 = all | (t0 << 16);
-        unsigned p1 = t1 | (zeros << 16) | (seen << 30);
+        const unsigned zeros = (unsigned)E - (unsigned)__popc(vmask);
+        unsigned p0 = all | (mn0 << 16);
+        unsigned p1 = mn1 | (zeros << 16) | (hp0 << 30) | (hp1 << 31);
         // warp inclusive scan
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
@@ -220,34 +239,61 @@ __global__ void __launch_bounds__(kSweepThreads, 2) sweep_kernel(SweepArgs w)
         const unsigned tot1 = __shfl_sync(FULLMASK, q1, NW - 1);
         const unsigned n0 = (tot1 >> 16) & 0x3FFFu;
         compose(w0, w1, x0, x1);                  // this thread's exclusive prefix
-        // pass 2: scatter into the other buffer with the new run lengths
-        unsigned mn0 = x0 >> 16, mn1 = x1 & 0xFFFFu;
-        unsigned hp0 = (x1 >> 30) & 1u, hp1 = x1 >> 31;
-        unsigned z = (x1 >> 16) & 0x3FFFu;
-        unsigned o = n0 + (unsigned)base - z;
+        // pass 2: place the elements; the first allele-0 / allele-1 element of
+        // the segment takes its run length from the prefix (0 if it is the
+        // first of its allele overall)
+        const unsigned zs = (x1 >> 16) & 0x3FFFu;
+        const unsigned os = n0 + (unsigned)base - zs;
+        unsigned z = zs, o = os;
         unsigned *Pn = P0 + (cur ^ 1) * np;
+        if (CACHE) {
 #pragma unroll
-        for (int e = 0; e < EMAX; ++e) {
-            if (e < E && base + e < n) {
-                const unsigned pv = CACHE ? val[e] : Pc[base + e];
-                const unsigned bi = pv & 0xFFFFu, mv = pv >> 16;
-                mn0 = min(mn0, mv);
-                mn1 = min(mn1, mv);
+            for (int e = 0; e < EMAX; ++e) {
+                if (e < E) {
+                    const unsigned one = (vmask >> e) & 1u;
+                    Pn[one ? o : z] = val[CACHE ? e : 0];
+                    o += one;
+                    z += one ^ 1u;
+                }
+            }
+        }
+        if (!CACHE) {
+            // second sweep over the segment for the run lengths (large samples)
+            unsigned a0 = x0 >> 16, a1 = x1 & 0xFFFFu;
+            unsigned h0 = (x1 >> 30) & 1u, h1 = x1 >> 31;
+            z = zs;
+            o = os;
+            for (int e = 0; e < E; ++e) {
+                const unsigned q = Pc[base + e];
+                const unsigned mv = q >> 16;
+                a0 = min(a0, mv);
+                a1 = min(a1, mv);
                 const unsigned one = (vmask >> e) & 1u;
-                const unsigned mn = one ? mn1 : mn0;
-                const unsigned hp = one ? hp1 : hp0;
-                const unsigned out = hp ? min(mn + 1u, kInf16) : 0u;
+                const unsigned mnv = one ? a1 : a0;
+                const unsigned hpv = one ? h1 : h0;
+                const unsigned out = hpv ? min(mnv + 1u, kInf16) : 0u;
                 const unsigned p = one ? o : z;
                 o += one;
                 z += one ^ 1u;
-                mn1 = one ? kInf16 : mn1;
-                mn0 = one ? mn0 : kInf16;
-                hp1 |= one;
-                hp0 |= one ^ 1u;
-                Pn[p] = bi | (out << 16);
+                a1 = one ? kInf16 : a1;
+                a0 = one ? a0 : kInf16;
+                h1 |= one;
+                h0 |= one ^ 1u;
+                Pn[p] = (q & 0xFFFFu) | (out << 16);
+            }
+        } else {
+            if (hp0) {                            // first allele-0 element of the segment
+                const unsigned out = ((x1 >> 30) & 1u) ? min(min(x0 >> 16, f0min) + 1u, kInf16) : 0u;
+                Pn[zs] = f0bi | (out << 16);
+            }
+            if (hp1) {
+                const unsigned out = (x1 >> 31) ? min(min(x1 & 0xFFFFu, f1min) + 1u, kInf16) : 0u;
+                Pn[os] = f1bi | (out << 16);
             }
         }
-        if (more && tid < W32) R0[(rb ^ 1) * W32r + tid] = rnext;
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            if (more && tid + j * T < W32) R0[(rb ^ 1) * W32r + tid + j * T] = rnext[j];
         __syncthreads();
         cur ^= 1;
         rb ^= 1;
@@ -266,7 +312,7 @@ __global__ void __launch_bounds__(kSweepThreads, 2) sweep_kernel(SweepArgs w)
             }
             const unsigned *Ps = P0 + cur * np;
             unsigned *Md = (unsigned *)(slot + 16);
-            for (int t = tid; t < (n + 1) / 2; t += kSweepThreads) {
+            for (int t = tid; t < (n + 1) / 2; t += T) {
                 const uint2 q = *(const uint2 *)(Ps + 2 * t);
                 Md[t] = (q.x >> 16) | (q.y & 0xFFFF0000u);
             }
@@ -274,7 +320,7 @@ __global__ void __launch_bounds__(kSweepThreads, 2) sweep_kernel(SweepArgs w)
                 const unsigned limA = 64u * (unsigned)w.a.WA;
                 unsigned *isA = (unsigned *)(slot + 16 + (((size_t)n * 2 + 15) & ~(size_t)15));
                 const int nw = split_nw(n);
-                for (int q = tid; q < nw; q += kSweepThreads) {
+                for (int q = tid; q < nw; q += T) {
                     unsigned word = 0u;
                     for (int b = 0; b < 32; ++b) {
                         const int t = q * 32 + b;
@@ -289,7 +335,7 @@ __global__ void __launch_bounds__(kSweepThreads, 2) sweep_kernel(SweepArgs w)
     // ---- state out for the next stage
     if (w.stage + 1 < w.nstages) {
         const unsigned *Ps = P0 + cur * np;
-        for (int t = tid; t < np; t += kSweepThreads) st[t] = Ps[t];
+        for (int t = tid; t < np; t += T) st[t] = Ps[t];
     }
 }
 
@@ -401,10 +447,12 @@ __device__ void build_window(const SplitSmem &s, const unsigned *M32, int n, int
         for (int u = 0; u < 4; ++u) {
             const int t0 = (base + u * 32 + lane) * 8;
             const unsigned wv[4] = {q[u].x, q[u].y, q[u].z, q[u].w};
-#pragma unroll
+            // one ballot per 16-bit pair of the 8 values in hand
+#pragma unroll 1
             for (int h = 0; h < 8; ++h) {
+                const unsigned ww = (h >> 1) == 0 ? wv[0] : (h >> 1) == 1 ? wv[1] : (h >> 1) == 2 ? wv[2] : wv[3];
                 const int t = t0 + h;
-                const unsigned d = ((h & 1) ? (wv[h >> 1] >> 16) : (wv[h >> 1] & 0xFFFFu)) - (unsigned)lo;
+                const unsigned d = ((h & 1) ? (ww >> 16) : (ww & 0xFFFFu)) - (unsigned)lo;
                 const bool in = t < n && d < 64u;
                 const unsigned bal = __ballot_sync(FULLMASK, in);
                 if (in) {
@@ -627,46 +675,29 @@ __global__ void __launch_bounds__(kSplitWarps * 32, 4) split_walk_kernel(SweepAr
             const unsigned j0 = s.off[i - lo], j1 = s.off[i - lo + 1];
             int d0 = 0, d1 = 0, d2 = 0;
             if (j1 > j0) {
-                if (j1 - j0 <= 32u) {             // one boundary per lane
-                    const bool has = lane < (int)(j1 - j0);
-                    const int b = has ? (int)list[j0 + lane] : 0;
-                    if (has) {
-                        atomicOr(s.N + (b >> 5), 1u << (b & 31));
-                        atomicOr(s.SN + (b >> 10), 1u << ((b >> 5) & 31));
-                    }
-                    __syncwarp();
-                    if (has) split_terms<NPOP>(s, b, n, n0, d0, d1, d2);
-                    __syncwarp();
-                    if (has) {
-                        atomicOr(s.O + (b >> 5), 1u << (b & 31));
-                        atomicOr(s.SO + (b >> 10), 1u << ((b >> 5) & 31));
-                        s.N[b >> 5] = 0u;
-                        s.SN[b >> 10] = 0u;
-                    }
-                    __syncwarp();
-                } else {
-                    for (unsigned j = j0 + lane; j < j1; j += 32) {
-                        const int b = list[j];
-                        atomicOr(s.N + (b >> 5), 1u << (b & 31));
-                        atomicOr(s.SN + (b >> 10), 1u << ((b >> 5) & 31));
-                    }
-                    __syncwarp();
-                    for (unsigned j = j0 + lane; j < j1; j += 32)
-                        split_terms<NPOP>(s, (int)list[j], n, n0, d0, d1, d2);
-                    __syncwarp();
-                    for (unsigned j = j0 + lane; j < j1; j += 32) {
-                        const int b = list[j];
-                        atomicOr(s.O + (b >> 5), 1u << (b & 31));
-                        atomicOr(s.SO + (b >> 10), 1u << ((b >> 5) & 31));
-                    }
-                    __syncwarp();
-                    for (unsigned j = j0 + lane; j < j1; j += 32) {
-                        const int b = list[j];
-                        s.N[b >> 5] = 0u;
-                        s.SN[b >> 10] = 0u;
-                    }
-                    __syncwarp();
+                // new run starts first, then their reductions, then merge
+                for (unsigned j = j0 + lane; j < j1; j += 32) {
+                    const int b = list[j];
+                    atomicOr(s.N + (b >> 5), 1u << (b & 31));
+                    atomicOr(s.SN + (b >> 10), 1u << ((b >> 5) & 31));
                 }
+                __syncwarp();
+#pragma unroll 1
+                for (unsigned j = j0 + lane; j < j1; j += 32)
+                    split_terms<NPOP>(s, (int)list[j], n, n0, d0, d1, d2);
+                __syncwarp();
+                for (unsigned j = j0 + lane; j < j1; j += 32) {
+                    const int b = list[j];
+                    atomicOr(s.O + (b >> 5), 1u << (b & 31));
+                    atomicOr(s.SO + (b >> 10), 1u << ((b >> 5) & 31));
+                }
+                __syncwarp();
+                for (unsigned j = j0 + lane; j < j1; j += 32) {
+                    const int b = list[j];
+                    s.N[b >> 5] = 0u;
+                    s.SN[b >> 10] = 0u;
+                }
+                __syncwarp();
                 d0 = __reduce_add_sync(FULLMASK, d0);
                 d1 = __reduce_add_sync(FULLMASK, d1);
                 if (NPOP == 2) d2 = __reduce_add_sync(FULLMASK, d2);
@@ -766,10 +797,16 @@ int split_walk_ctas(int n, int xpehh)
 cudaError_t launch_sweep_path(const SweepArgs &w0, cudaStream_t s)
 {
     SweepArgs w = w0;
-    const size_t ssm = sweep_smem_bytes(w.n, w.a.W);
-    const int E = sweep_e(w.n);
-    void (*sweep)(SweepArgs) = E <= 4 ? sweep_kernel<4> : E <= 8 ? sweep_kernel<8>
-                             : E <= 16 ? sweep_kernel<16> : sweep_kernel<32>;
+    const size_t ssm = sweep_smem_bytes(w.n, w.a.W, w.threads);
+    const int E = sweep_e(w.n, w.threads);
+    void (*sweep)(SweepArgs);
+    if (w.threads == 256)
+        sweep = E <= 8 ? sweep_kernel<256, 8> : E <= 16 ? sweep_kernel<256, 16>
+              : E <= 24 ? sweep_kernel<256, 24> : sweep_kernel<256, 64>;
+    else
+        sweep = E <= 4 ? sweep_kernel<512, 4> : E <= 8 ? sweep_kernel<512, 8>
+              : E <= 16 ? sweep_kernel<512, 16> : E <= 24 ? sweep_kernel<512, 24>
+              : sweep_kernel<512, 32>;
     cudaError_t e = cudaFuncSetAttribute(sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm);
     if (e != cudaSuccess) return e;
     const size_t wsm = (size_t)w.split_bytes * kSplitWarps;
@@ -779,7 +816,7 @@ cudaError_t launch_sweep_path(const SweepArgs &w0, cudaStream_t s)
         return e;
     for (int st = 0; st < w.nstages; ++st) {
         w.stage = st;
-        sweep<<<2 * w.nch, kSweepThreads, ssm, s>>>(w);
+        sweep<<<2 * w.nch, w.threads, ssm, s>>>(w);
         walk<<<w.walk_ctas, kSplitWarps * 32, wsm, s>>>(w);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }

@@ -17,7 +17,8 @@ from parity_util import assert_ihs_equal, assert_xpehh_equal, to_np
 pytestmark = pytest.mark.gpu
 
 SHAPES = [dict(), dict(sweep_warmup=16, sweep_stage_cores=7), dict(sweep_warmup=40, sweep_stage_cores=1),
-          dict(sweep_warmup=300, sweep_stage_cores=4096)]
+          dict(sweep_warmup=300, sweep_stage_cores=4096), dict(sweep_threads=512),
+          dict(sweep_threads=256, sweep_warmup=64, sweep_stage_cores=33)]
 
 
 @pytest.fixture(scope="module")
@@ -135,6 +136,31 @@ def test_identical_haplotypes_and_long_walks(sg):
     ref = oracle.ihs(rows, n, pos, gmap)
     for kw in (dict(), dict(sweep_warmup=16, sweep_stage_cores=9), dict(sweep_warmup=100)):
         assert_ihs_equal(run_ihs(sg, rows, n, pos, gmap, launch=sweep(sg, **kw)), ref)
+
+
+@pytest.mark.parametrize("n,threads", [(6000, 256), (6000, 512), (9000, 0)])
+def test_elements_per_thread(sg, n, threads):
+    """Samples near the register-cached limit of each CTA width, and one that
+    re-reads its elements from shared memory."""
+    m = 90
+    hap, pos, gmap = synth.tiny_mosaic(n, m, n + threads, founders=5, switch=0.05, flip=0.003)
+    rows = synth.pack(hap)
+    cores = np.array([0, 3, 44, 45, 88, 89])
+    ref = oracle.ihs(rows, n, pos, gmap, cores=cores)
+    got = run_ihs(sg, rows, n, pos, gmap,
+                  launch=sweep(sg, sweep_warmup=24, sweep_stage_cores=10, sweep_threads=threads))
+    assert_ihs_equal(got, ref, idx=cores)
+
+
+def test_xpehh_widest_rows(sg):
+    """n_A + n_B = 16383 over 129 + 128 words: rows of 514 32-bit words."""
+    nA, nB, m = 8193, 8190, 60
+    hap, pos, gmap = synth.tiny_mosaic(nA + nB, m, 4242, founders=5, switch=0.05, flip=0.003)
+    rows = np.concatenate([synth.pack(hap[:, :nA]), synth.pack(hap[:, nA:])], 1)
+    cores = np.array([0, 29, 30, 59])
+    ref = oracle.xpehh(rows, nA, nB, pos, gmap, cores=cores)
+    got = run_xpehh(sg, rows, nA, nB, pos, gmap, launch=sweep(sg, sweep_warmup=20, sweep_stage_cores=8))
+    assert_xpehh_equal(got, ref, idx=cores)
 
 
 @pytest.mark.parametrize("n", [16383, 16384])
