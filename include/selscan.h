@@ -121,7 +121,7 @@ typedef struct {
                                   second pass */
     int32_t sweep_stage_cores; /* sweep schedule: cores per chunk between walk launches,
                                   1..4096 (0 = the whole chunk, capped so that the slot
-                                  buffer stays near 4 GiB); sizes the slot buffer */
+                                  buffer stays near 12 GiB); sizes the slot buffer */
     int32_t sweep_threads;     /* sweep schedule: threads per sorting CTA, 256 or 512
                                   (0 = 256 up to 6144 haplotypes, else 512) */
 } selscan_launch;

@@ -20,7 +20,7 @@ constexpr int kDefaultProbeSteps = 48;
 constexpr int kDefaultBigGroup = 32;
 constexpr int kMaxHaplotypes = 65000;
 constexpr int kDefaultSweepWarmup = 2048;
-constexpr size_t kSweepSlotBudget = (size_t)4 << 30;   // bytes of sweep slots per scan
+constexpr size_t kSweepSlotBudget = (size_t)12 << 30;  // bytes of sweep slots per scan
 constexpr size_t kMaxSmemPerCta = 227 * 1024;
 
 struct SweepPlan {

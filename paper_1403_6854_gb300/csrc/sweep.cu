@@ -485,7 +485,7 @@ __device__ void build_window(const SplitSmem &s, const unsigned *M32, int n, int
 }
 
 struct ClassWalk {
-    unsigned long long D, S, prev, dig;
+    unsigned long long D, S, prev, dig, numD;   // numD = cut_num * D
     double acc;
     int status, stop;
     bool active;
@@ -523,6 +523,36 @@ __device__ __forceinline__ void split_terms(const SplitSmem &s, int b, int n, in
     }
 }
 
+// Steps that part more than 32 pairs (a few per walk): kept out of line so
+// that the common one-round path stays small in the instruction cache.
+template <int NPOP>
+__device__ __noinline__ void split_many(const SplitSmem &s, const unsigned short *list, unsigned j0,
+                                        unsigned j1, int n, int n0, int &d0, int &d1, int &d2)
+{
+    const int lane = threadIdx.x & 31;
+    for (unsigned j = j0 + lane; j < j1; j += 32) {
+        const int b = list[j];
+        atomicOr(s.N + (b >> 5), 1u << (b & 31));
+        atomicOr(s.SN + (b >> 10), 1u << ((b >> 5) & 31));
+    }
+    __syncwarp();
+    for (unsigned j = j0 + lane; j < j1; j += 32)
+        split_terms<NPOP>(s, (int)list[j], n, n0, d0, d1, d2);
+    __syncwarp();
+    for (unsigned j = j0 + lane; j < j1; j += 32) {
+        const int b = list[j];
+        atomicOr(s.O + (b >> 5), 1u << (b & 31));
+        atomicOr(s.SO + (b >> 10), 1u << ((b >> 5) & 31));
+    }
+    __syncwarp();
+    for (unsigned j = j0 + lane; j < j1; j += 32) {
+        const int b = list[j];
+        s.N[b >> 5] = 0u;
+        s.SN[b >> 10] = 0u;
+    }
+    __syncwarp();
+}
+
 }  // namespace
 
 size_t split_smem_per_warp(int n, int xpehh)
@@ -537,8 +567,11 @@ size_t split_scratch_per_warp(int n) { return (((size_t)n * 10) + 255) & ~(size_
 
 // Persistent: each warp takes slots of this stage (both directions) from a
 // counter and walks the cores in them.
+#ifndef SPLIT_MIN_CTAS
+#define SPLIT_MIN_CTAS 3
+#endif
 template <int NPOP>
-__global__ void __launch_bounds__(kSplitWarps * 32, 4) split_walk_kernel(SweepArgs w)
+__global__ void __launch_bounds__(kSplitWarps * 32, SPLIT_MIN_CTAS) split_walk_kernel(SweepArgs w)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -633,6 +666,7 @@ __global__ void __launch_bounds__(kSplitWarps * 32, 4) split_walk_kernel(SweepAr
         bool any = false;
 #pragma unroll
         for (int q = 0; q < NWK; ++q) {
+            cw[q].numD = (unsigned long long)w.a.cut_num * cw[q].D;
             cw[q].prev = cw[q].S;
             cw[q].dig = cw[q].S;
             cw[q].acc = 0.0;
@@ -643,29 +677,30 @@ __global__ void __launch_bounds__(kSplitWarps * 32, 4) split_walk_kernel(SweepAr
         }
 
         const long long step = dir ? 1 : -1;
-        long long pprev = __ldg(w.a.pos + k);
-        double gprev = __ldg(w.a.gmap + k);
-        long long preg = 0;
-        double greg = 0.0;
+        double gq = 0.0;        // this lane's step of the current 32-step block:
+                                // map step g >= 0, -1 past the array end, -2 a gap abort
         int lo = 1;
         if (any) build_window(s, M32, n, lo, stage, list);
         int fin = W_OK;                           // how the still-active walks end
         long long i = 1;
         for (; any; ++i) {
-            const long long x = k + step * i;
-            if (x < 0 || x >= m) { fin = W_EDGE; break; }
-            if (((i - 1) & 31) == 0) {            // positions and map of the next 32 steps
-                const long long xl = x + step * lane;
-                if (xl >= 0 && xl < m) { preg = __ldg(w.a.pos + xl); greg = __ldg(w.a.gmap + xl); }
+            if (((i - 1) & 31) == 0) {            // gaps and map steps of the next 32 steps
+                const long long xl = k + step * (i + lane), xp = xl - step;
+                if (xl < 0 || xl >= m) gq = -1.0;
+                else {
+                    const long long p1 = __ldg(w.a.pos + xl), p0 = __ldg(w.a.pos + xp);
+                    const long long bp = dir ? p1 - p0 : p0 - p1;
+                    if (bp > w.a.max_gap) gq = -2.0;
+                    else {
+                        const double g1 = __ldg(w.a.gmap + xl), g0 = __ldg(w.a.gmap + xp);
+                        double gg = dir ? g1 - g0 : g0 - g1;
+                        if (bp > w.a.gap_scale) gg = gg * ((double)w.a.gap_scale / (double)bp);
+                        gq = gg;
+                    }
+                }
             }
-            const long long px = __shfl_sync(FULLMASK, preg, (int)((i - 1) & 31));
-            const double gx = __shfl_sync(FULLMASK, greg, (int)((i - 1) & 31));
-            const long long bp = dir ? px - pprev : pprev - px;
-            if (bp > w.a.max_gap) { fin = W_GAP; break; }
-            double g = dir ? gx - gprev : gprev - gx;
-            if (bp > w.a.gap_scale) g = g * ((double)w.a.gap_scale / (double)bp);
-            pprev = px;
-            gprev = gx;
+            const double g = __shfl_sync(FULLMASK, gq, (int)((i - 1) & 31));
+            if (g < 0.0) { fin = g == -1.0 ? W_EDGE : W_GAP; break; }
             if (i > (long long)hz) { fin = W_UNFINISHED; break; }
             if (i >= lo + 64) {
                 lo += 64;
@@ -676,28 +711,27 @@ __global__ void __launch_bounds__(kSplitWarps * 32, 4) split_walk_kernel(SweepAr
             int d0 = 0, d1 = 0, d2 = 0;
             if (j1 > j0) {
                 // new run starts first, then their reductions, then merge
-                for (unsigned j = j0 + lane; j < j1; j += 32) {
-                    const int b = list[j];
-                    atomicOr(s.N + (b >> 5), 1u << (b & 31));
-                    atomicOr(s.SN + (b >> 10), 1u << ((b >> 5) & 31));
+                if (j1 - j0 <= 32u) {             // one boundary per lane, loaded once
+                    const bool has = lane < (int)(j1 - j0);
+                    const int b = has ? (int)list[j0 + lane] : 0;
+                    const unsigned bw = 1u << (b & 31), sw = 1u << ((b >> 5) & 31);
+                    if (has) {
+                        atomicOr(s.N + (b >> 5), bw);
+                        atomicOr(s.SN + (b >> 10), sw);
+                    }
+                    __syncwarp();
+                    if (has) split_terms<NPOP>(s, b, n, n0, d0, d1, d2);
+                    __syncwarp();
+                    if (has) {
+                        atomicOr(s.O + (b >> 5), bw);
+                        atomicOr(s.SO + (b >> 10), sw);
+                        s.N[b >> 5] = 0u;
+                        s.SN[b >> 10] = 0u;
+                    }
+                    __syncwarp();
+                } else {
+                    split_many<NPOP>(s, list, j0, j1, n, n0, d0, d1, d2);
                 }
-                __syncwarp();
-#pragma unroll 1
-                for (unsigned j = j0 + lane; j < j1; j += 32)
-                    split_terms<NPOP>(s, (int)list[j], n, n0, d0, d1, d2);
-                __syncwarp();
-                for (unsigned j = j0 + lane; j < j1; j += 32) {
-                    const int b = list[j];
-                    atomicOr(s.O + (b >> 5), 1u << (b & 31));
-                    atomicOr(s.SO + (b >> 10), 1u << ((b >> 5) & 31));
-                }
-                __syncwarp();
-                for (unsigned j = j0 + lane; j < j1; j += 32) {
-                    const int b = list[j];
-                    s.N[b >> 5] = 0u;
-                    s.SN[b >> 10] = 0u;
-                }
-                __syncwarp();
                 d0 = __reduce_add_sync(FULLMASK, d0);
                 d1 = __reduce_add_sync(FULLMASK, d1);
                 if (NPOP == 2) d2 = __reduce_add_sync(FULLMASK, d2);
@@ -711,7 +745,7 @@ __global__ void __launch_bounds__(kSplitWarps * 32, 4) split_walk_kernel(SweepAr
                 dA += ii * SA;
                 dB += ii * SB;
                 q.dig += ii * q.S;
-                const bool stop = below_cut(w.a, q.S, q.D);
+                const bool stop = (unsigned long long)w.a.cut_den * q.S < q.numD;
                 if (stop && !w.a.crossing) { q.stop = (int)i; q.active = false; }
                 else {
                     if (lane == 0) {
@@ -729,7 +763,7 @@ __global__ void __launch_bounds__(kSplitWarps * 32, 4) split_walk_kernel(SweepAr
                     if (!q.active) continue;
                     q.S = (unsigned long long)((long long)q.S + (c_ ? d1 : d0));
                     q.dig += ii * q.S;
-                    const bool stop = below_cut(w.a, q.S, q.D);
+                    const bool stop = (unsigned long long)w.a.cut_den * q.S < q.numD;
                     if (stop && !w.a.crossing) { q.stop = (int)i; q.active = false; continue; }
                     if (lane == 0) q.acc += (double)(q.prev + q.S) * g;
                     if (stop) { q.stop = (int)i; q.active = false; continue; }
