@@ -65,6 +65,8 @@ class Active:
     req: Request
     next_core: int = 0
     handle: object = None         # executor state
+    fp: int = 0                   # HBM bytes held while resident
+    whole: bool = False           # runs as one whole-scan launch instead of ticks
 
     @property
     def remaining(self) -> int:
@@ -78,10 +80,11 @@ class Scheduler:
     MAX_SCANS = 64                # scans one tick can carry (the C ABI's limit)
 
     def __init__(self, hbm_budget: int, tick_cores: int = 32768, max_active: int = MAX_SCANS,
-                 policy: str = "fifo"):
+                 policy: str = "fifo", footprint_fn: Optional[Callable[[Request], int]] = None):
         if policy not in self.POLICIES:
             raise ValueError(policy)
         self.policy = policy
+        self.fp = footprint_fn or footprint
         self.budget = int(hbm_budget)
         self.tick_cores = int(tick_cores)
         self.max_active = min(int(max_active), self.MAX_SCANS)
@@ -90,8 +93,8 @@ class Scheduler:
         self.used = 0
 
     def submit(self, req: Request) -> None:
-        if footprint(req) > self.budget:
-            raise ValueError(f"request {req.rid} needs {footprint(req)} B, budget {self.budget} B")
+        if self.fp(req) > self.budget:
+            raise ValueError(f"request {req.rid} needs {self.fp(req)} B, budget {self.budget} B")
         self.waiting.append(req)
 
     def cancel(self, rid: int) -> bool:
@@ -106,12 +109,12 @@ class Scheduler:
         """Admit waiting requests, in arrival order, while they fit."""
         new = []
         while self.waiting and len(self.active) < self.max_active:
-            f = footprint(self.waiting[0])
+            f = self.fp(self.waiting[0])
             if self.used + f > self.budget:
                 break
             req = self.waiting.popleft()
             self.used += f
-            a = Active(req)
+            a = Active(req, fp=f)
             self.active.append(a)
             new.append(a)
         return new
@@ -123,7 +126,7 @@ class Scheduler:
         remaining work first; "ps" equal shares).  The device walks the ranges
         in this order, one core per warp fetch.  Returns the tick's scans and
         an int64 array of units (index into that list, c0, c1)."""
-        live = [a for a in self.active if a.remaining > 0]
+        live = [a for a in self.active if a.remaining > 0 and not a.whole]
         if not live:
             return [], np.zeros((0, 3), np.int64)
         if self.policy == "srpt":
@@ -142,7 +145,7 @@ class Scheduler:
         return out, np.array(rows, np.int64).reshape(-1, 3)
 
     def has_work(self) -> bool:
-        return any(a.remaining > 0 for a in self.active)
+        return any(a.remaining > 0 and not a.whole for a in self.active)
 
     def finished(self) -> List[Active]:
         done = [a for a in self.active if a.remaining == 0]
@@ -150,7 +153,7 @@ class Scheduler:
 
     def release(self, a: Active) -> None:
         self.active.remove(a)
-        self.used -= footprint(a.req)
+        self.used -= a.fp
 
 
 def summarize(latencies: Dict[int, float], cores: int, makespan: float) -> Dict:
@@ -163,13 +166,27 @@ def summarize(latencies: Dict[int, float], cores: int, makespan: float) -> Dict:
 class GpuExecutor:
     """Runs the scheduler's ticks on the GPU through the batch C ABI.  Ticks
     alternate between two streams so that one tick's tail overlaps the next
-    tick's start; a scan is finalised after every tick that touched it."""
+    tick's start; a scan is finalised after every tick that touched it.
 
-    def __init__(self, device="cuda"):
+    Long requests (at least `whole_min_markers` markers and at most 16383
+    haplotypes) do not take ticks: each runs as one whole-scan call with the
+    sorted-sweep schedule on one of `whole_streams` side streams, its results
+    copied to pinned host memory behind it, so it completes asynchronously
+    next to the ticks.  Its footprint includes the sweep's workspace (stages
+    of `whole_stage_cores` cores keep the slot buffer near 1 GiB)."""
+
+    WHOLE_MAX_N = 16383
+
+    def __init__(self, device="cuda", whole_min_markers: int = 131072, whole_streams: int = 3,
+                 whole_stage_cores: int = 256):
         import torch
         import paper_1403_6854_gb300 as sg
         self.torch, self.sg = torch, sg
         self.device = torch.device(device)
+        self.whole_min = int(whole_min_markers)
+        self.whole_stage = int(whole_stage_cores)
+        self.wstreams = [torch.cuda.Stream(self.device) for _ in range(max(1, whole_streams))]
+        self.wk = 0
         self.streams = [torch.cuda.Stream(self.device), torch.cuda.Stream(self.device)]
         self.events = [None, None]
         self.ws = [None, None]
@@ -177,6 +194,47 @@ class GpuExecutor:
         self.k = 0
         self.last_tick = {}
 
+    # ------------------------------------------------------------ whole scans
+    def is_whole(self, req: Request) -> bool:
+        return self.whole_min > 0 and req.m >= self.whole_min and req.n_total <= self.WHOLE_MAX_N
+
+    def _whole_launch(self):
+        return self.sg.make_launch(self.sg.SCHED_SWEEP, sweep_stage_cores=self.whole_stage)
+
+    def footprint(self, req: Request) -> int:
+        f = footprint(req)
+        if self.is_whole(req):
+            mode = self.sg.MODE_IHS if req.mode == "ihs" else self.sg.MODE_XPEHH
+            f += self.sg.selscan_workspace_bytes(req.n_total, req.m, mode, self._whole_launch())
+        return f
+
+    def start_whole(self, a: Active):
+        """Queue the whole scan and the copy of its results; returns a handle
+        for poll_finish."""
+        torch, sg = self.torch, self.sg
+        req = a.req
+        st = self.wstreams[self.wk % len(self.wstreams)]
+        self.wk += 1
+        p = sg.selscan_default_params(**req.params)
+        L = self._whole_launch()
+        with torch.cuda.stream(st):
+            hap, pos, gmap = sg.to_device(req.rows, req.pos, req.gmap, self.device)
+            if req.mode == "ihs":
+                o = sg.selscan_ihs(hap, req.nA, pos, gmap, params=p, launch=L, stream=st)
+                o["ihh_a"], o["ihh_b"] = o["ihh1"], o["ihh0"]
+            else:
+                o = sg.selscan_xpehh(hap, req.nA, req.nB, pos, gmap, params=p, launch=L, stream=st)
+                o["ihh_a"], o["ihh_b"] = o["ihhA"], o["ihhB"]
+            host = {}
+            for f in self.FIELDS:
+                h = torch.empty(o[f].shape, dtype=o[f].dtype, pin_memory=True)
+                h.copy_(o[f], non_blocking=True)
+                host[f] = h
+        done = torch.cuda.Event()
+        done.record(st)
+        return (done, host, (o, hap, pos, gmap))
+
+    # ------------------------------------------------------------ ticks
     def upload(self, req: Request):
         torch, sg = self.torch, self.sg
         dev = self.device
@@ -299,6 +357,7 @@ class _Loop:
         self.finishing: List[Tuple[Active, object]] = []
         self.cancelled = set()
         self.async_finish = hasattr(executor, "start_finish")
+        self.whole = hasattr(executor, "start_whole")
 
     def busy(self) -> bool:
         return bool(self.sch.waiting or self.sch.active or self.finishing)
@@ -322,7 +381,12 @@ class _Loop:
         sch, ex = self.sch, self.ex
         done = []
         for a in sch.admit():
-            a.handle = ex.upload(a.req)
+            if self.whole and ex.is_whole(a.req):
+                a.whole = True
+                a.next_core = a.req.m
+                self.finishing.append((a, ex.start_whole(a)))
+            else:
+                a.handle = ex.upload(a.req)
         if sch.has_work() and hasattr(ex, "wait_slot"):
             ex.wait_slot()      # at most two ticks in flight: new scans join the next one
         live, units = sch.compose_tick()
@@ -359,7 +423,8 @@ def serve(requests: List[Request], executor, hbm_budget: int, tick_cores: int = 
           realtime: bool = True, policy: str = "fifo") -> Tuple[Dict[int, Dict], Dict[int, float], float]:
     """Replay requests (by arrival time; realtime=False submits all at once).
     Returns results, latencies (result on the host - arrival), makespan."""
-    loop = _Loop(Scheduler(hbm_budget, tick_cores, policy=policy), executor)
+    loop = _Loop(Scheduler(hbm_budget, tick_cores, policy=policy,
+                           footprint_fn=getattr(executor, "footprint", None)), executor)
     pending = deque(sorted(requests, key=lambda r: r.arrival))
     results, latency = {}, {}
     t0 = clock()
@@ -388,7 +453,8 @@ class Server:
     def __init__(self, executor, hbm_budget: int, tick_cores: int = 32768, policy: str = "fifo",
                  idle_wait: float = 0.002):
         import threading
-        self._loop = _Loop(Scheduler(hbm_budget, tick_cores, policy=policy), executor)
+        self._loop = _Loop(Scheduler(hbm_budget, tick_cores, policy=policy,
+                                     footprint_fn=getattr(executor, "footprint", None)), executor)
         self._lock = threading.Lock()
         self._inbox: deque = deque()
         self._cancels: deque = deque()
@@ -402,8 +468,9 @@ class Server:
 
     def submit(self, req: Request):
         from concurrent.futures import Future
-        if footprint(req) > self._loop.sch.budget:
-            raise ValueError(f"request {req.rid} needs {footprint(req)} B, budget {self._loop.sch.budget} B")
+        need = self._loop.sch.fp(req)
+        if need > self._loop.sch.budget:
+            raise ValueError(f"request {req.rid} needs {need} B, budget {self._loop.sch.budget} B")
         fut = Future()
         with self._lock:
             if self._stop:

@@ -59,6 +59,23 @@ def test_served_results_equal_alone(sg):
         np.testing.assert_allclose(got["lnratio"][ok], ref["lnratio"][ok], rtol=0, atol=LN_ATOL)
 
 
+def test_whole_scans_next_to_ticks_equal_alone(sg):
+    """Requests above the whole-scan threshold run as one sorted-sweep call on a
+    side stream while the others take ticks; every result equals the scan alone."""
+    from paper_1403_6854_gb300.serve import GpuExecutor, serve
+    reqs = make_requests()
+    ex = GpuExecutor(whole_min_markers=2600, whole_stage_cores=37)
+    assert {r.rid for r in reqs if ex.is_whole(r)} == {0, 2, 4}
+    budget = sum(ex.footprint(r) for r in reqs)
+    res, lat, mk = serve(reqs, ex, budget, tick_cores=700, realtime=False)
+    for r in reqs:
+        got, ref = res[r.rid], alone(sg, r)
+        for f in ("status", "n1", "stop", "digest"):
+            assert np.array_equal(got[f], ref[f]), (r.rid, f)
+        np.testing.assert_allclose(got["ihh_a"], ref["ihh_a"], rtol=IHH_RTOL, atol=0)
+        np.testing.assert_allclose(got["ihh_b"], ref["ihh_b"], rtol=IHH_RTOL, atol=0)
+
+
 def test_server_futures_equal_alone(sg):
     """The online form: futures resolve to the same results; a cancelled
     resident scan frees its memory and the rest complete."""
