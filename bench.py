@@ -192,6 +192,9 @@ def run_reference(args, rank, world):
     }), flush=True)
 
 
+SWEEP_DRAM_BYTES_PER_CORE = 6.4186e9 / 125020
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -340,6 +343,15 @@ def main():
     if rank == 0:
         hbm, src = peaks()
         achieved = walk_bytes / (walk_ms / 1e3) / 1e9
+        # DRAM bytes of the sorted-sweep kernels from one ncu capture of the
+        # 250k-marker case (dram__bytes_read.sum + dram__bytes_write.sum of
+        # sweep_kernel and split_walk_kernel: 6.42 GB over 125,020 core loci),
+        # scaled by core loci
+        traffic, traffic_note = None, "no capture for this schedule"
+        if launch_fields.get("schedule") == 3:
+            traffic = cores * SWEEP_DRAM_BYTES_PER_CORE
+            traffic_note = ("ncu capture of the 250k case, 51,340 DRAM bytes per core locus, "
+                            "scaled by core loci")
         line = {
             "metric": METRIC, "value": value, "unit": "core loci/s", "n_gpus": world,
             "steps": K, "warmup": Wm, "ms_per_step": ms_max / K, "higher_is_better": True,
@@ -355,7 +367,7 @@ def main():
                        "l2": "inputs larger than L2 (packed matrix 632 MB), no flush",
                        "parallelism": f"weak: one chromosome (seed = rank) per GPU x{world}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": achieved / hbm, "traffic": None,
+                         "frac": achieved / hbm, "traffic": traffic, "traffic_note": traffic_note,
                          "kernel": ("sweep_kernel + split_walk_kernel, all stages, and the "
                                     "second per-step pass" if launch_fields.get("schedule") == 3
                                     else "walk_persistent_kernel (both passes)"),

@@ -587,10 +587,13 @@ __global__ void __launch_bounds__(kSplitWarps * 32, SPLIT_MIN_CTAS) split_walk_k
         if (lane == 0) gs = atomicAdd(w.walk_head, 1ull);
         gs = __shfl_sync(FULLMASK, gs, 0);
         if (gs >= (unsigned long long)(2 * per_dir)) break;
+        // slot counts are below 2^31 (2 x chunks x stage cores): 32-bit decode
+        const unsigned gsl = (unsigned)gs;
         const long long gslot = (long long)gs;
-        const int dir = (int)(gslot / per_dir);
-        const int c = (int)((gslot / w.R) % w.nch);
-        const int r = (int)(gslot % w.R);
+        const unsigned cr = gsl / (unsigned)w.R;
+        const int r = (int)(gsl - cr * (unsigned)w.R);
+        const int dir = cr >= (unsigned)w.nch ? 1 : 0;
+        const int c = (int)(cr - (unsigned)dir * (unsigned)w.nch);
         const long long c0 = (long long)c * w.B;
         if (c0 >= m) continue;
         const long long c1 = c0 + w.B < m ? c0 + w.B : m;
@@ -712,9 +715,12 @@ __global__ void __launch_bounds__(kSplitWarps * 32, SPLIT_MIN_CTAS) split_walk_k
             if (j1 > j0) {
                 // new run starts first, then their reductions, then merge
                 if (j1 - j0 <= 32u) {             // one boundary per lane, loaded once
-                    const bool has = lane < (int)(j1 - j0);
+                    bool has = lane < (int)(j1 - j0);
                     const int b = has ? (int)list[j0 + lane] : 0;
+                    // an iHS class whose walk has ended needs its runs no more
+                    if (NPOP == 1) has = has && (b < n0 ? cw[0].active : cw[NWK - 1].active);
                     const unsigned bw = 1u << (b & 31), sw = 1u << ((b >> 5) & 31);
+                    if (__ballot_sync(FULLMASK, has) != 0u) {
                     if (has) {
                         atomicOr(s.N + (b >> 5), bw);
                         atomicOr(s.SN + (b >> 10), sw);
@@ -729,6 +735,7 @@ __global__ void __launch_bounds__(kSplitWarps * 32, SPLIT_MIN_CTAS) split_walk_k
                         s.SN[b >> 10] = 0u;
                     }
                     __syncwarp();
+                    }
                 } else {
                     split_many<NPOP>(s, list, j0, j1, n, n0, d0, d1, d2);
                 }
