@@ -500,7 +500,10 @@ __device__ __forceinline__ void split_terms(const SplitSmem &s, int b, int n, in
     const int p = prev_set<true>(s, b);
     const int rr = next_set<true>(s, b, n);
     const bool old = (s.O[p >> 5] >> (p & 31)) & 1u;
-    const int e = old ? next_set<false>(s, b, n) : 0;
+    // the old run [p, e) that b splits ends at the first old start after b: rr
+    // itself unless rr is another boundary of this step
+    int e = 0;
+    if (old) e = ((s.O[rr >> 5] >> (rr & 31)) & 1u) ? rr : next_set<false>(s, rr, n);
     if (NPOP == 2) {
         const unsigned ab = count_a(s, b), ar = count_a(s, rr);
         const unsigned la = ar - ab, lb = (unsigned)(rr - b) - la;
