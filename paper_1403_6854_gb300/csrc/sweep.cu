@@ -48,22 +48,22 @@ __host__ __device__ inline int sweep_npad(int n, int T) { return sweep_e(n, T) *
 __host__ __device__ inline int split_nw(int n) { return (n + 32) >> 5; }   // bits 0..n
 
 // ---- prefix-state algebra of the stable partition --------------------------
-// A segment of the current order summarised as: minimum run length over the
-// segment, the running minimum since the last allele-0 / allele-1 element
-// (or the whole-segment minimum if the segment has none), the number of
-// allele-0 elements, and whether each allele occurs.  Packed in two words:
-// p0 = min_all | tail0 << 16; p1 = tail1 | zeros << 16 | seen0 << 30 | seen1 << 31.
-__device__ __forceinline__ void compose(unsigned l0, unsigned l1, unsigned &r0, unsigned &r1)
+// A segment of the current order summarised as: the running minimum of the
+// run lengths since its last allele-0 / allele-1 element (or over the whole
+// segment if it has none) -- the "tails" -- the minimum over the segment, the
+// number of allele-0 elements, and whether each allele occurs.  Packed in
+// two words: A = tail0 | tail1 << 16; B = min | zeros << 16 | seen0 << 30 |
+// seen1 << 31.  compose(L, R) replaces R by the summary of L followed by R;
+// both tails are continued through R with one 16-bit SIMD minimum.
+__device__ __forceinline__ void compose(unsigned lA, unsigned lB, unsigned &rA, unsigned &rB)
 {
-    const unsigned lall = l0 & 0xFFFFu, lt0 = l0 >> 16, lt1 = l1 & 0xFFFFu;
-    const unsigned rall = r0 & 0xFFFFu, rt0 = r0 >> 16, rt1 = r1 & 0xFFFFu;
-    const unsigned all = min(lall, rall);
-    const unsigned t0 = (r1 >> 30) & 1u ? rt0 : min(lt0, rall);
-    const unsigned t1 = (r1 >> 31) ? rt1 : min(lt1, rall);
-    const unsigned zeros = ((l1 >> 16) & 0x3FFFu) + ((r1 >> 16) & 0x3FFFu);
-    const unsigned flags = (l1 | r1) & 0xC0000000u;
-    r0 = all | (t0 << 16);
-    r1 = t1 | (zeros << 16) | flags;
+    const unsigned rmin2 = __byte_perm(rB, 0u, 0x1010u);          // R's minimum in both halves
+    const unsigned cont = __vminu2(lA, rmin2);                     // L's tails continued through R
+    const unsigned f = rB >> 30;                                   // alleles present in R
+    const unsigned keep = ((f & 1u) ? 0x0000FFFFu : 0u) | ((f & 2u) ? 0xFFFF0000u : 0u);
+    rA = (rA & keep) | (cont & ~keep);
+    const unsigned mn = min(lB & 0xFFFFu, rB & 0xFFFFu);
+    rB = mn | ((lB & 0x3FFF0000u) + (rB & 0x3FFF0000u)) | ((lB | rB) & 0xC0000000u);
 }
 constexpr unsigned kId0 = 0xFFFFFFFFu;
 constexpr unsigned kId1 = 0x0000FFFFu;
@@ -211,8 +211,8 @@ __global__ void __launch_bounds__(T, T == 512 ? 2 : 3) sweep_kernel(SweepArgs w)
             }
         }
         const unsigned zeros = (unsigned)E - (unsigned)__popc(vmask);
-        unsigned p0 = all | (mn0 << 16);
-        unsigned p1 = mn1 | (zeros << 16) | (hp0 << 30) | (hp1 << 31);
+        unsigned p0 = mn0 | (mn1 << 16);
+        unsigned p1 = all | (zeros << 16) | (hp0 << 30) | (hp1 << 31);
         // warp inclusive scan
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
@@ -259,7 +259,7 @@ __global__ void __launch_bounds__(T, T == 512 ? 2 : 3) sweep_kernel(SweepArgs w)
         }
         if (!CACHE) {
             // second sweep over the segment for the run lengths (large samples)
-            unsigned a0 = x0 >> 16, a1 = x1 & 0xFFFFu;
+            unsigned a0 = x0 & 0xFFFFu, a1 = x0 >> 16;
             unsigned h0 = (x1 >> 30) & 1u, h1 = x1 >> 31;
             z = zs;
             o = os;
@@ -283,11 +283,11 @@ __global__ void __launch_bounds__(T, T == 512 ? 2 : 3) sweep_kernel(SweepArgs w)
             }
         } else {
             if (hp0) {                            // first allele-0 element of the segment
-                const unsigned out = ((x1 >> 30) & 1u) ? min(min(x0 >> 16, f0min) + 1u, kInf16) : 0u;
+                const unsigned out = ((x1 >> 30) & 1u) ? min(min(x0 & 0xFFFFu, f0min) + 1u, kInf16) : 0u;
                 Pn[zs] = f0bi | (out << 16);
             }
             if (hp1) {
-                const unsigned out = (x1 >> 31) ? min(min(x1 & 0xFFFFu, f1min) + 1u, kInf16) : 0u;
+                const unsigned out = (x1 >> 31) ? min(min(x0 >> 16, f1min) + 1u, kInf16) : 0u;
                 Pn[os] = f1bi | (out << 16);
             }
         }
@@ -311,10 +311,14 @@ __global__ void __launch_bounds__(T, T == 512 ? 2 : 3) sweep_kernel(SweepArgs w)
                 hdr[1] = (int)hz;
             }
             const unsigned *Ps = P0 + cur * np;
-            unsigned *Md = (unsigned *)(slot + 16);
-            for (int t = tid; t < (n + 1) / 2; t += T) {
-                const uint2 q = *(const uint2 *)(Ps + 2 * t);
-                Md[t] = (q.x >> 16) | (q.y & 0xFFFF0000u);
+            // run lengths, 8 per 16-byte store (np is a multiple of 512, the
+            // slot's M region a multiple of 16 bytes; values past n are never read)
+            const uint4 *P4 = (const uint4 *)Ps;
+            uint4 *M4 = (uint4 *)(slot + 16);
+            for (int t = tid; t < (n + 7) / 8; t += T) {
+                const uint4 a = P4[2 * t], b = P4[2 * t + 1];
+                M4[t] = make_uint4((a.x >> 16) | (a.y & 0xFFFF0000u), (a.z >> 16) | (a.w & 0xFFFF0000u),
+                                   (b.x >> 16) | (b.y & 0xFFFF0000u), (b.z >> 16) | (b.w & 0xFFFF0000u));
             }
             if (w.a.nB > 0) {                    // population of each sorted position
                 const unsigned limA = 64u * (unsigned)w.a.WA;
