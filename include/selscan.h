@@ -86,6 +86,12 @@ typedef struct {
     int64_t max_gap_bp;                  /* default 200000: b > 200 kbp => abort */
     int32_t include_crossing_term;       /* 0 (default) or 1 */
     int32_t xpehh_maf_filter;            /* 0 (default): XPEHH at every marker */
+    int32_t use_physical_map;            /* 0 (default): g = genetic-map distance (Section 1.2);
+                                            1: g = physical distance in position units (the
+                                            rehh convention of Section 2), same gap rules; the
+                                            map's values are then neither read for g nor
+                                            checked, but gmap must still point to m doubles */
+    int32_t reserved;                    /* 0 */
 } selscan_params;
 
 /* Scheduling of the walk kernels.  Changes how the work runs, never the
@@ -268,6 +274,25 @@ int selscan_batch_run(const selscan_scan *scans, int32_t nscans, const int32_t *
                       int32_t max_n_total, int64_t max_ld, void *workspace, size_t ws_bytes,
                       void *stream);
 int selscan_batch_finalize(const selscan_scan *scan, void *stream);
+
+/* Standardised scores (Eq. 7 for iHS, Eq. 11 for XPEHH).  Markers with
+ * status[k] == SELSCAN_LOCUS_OK are grouped by the derived-allele frequency of
+ * the core, n1[k] / n, into nbins equal bins, bin = min(nbins - 1,
+ * floor(nbins * n1 / n)) decided in integers (nbins = 1: one genome-wide bin,
+ * as XPEHH's normalisation uses; n = n_A + n_B there).  Each bin's mean and
+ * standard deviation (sample SD, count - 1 in the denominator) are taken over
+ * the markers passed in -- concatenate the chromosomes of a genome into one
+ * call -- and out[k] = (score[k] - mean) / SD; NaN for markers that are not OK
+ * and for bins with fewer than two scores or SD 0.  All arrays are device
+ * memory: score, status, n1, out [m] (the outputs of selscan_ihs /
+ * selscan_xpehh: lnratio, status, n1), bin_count / bin_mean / bin_sd [nbins].
+ * The reduction is deterministic (fixed summation order).  Workspace:
+ * selscan_normalize_workspace_bytes(nbins), 256-byte aligned. */
+#define SELSCAN_NORM_MAX_BINS 1024
+size_t selscan_normalize_workspace_bytes(int32_t nbins);
+int selscan_normalize(const double *score, const int8_t *status, const int32_t *n1, int64_t m,
+                      int32_t n, int32_t nbins, double *out, int64_t *bin_count, double *bin_mean,
+                      double *bin_sd, void *workspace, size_t ws_bytes, void *stream);
 
 /* Pack a 0/1 uint8 matrix into rows (Section 1.1 coding, 0 ancestral / 1
  * derived).  hap_major = 0: hap01 is [m][n] (marker-major); 1: [n][m].

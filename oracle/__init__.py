@@ -33,14 +33,16 @@ class Params(ctypes.Structure):
                 ("maf_num", ctypes.c_uint32), ("maf_den", ctypes.c_uint32),
                 ("gap_scale_bp", ctypes.c_int64), ("max_gap_bp", ctypes.c_int64),
                 ("include_crossing_term", ctypes.c_int32),
-                ("xpehh_maf_filter", ctypes.c_int32)]
+                ("xpehh_maf_filter", ctypes.c_int32),
+                ("use_physical_map", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 def params(ehh_cut=(1, 20), maf=(1, 20), gap_scale_bp=20_000, max_gap_bp=200_000,
-           include_crossing_term=0, xpehh_maf_filter=0) -> Params:
-    """Section 1.2 defaults: EHH cutoff 0.05, MAF 0.05, 20 kbp scale, 200 kbp abort."""
+           include_crossing_term=0, xpehh_maf_filter=0, use_physical_map=0) -> Params:
+    """Section 1.2 defaults: EHH cutoff 0.05, MAF 0.05, 20 kbp scale, 200 kbp abort;
+    use_physical_map=1 integrates over physical distance (the Section 2 option)."""
     return Params(ehh_cut[0], ehh_cut[1], maf[0], maf[1], gap_scale_bp, max_gap_bp,
-                  include_crossing_term, xpehh_maf_filter)
+                  include_crossing_term, xpehh_maf_filter, use_physical_map, 0)
 
 
 def build(force: bool = False) -> str:
@@ -147,3 +149,34 @@ def ehh(rows, n: int, pos, gmap, locus: int, capacity: int,
     if rc != 0:
         raise ValueError("oracle_ehh: invalid arguments")
     return out
+
+
+def normalize(score, status, n1, n: int, nbins: int) -> dict:
+    """Standardised scores: Eq. 7 (iHS, nbins equal bins of the core's derived
+    allele frequency n1 / n) and Eq. 11 (XPEHH, nbins = 1, genome-wide).  Only
+    markers of status OK enter a bin; a bin's E and SD are its mean and sample
+    standard deviation (count - 1); scores of bins with fewer than two values
+    or SD 0, and markers that are not OK, are NaN."""
+    score = np.asarray(score, dtype=np.float64)
+    status = np.asarray(status)
+    n1 = np.asarray(n1, dtype=np.int64)
+    if nbins == 1:
+        bins = np.zeros(score.size, dtype=np.int64)
+    else:
+        bins = np.minimum(nbins - 1, (n1 * nbins) // n)
+    ok = status == OK
+    out = np.full(score.size, np.nan)
+    count = np.zeros(nbins, dtype=np.int64)
+    mean = np.full(nbins, np.nan)
+    sd = np.full(nbins, np.nan)
+    for b in range(nbins):
+        sel = ok & (bins == b)
+        vals = score[sel]
+        count[b] = vals.size
+        if vals.size >= 1:
+            mean[b] = vals.mean()
+        if vals.size >= 2:
+            sd[b] = vals.std(ddof=1)
+            if sd[b] > 0:
+                out[sel] = (vals - mean[b]) / sd[b]
+    return dict(score=out, count=count, mean=mean, sd=sd)

@@ -63,6 +63,8 @@ typedef struct {
     int64_t max_gap_bp;
     int32_t include_crossing_term;
     int32_t xpehh_maf_filter;
+    int32_t use_physical_map;   /* g = physical distance b instead of the map (Section 2) */
+    int32_t reserved;
 } oracle_params;
 
 enum { ST_OK = 0, ST_MAF_FILTERED = 1, ST_UNDEFINED = 2, ST_ABORT_EDGE = 3, ST_ABORT_GAP = 4 };
@@ -201,7 +203,7 @@ static walk_out walk(const uint64_t *rows, int64_t ld, int64_t m, const int64_t 
         if (x < 0 || x >= m) { o.status = ST_ABORT_EDGE; o.stop = (int32_t)i; break; }
         int64_t b = pos[x] > pos[xp] ? pos[x] - pos[xp] : pos[xp] - pos[x];
         if (b > p->max_gap_bp) { o.status = ST_ABORT_GAP; o.stop = (int32_t)i; break; }
-        double g = fabs(gmap[x] - gmap[xp]);
+        double g = p->use_physical_map ? (double)b : fabs(gmap[x] - gmap[xp]);
         if (b > p->gap_scale_bp)
             g = g * (((double)p->gap_scale_bp / 1000.0) / ((double)b / 1000.0));
 
@@ -238,7 +240,8 @@ static walk_out walk(const uint64_t *rows, int64_t ld, int64_t m, const int64_t 
 static int params_ok(const oracle_params *p)
 {
     return p && p->ehh_cut_den > 0 && p->maf_den > 0 && p->ehh_cut_num <= p->ehh_cut_den &&
-           p->maf_num <= p->maf_den && p->gap_scale_bp > 0 && p->max_gap_bp >= 0;
+           p->maf_num <= p->maf_den && p->gap_scale_bp > 0 && p->max_gap_bp >= 0 &&
+           (p->use_physical_map == 0 || p->use_physical_map == 1);
 }
 
 static void set_members(strings *s, int32_t n, const int32_t *list, const int8_t *popid,

@@ -39,7 +39,8 @@ class selscan_params(ctypes.Structure):
     _fields_ = [("ehh_cut_num", ctypes.c_uint32), ("ehh_cut_den", ctypes.c_uint32),
                 ("maf_num", ctypes.c_uint32), ("maf_den", ctypes.c_uint32),
                 ("gap_scale_bp", ctypes.c_int64), ("max_gap_bp", ctypes.c_int64),
-                ("include_crossing_term", ctypes.c_int32), ("xpehh_maf_filter", ctypes.c_int32)]
+                ("include_crossing_term", ctypes.c_int32), ("xpehh_maf_filter", ctypes.c_int32),
+                ("use_physical_map", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class selscan_launch(ctypes.Structure):
@@ -77,7 +78,8 @@ class selscan_scan(ctypes.Structure):
 EXPORTS = ("selscan_default_params", "selscan_workspace_bytes", "selscan_ihs", "selscan_xpehh",
            "selscan_ehh", "selscan_ehh_noalloc", "selscan_pack", "selscan_strerror",
            "selscan_batch_item_bytes", "selscan_batch_workspace_bytes", "selscan_batch_prepare",
-           "selscan_batch_run", "selscan_batch_finalize", "selscan_launch_count")
+           "selscan_batch_run", "selscan_batch_finalize", "selscan_launch_count",
+           "selscan_normalize", "selscan_normalize_workspace_bytes")
 EHH_NOALLOC_MAX_N = 8192
 
 _lib = None
@@ -129,6 +131,11 @@ def load_library():
     lib.selscan_batch_run.argtypes = [ctypes.POINTER(selscan_scan), ctypes.c_int32, _P, _P, _P,
                                       ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, _P,
                                       ctypes.c_size_t, _P]
+    lib.selscan_normalize_workspace_bytes.restype = ctypes.c_size_t
+    lib.selscan_normalize_workspace_bytes.argtypes = [ctypes.c_int32]
+    lib.selscan_normalize.restype = ctypes.c_int
+    lib.selscan_normalize.argtypes = [_P, _P, _P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                      _P, _P, _P, _P, _P, ctypes.c_size_t, _P]
     lib.selscan_launch_count.restype = ctypes.c_int32
     lib.selscan_launch_count.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, _P]
     lib.selscan_batch_finalize.restype = ctypes.c_int
@@ -178,6 +185,30 @@ def make_launch(schedule: int = SCHED_DEFAULT, warps_per_cta: int = 0, ctas_per_
         L.walk_begin_event = ctypes.c_void_p(events[0].cuda_event)
         L.walk_end_event = ctypes.c_void_p(events[1].cuda_event)
     return L
+
+
+def selscan_normalize(score: torch.Tensor, status: torch.Tensor, n1: torch.Tensor, n: int,
+                      nbins: int, stream=None) -> Dict[str, torch.Tensor]:
+    """Standardised scores (Eq. 7 / Eq. 11) of lnratio/status/n1 device tensors
+    (nbins = 1 for XPEHH's genome-wide normalisation)."""
+    lib = load_library()
+    m = score.numel()
+    dev = score.device
+    out = dict(score=torch.empty(m, dtype=torch.float64, device=dev),
+               count=torch.empty(nbins, dtype=torch.int64, device=dev),
+               mean=torch.empty(nbins, dtype=torch.float64, device=dev),
+               sd=torch.empty(nbins, dtype=torch.float64, device=dev))
+    nb = int(lib.selscan_normalize_workspace_bytes(nbins))
+    if nb == 0:
+        raise SelscanError(ERR_INVALID_ARG, "selscan_normalize_workspace_bytes")
+    ws = _workspace(nb, dev, None)
+    rc = lib.selscan_normalize(_ptr(score), _ptr(status), _ptr(n1), m, n, nbins, _ptr(out["score"]),
+                               _ptr(out["count"]), _ptr(out["mean"]), _ptr(out["sd"]), _ptr(ws),
+                               ws.numel(), _stream(stream))
+    if rc != OK:
+        raise SelscanError(rc, "selscan_normalize")
+    out["_workspace"] = ws
+    return out
 
 
 def selscan_launch_count(n_total: int, m: int, mode: int,

@@ -10,7 +10,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libselscan_gb300.so")
-SOURCES = ["api.cu", "kernels.cu", "batch.cu", "noalloc.cu", "sweep.cu"]
+SOURCES = ["api.cu", "kernels.cu", "batch.cu", "noalloc.cu", "sweep.cu", "normalize.cu"]
 HEADERS = ["walk.cuh", "internal.h", "device_common.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")

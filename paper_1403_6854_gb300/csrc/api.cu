@@ -51,7 +51,8 @@ inline size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
 bool params_ok(const selscan_params *p)
 {
     return p && p->ehh_cut_den > 0 && p->maf_den > 0 && p->gap_scale_bp > 0 && p->max_gap_bp >= 0 &&
-           (p->include_crossing_term == 0 || p->include_crossing_term == 1);
+           (p->include_crossing_term == 0 || p->include_crossing_term == 1) &&
+           (p->use_physical_map == 0 || p->use_physical_map == 1);
 }
 
 SweepPlan make_sweep_plan(int n_total, long long m, int mode, const selscan_launch *L)
@@ -215,6 +216,7 @@ ScanArgs make_args(const uint64_t *hap, int64_t ld, int nA, int nB, int64_t m, c
     a.gap_scale = p->gap_scale_bp;
     a.max_gap = p->max_gap_bp;
     a.crossing = p->include_crossing_term;
+    a.physical = p->use_physical_map;
     return a;
 }
 
@@ -275,7 +277,8 @@ int run_scan(int mode, const uint64_t *hap, int64_t ld, int32_t nA, int32_t nB, 
     if ((e = cudaMemsetAsync(ws, 0, l.item_status, s)) != cudaSuccess) return SELSCAN_ERR_CUDA;
     if ((e = cudaMemsetAsync(ws + l.bucket, 0, (NBUCKET + 1) * 4, s)) != cudaSuccess) return SELSCAN_ERR_CUDA;
     if ((e = cudaMemsetAsync(err, 0, sizeof(int32_t), s)) != cudaSuccess) return SELSCAN_ERR_CUDA;
-    if (launch_validate((const long long *)pos, gmap, m, err, s) != cudaSuccess) return SELSCAN_ERR_CUDA;
+    if (launch_validate((const long long *)pos, gmap, m, err, s, !p->use_physical_map) != cudaSuccess)
+        return SELSCAN_ERR_CUDA;
     if (launch_core_select(a, sk.mode, p->maf_num, p->maf_den, p->xpehh_maf_filter, n1, status, s) !=
         cudaSuccess)
         return SELSCAN_ERR_CUDA;
@@ -335,6 +338,8 @@ void selscan_default_params(selscan_params *p)
     p->max_gap_bp = 200000;
     p->include_crossing_term = 0;
     p->xpehh_maf_filter = 0;
+    p->use_physical_map = 0;
+    p->reserved = 0;
 }
 
 size_t selscan_workspace_bytes(int32_t n_total, int64_t m, int32_t mode, const selscan_launch *launch)
@@ -413,7 +418,8 @@ int selscan_ehh(const uint64_t *hap, int64_t ld, int32_t n, int64_t m, const int
     Scratch sc = make_scratch((unsigned char *)workspace, l, n, plan);
     sc.err = out->error;
     if (cudaMemsetAsync(out->error, 0, sizeof(int32_t), s) != cudaSuccess) return SELSCAN_ERR_CUDA;
-    if (launch_validate((const long long *)pos_bp, gmap, m, out->error, s) != cudaSuccess)
+    if (launch_validate((const long long *)pos_bp, gmap, m, out->error, s, !p->use_physical_map) !=
+        cudaSuccess)
         return SELSCAN_ERR_CUDA;
     if (launch_ehh(a, locus, sc, (unsigned long long *)out->S, capacity, (long long *)out->len,
                    out->stop, out->status, out->ihh, (unsigned long long *)out->denom, s) !=

@@ -116,7 +116,8 @@ bool scan_ok(const selscan_scan *s)
     if (s->m < 1 || s->m >= (1ll << 30) || s->ld < (s->nA + 63) / 64 + (nB + 63) / 64) return false;
     const selscan_params *p = &s->params;
     if (p->ehh_cut_den == 0 || p->maf_den == 0 || p->gap_scale_bp <= 0 || p->max_gap_bp < 0 ||
-        (p->include_crossing_term != 0 && p->include_crossing_term != 1))
+        (p->include_crossing_term != 0 && p->include_crossing_term != 1) ||
+        (p->use_physical_map != 0 && p->use_physical_map != 1))
         return false;
     return ((uintptr_t)s->items & 255) == 0;
 }
@@ -142,6 +143,7 @@ BatchDesc make_desc(const selscan_scan *s)
     a.gap_scale = s->params.gap_scale_bp;
     a.max_gap = s->params.max_gap_bp;
     a.crossing = s->params.include_crossing_term;
+    a.physical = s->params.use_physical_map;
     size_t off_ihh = 0;
     item_bytes_layout(s->m, s->mode, &off_ihh);
     ItemSink &k = d.sk;
@@ -223,7 +225,8 @@ int selscan_batch_prepare(const selscan_scan *s, void *stream)
     const size_t ib = item_bytes_layout(s->m, s->mode, &off_ihh);
     if (cudaMemsetAsync(s->items, 0, ib, st) != cudaSuccess) return SELSCAN_ERR_CUDA;
     if (cudaMemsetAsync(s->error, 0, sizeof(int32_t), st) != cudaSuccess) return SELSCAN_ERR_CUDA;
-    if (launch_validate((const long long *)s->pos_bp, s->gmap, s->m, s->error, st) != cudaSuccess)
+    if (launch_validate((const long long *)s->pos_bp, s->gmap, s->m, s->error, st,
+                        !s->params.use_physical_map) != cudaSuccess)
         return SELSCAN_ERR_CUDA;
     if (launch_core_select(d.a, d.sk.mode, s->params.maf_num, s->params.maf_den,
                            s->params.xpehh_maf_filter, s->n1, s->status, st) != cudaSuccess)

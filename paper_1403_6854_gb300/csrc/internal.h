@@ -79,7 +79,7 @@ __host__ __device__ constexpr size_t scratch_per_warp(int n_total)
 
 // kernel launchers (kernels.cu)
 cudaError_t launch_validate(const long long *pos, const double *gmap, long long m, int32_t *err,
-                            cudaStream_t s);
+                            cudaStream_t s, int check_map = 1);
 cudaError_t launch_core_select(const ScanArgs &a, int mode, unsigned maf_num, unsigned maf_den,
                                int maf_filter, int32_t *n1, int8_t *core_status, cudaStream_t s);
 cudaError_t launch_walk(const ScanArgs &a, const ItemSink &sink, const Scratch &sc,

@@ -17,23 +17,25 @@
 namespace selscan {
 
 // ------------------------------------------------------------ validate
-__global__ void validate_kernel(const long long *pos, const double *gmap, long long m, int32_t *err)
+__global__ void validate_kernel(const long long *pos, const double *gmap, long long m, int32_t *err,
+                                int check_map)
 {
     for (long long k = 1 + blockIdx.x * (long long)blockDim.x + threadIdx.x; k < m;
          k += (long long)gridDim.x * blockDim.x) {
-        if (pos[k] < pos[k - 1] || !(gmap[k] >= gmap[k - 1])) atomicExch(err, SELSCAN_ERR_UNSORTED);
+        if (pos[k] < pos[k - 1] || (check_map && !(gmap[k] >= gmap[k - 1])))
+            atomicExch(err, SELSCAN_ERR_UNSORTED);
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0 && m >= 1 && !(gmap[0] == gmap[0]))
+    if (check_map && blockIdx.x == 0 && threadIdx.x == 0 && m >= 1 && !(gmap[0] == gmap[0]))
         atomicExch(err, SELSCAN_ERR_UNSORTED);
 }
 
 cudaError_t launch_validate(const long long *pos, const double *gmap, long long m, int32_t *err,
-                            cudaStream_t s)
+                            cudaStream_t s, int check_map)
 {
     long long blocks = (m + 255) / 256;
     if (blocks > 4096) blocks = 4096;
     if (blocks < 1) blocks = 1;
-    validate_kernel<<<(unsigned)blocks, 256, 0, s>>>(pos, gmap, m, err);
+    validate_kernel<<<(unsigned)blocks, 256, 0, s>>>(pos, gmap, m, err, check_map);
     return cudaGetLastError();
 }
 

@@ -63,7 +63,8 @@ extern "C" int selscan_ehh_noalloc(const uint64_t *hap, int64_t ld, int32_t n, i
 {
     if (!hap || !pos_bp || !gmap || !out || !p) return SELSCAN_ERR_INVALID_ARG;
     if (p->ehh_cut_den == 0 || p->maf_den == 0 || p->gap_scale_bp <= 0 || p->max_gap_bp < 0 ||
-        (p->include_crossing_term != 0 && p->include_crossing_term != 1))
+        (p->include_crossing_term != 0 && p->include_crossing_term != 1) ||
+        (p->use_physical_map != 0 && p->use_physical_map != 1))
         return SELSCAN_ERR_INVALID_ARG;
     // the fixed array holds six slices of the size a sample of
     // SELSCAN_EHH_NOALLOC_MAX_N haplotypes needs: larger samples are refused
@@ -94,6 +95,7 @@ extern "C" int selscan_ehh_noalloc(const uint64_t *hap, int64_t ld, int32_t n, i
     a.gap_scale = p->gap_scale_bp;
     a.max_gap = p->max_gap_bp;
     a.crossing = p->include_crossing_term;
+    a.physical = p->use_physical_map;
 
     Scratch sc;
     sc.base = (unsigned char *)base;
@@ -110,7 +112,8 @@ extern "C" int selscan_ehh_noalloc(const uint64_t *hap, int64_t ld, int32_t n, i
 
     cudaStream_t s = (cudaStream_t)stream;
     if (cudaMemsetAsync(out->error, 0, sizeof(int32_t), s) != cudaSuccess) return SELSCAN_ERR_CUDA;
-    if (launch_validate((const long long *)pos_bp, gmap, m, out->error, s) != cudaSuccess)
+    if (launch_validate((const long long *)pos_bp, gmap, m, out->error, s, !p->use_physical_map) !=
+        cudaSuccess)
         return SELSCAN_ERR_CUDA;
     if (launch_ehh(a, locus, sc, (unsigned long long *)out->S, capacity, (long long *)out->len,
                    out->stop, out->status, out->ihh, (unsigned long long *)out->denom, s) !=

@@ -1,0 +1,152 @@
+// Standardised scores (Eq. 7 for iHS, Eq. 11 for XPEHH): each unstandardised
+// score is centred and scaled by the mean and standard deviation of its
+// frequency bin, over all markers passed in (the caller's genome).
+//
+// Deterministic reduction: CTA (b, s) sums bin b over segment s of the
+// markers in a fixed order (thread stride, then a fixed tree); the segments
+// are combined in segment order.  Two passes: the mean, then the sum of
+// squared deviations about it (no cancellation of E[x^2] - E[x]^2).
+#include <math.h>
+
+#include "../../include/selscan.h"
+#include "internal.h"
+
+namespace selscan {
+
+namespace {
+
+constexpr int kNormThreads = 256;
+constexpr int kNormSegments = 16;
+
+__device__ __forceinline__ int bin_of(int32_t n1, int n, int nbins)
+{
+    // derived-allele frequency n1 / n in nbins equal bins, decided in integers
+    if (nbins == 1) return 0;
+    long long b = ((long long)n1 * nbins) / n;
+    return b >= nbins ? nbins - 1 : (b < 0 ? 0 : (int)b);
+}
+
+template <typename T>
+__device__ __forceinline__ T block_sum(T v, T *red)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) v += __shfl_down_sync(0xffffffffu, v, d);
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    T t = 0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < kNormThreads / 32; ++w) t += red[w];
+    __syncthreads();
+    return t;                       // valid in thread 0
+}
+
+// pass 0: count and sum per (bin, segment); pass 1: squared deviations about mean[bin]
+__global__ void __launch_bounds__(kNormThreads) norm_partial_kernel(
+    const double *score, const int8_t *status, const int32_t *n1, long long m, int n, int nbins,
+    int pass, const double *mean, double *part_sum, long long *part_cnt)
+{
+    __shared__ double red_d[kNormThreads / 32];
+    __shared__ long long red_c[kNormThreads / 32];
+    const int b = blockIdx.x / kNormSegments, seg = blockIdx.x % kNormSegments;
+    const long long per = (m + kNormSegments - 1) / kNormSegments;
+    const long long lo = (long long)seg * per, hi = lo + per < m ? lo + per : m;
+    double acc = 0.0;
+    long long cnt = 0;
+    const double mu = pass == 1 ? mean[b] : 0.0;
+    for (long long k = lo + threadIdx.x; k < hi; k += kNormThreads) {
+        if (status[k] != (int8_t)SELSCAN_LOCUS_OK) continue;
+        if (bin_of(n1[k], n, nbins) != b) continue;
+        const double x = score[k];
+        if (pass == 0) { acc += x; ++cnt; }
+        else { const double d = x - mu; acc += d * d; }
+    }
+    const double s = block_sum(acc, red_d);
+    const long long c = block_sum(cnt, red_c);
+    if (threadIdx.x == 0) {
+        part_sum[blockIdx.x] = s;
+        if (pass == 0) part_cnt[blockIdx.x] = c;
+    }
+}
+
+__global__ void norm_combine_kernel(int nbins, int pass, const double *part_sum,
+                                    const long long *part_cnt, long long *bin_count,
+                                    double *bin_mean, double *bin_sd)
+{
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nbins; b += gridDim.x * blockDim.x) {
+        double s = 0.0;
+        long long c = 0;
+        for (int seg = 0; seg < kNormSegments; ++seg) {
+            s += part_sum[b * kNormSegments + seg];
+            c += part_cnt[b * kNormSegments + seg];
+        }
+        if (pass == 0) {
+            bin_count[b] = c;
+            bin_mean[b] = c > 0 ? s / (double)c : __longlong_as_double(0x7ff8000000000000ll);
+        } else {
+            bin_sd[b] = c > 1 ? sqrt(s / (double)(c - 1)) : __longlong_as_double(0x7ff8000000000000ll);
+        }
+    }
+}
+
+__global__ void norm_apply_kernel(const double *score, const int8_t *status, const int32_t *n1,
+                                  long long m, int n, int nbins, const double *bin_mean,
+                                  const double *bin_sd, const long long *bin_count, double *out)
+{
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < m;
+         k += (long long)gridDim.x * blockDim.x) {
+        double r = __longlong_as_double(0x7ff8000000000000ll);
+        if (status[k] == (int8_t)SELSCAN_LOCUS_OK) {
+            const int b = bin_of(n1[k], n, nbins);
+            const double sd = bin_sd[b];
+            if (bin_count[b] >= 2 && sd > 0.0) r = (score[k] - bin_mean[b]) / sd;
+        }
+        out[k] = r;
+    }
+}
+
+}  // namespace
+
+}  // namespace selscan
+
+using namespace selscan;
+
+extern "C" {
+
+size_t selscan_normalize_workspace_bytes(int32_t nbins)
+{
+    if (nbins < 1 || nbins > SELSCAN_NORM_MAX_BINS) return 0;
+    const size_t parts = (size_t)nbins * kNormSegments;
+    return ((parts * 8 + 255) & ~(size_t)255) * 2;
+}
+
+int selscan_normalize(const double *score, const int8_t *status, const int32_t *n1, int64_t m,
+                      int32_t n, int32_t nbins, double *out, int64_t *bin_count, double *bin_mean,
+                      double *bin_sd, void *workspace, size_t ws_bytes, void *stream)
+{
+    if (!score || !status || !n1 || !out || !bin_count || !bin_mean || !bin_sd || m < 1 ||
+        n < 1 || nbins < 1 || nbins > SELSCAN_NORM_MAX_BINS)
+        return SELSCAN_ERR_INVALID_ARG;
+    const size_t need = selscan_normalize_workspace_bytes(nbins);
+    if (!workspace || ws_bytes < need || ((uintptr_t)workspace & 255)) return SELSCAN_ERR_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t half = need / 2;
+    double *part_sum = (double *)workspace;
+    long long *part_cnt = (long long *)((unsigned char *)workspace + half);
+    const unsigned grid = (unsigned)(nbins * kNormSegments);
+    norm_partial_kernel<<<grid, kNormThreads, 0, s>>>(score, status, n1, m, n, nbins, 0, nullptr,
+                                                      part_sum, part_cnt);
+    norm_combine_kernel<<<(nbins + 127) / 128, 128, 0, s>>>(nbins, 0, part_sum, part_cnt,
+                                                           (long long *)bin_count, bin_mean, bin_sd);
+    norm_partial_kernel<<<grid, kNormThreads, 0, s>>>(score, status, n1, m, n, nbins, 1, bin_mean,
+                                                      part_sum, part_cnt);
+    norm_combine_kernel<<<(nbins + 127) / 128, 128, 0, s>>>(nbins, 1, part_sum, part_cnt,
+                                                           (long long *)bin_count, bin_mean, bin_sd);
+    long long blocks = (m + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    norm_apply_kernel<<<(unsigned)blocks, 256, 0, s>>>(score, status, n1, m, n, nbins, bin_mean,
+                                                       bin_sd, (const long long *)bin_count, out);
+    return cudaGetLastError() == cudaSuccess ? SELSCAN_OK : SELSCAN_ERR_CUDA;
+}
+
+}  // extern "C"

@@ -702,8 +702,12 @@ __global__ void __launch_bounds__(kSplitWarps * 32, SPLIT_MIN_CTAS) split_walk_k
                     const long long bp = dir ? p1 - p0 : p0 - p1;
                     if (bp > w.a.max_gap) gq = -2.0;
                     else {
-                        const double g1 = __ldg(w.a.gmap + xl), g0 = __ldg(w.a.gmap + xp);
-                        double gg = dir ? g1 - g0 : g0 - g1;
+                        double gg;
+                        if (w.a.physical) gg = (double)bp;
+                        else {
+                            const double g1 = __ldg(w.a.gmap + xl), g0 = __ldg(w.a.gmap + xp);
+                            gg = dir ? g1 - g0 : g0 - g1;
+                        }
                         if (bp > w.a.gap_scale) gg = gg * ((double)w.a.gap_scale / (double)bp);
                         gq = gg;
                     }

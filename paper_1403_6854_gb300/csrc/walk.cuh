@@ -54,6 +54,7 @@ struct ScanArgs {
     unsigned int cut_num, cut_den;
     long long gap_scale, max_gap;
     int crossing;
+    int physical;                    // g = physical distance instead of the genetic map
 };
 
 // One warp's buffers: tier 0 on chip, tier 1 in global scratch.
@@ -676,7 +677,8 @@ __device__ WalkOut walk(const ScanArgs &a, long long core, int dir, int sel, con
         const long long bp = dir ? lds64(pos_sa) - lds64(pos_sa + prev_off)
                                  : lds64(pos_sa + prev_off) - lds64(pos_sa);
         if (bp > a.max_gap) { o.status = W_GAP; o.stop = (int)i; break; }
-        double g = dir ? ldsf64(gm_sa) - ldsf64(gm_sa + prev_off) : ldsf64(gm_sa + prev_off) - ldsf64(gm_sa);
+        double g = a.physical ? (double)bp
+                 : (dir ? ldsf64(gm_sa) - ldsf64(gm_sa + prev_off) : ldsf64(gm_sa + prev_off) - ldsf64(gm_sa));
         if (bp > a.gap_scale) g = g * ((double)a.gap_scale / (double)bp);
 
         split_step<NPOP>(a, row_sa, b, L, dS);

@@ -139,6 +139,82 @@ def test_gap_rules_and_parameters(sg):
         assert_xpehh_equal(gotx, refx)
 
 
+@pytest.mark.parametrize("schedule", ["in_order", "sweep"])
+def test_physical_map_on_gpu(sg, chr22, xp, schedule):
+    """use_physical_map on both the per-step and the sorted-sweep walks: g is the
+    position difference; a decreasing map is passed to show it is neither read
+    for g nor rejected."""
+    L = sg.make_launch(sg.SCHED_IN_ORDER if schedule == "in_order" else sg.SCHED_SWEEP)
+    p = sg.selscan_default_params(use_physical_map=1)
+    bad_map = chr22.gmap[::-1].copy()
+    ref = oracle.ihs(chr22.rows, 204, chr22.pos, bad_map, p=oracle.params(use_physical_map=1))
+    got = run_ihs(sg, chr22.rows, 204, chr22.pos, bad_map, params=p, launch=L)
+    assert_ihs_equal(got, ref)
+    refx = oracle.xpehh(xp.rows, 204, 210, xp.pos, xp.gmap, p=oracle.params(use_physical_map=1))
+    gotx = run_xpehh(sg, xp.rows, 204, 210, xp.pos, xp.gmap, params=p, launch=L)
+    assert_xpehh_equal(gotx, refx)
+
+
+def test_physical_map_single_locus(sg, chr22):
+    hap, pos, gmap = sg.to_device(chr22.rows, chr22.pos, chr22.gmap)
+    p = sg.selscan_default_params(use_physical_map=1)
+    for locus in (5, 11_000, 22_000):
+        got = sg.selscan_ehh(hap, 204, pos, gmap, locus, capacity=64, params=p)
+        ref = oracle.ehh(chr22.rows, 204, chr22.pos, chr22.gmap, locus, capacity=64,
+                         p=oracle.params(use_physical_map=1))
+        np.testing.assert_allclose(got["ihh"].cpu().numpy().reshape(ref["ihh"].shape), ref["ihh"],
+                                   rtol=1e-12, atol=0)
+
+
+def _norm_equal(got, ref):
+    g = {k: v.cpu().numpy() for k, v in got.items() if not k.startswith("_")}
+    assert np.array_equal(g["count"], ref["count"])
+    assert np.array_equal(np.isnan(g["score"]), np.isnan(ref["score"]))
+    ok = ~np.isnan(ref["score"])
+    np.testing.assert_allclose(g["score"][ok], ref["score"][ok], rtol=0, atol=1e-9)
+    okm = ~np.isnan(ref["mean"])
+    np.testing.assert_allclose(g["mean"][okm], ref["mean"][okm], rtol=1e-12, atol=1e-15)
+    oks = ~np.isnan(ref["sd"])
+    np.testing.assert_allclose(g["sd"][oks], ref["sd"][oks], rtol=1e-12)
+
+
+@pytest.mark.parametrize("nbins", [1, 10, 100])
+def test_normalize_ihs_on_gpu(sg, chr22, nbins):
+    hap, pos, gmap = sg.to_device(chr22.rows, chr22.pos, chr22.gmap)
+    o = sg.selscan_ihs(hap, 204, pos, gmap)
+    got = sg.selscan_normalize(o["lnratio"], o["status"], o["n1"], 204, nbins)
+    r = to_np(o)
+    ref = oracle.normalize(r["lnratio"], r["status"], r["n1"], 204, nbins)
+    _norm_equal(got, ref)
+    # deterministic reduction: a second call gives the same bits
+    again = sg.selscan_normalize(o["lnratio"], o["status"], o["n1"], 204, nbins)
+    assert torch.equal(again["score"].nan_to_num(0.0), got["score"].nan_to_num(0.0))
+
+
+def test_normalize_xpehh_genome_wide_on_gpu(sg, xp):
+    hap, pos, gmap = sg.to_device(xp.rows, xp.pos, xp.gmap)
+    o = sg.selscan_xpehh(hap, 204, 210, pos, gmap)
+    got = sg.selscan_normalize(o["lnratio"], o["status"], o["n1"], 414, 1)
+    r = to_np(o)
+    _norm_equal(got, oracle.normalize(r["lnratio"], r["status"], r["n1"], 414, 1))
+
+
+def test_normalize_edge_cases_on_gpu(sg):
+    dev = torch.device("cuda")
+    for m, n, nbins in ((1, 10, 1), (7, 10, 4), (3000, 500, 1024)):
+        rng = np.random.default_rng(m)
+        score = rng.normal(size=m)
+        st = rng.choice(np.array([0, 0, 0, 1, 2, 3, 4], dtype=np.int8), size=m)
+        n1 = rng.integers(0, n + 1, size=m).astype(np.int32)
+        got = sg.selscan_normalize(torch.from_numpy(score).to(dev), torch.from_numpy(st).to(dev),
+                                   torch.from_numpy(n1).to(dev), n, nbins)
+        _norm_equal(got, oracle.normalize(score, st, n1, n, nbins))
+    with pytest.raises(sg.SelscanError):
+        sg.selscan_normalize(torch.zeros(5, dtype=torch.float64, device=dev),
+                             torch.zeros(5, dtype=torch.int8, device=dev),
+                             torch.zeros(5, dtype=torch.int32, device=dev), 10, 2000)
+
+
 def test_xpehh_small_and_maf_flag(sg):
     for nA, nB in ((2, 2), (5, 64), (64, 65), (100, 31)):
         hap, pos, gmap = synth.tiny_mosaic(nA + nB, 35, nA * 31 + nB, founders=3, switch=0.1,

@@ -229,6 +229,46 @@ def test_gap_abort_boundary(gap_bp, aborts):
         assert r["status"][0, 1] == oracle.OK and r["stop"][0, 1] == k
 
 
+@pytest.mark.parametrize("k", [2, 7])
+def test_physical_map_closed_form(k):
+    """use_physical_map: g is the physical distance (position units); the map's
+    values are ignored (a constant map here would give iHH = 0 otherwise)."""
+    hap, pos, gmap = line_case(k, spacing=1000)
+    flat = np.full_like(gmap, 5.0)
+    r = oracle.ehh(pack(hap), hap.shape[1], pos, flat, 0, capacity=64,
+                   p=oracle.params(use_physical_map=1))
+    assert r["status"][0, 1] == oracle.OK and r["stop"][0, 1] == k
+    assert r["ihh"][0, 1] == (k - 1) * 1000.0
+
+
+@pytest.mark.parametrize("gap_bp", [20_000, 20_001, 40_000, 150_000])
+def test_physical_map_gap_scaling(gap_bp):
+    """A step longer than the 20 kbp scale contributes g = b * 20000 / b, i.e.
+    the scale itself; shorter steps contribute b."""
+    k = 6
+    hap, pos, gmap = line_case(k, gap_at=3, gap_bp=gap_bp)
+    r = oracle.ehh(pack(hap), hap.shape[1], pos, gmap, 0, capacity=64,
+                   p=oracle.params(use_physical_map=1))
+    assert r["status"][0, 1] == oracle.OK
+    want = (k - 2) * 1000.0 + min(gap_bp, 20_000)
+    assert r["ihh"][0, 1] == pytest.approx(want, rel=1e-15)
+
+
+@pytest.mark.parametrize("seed", [3, 4])
+def test_physical_map_equals_map_of_positions(seed):
+    """Physical mode equals genetic mode run with the positions as the map
+    (both integrate the same doubles), whatever map is passed."""
+    hap, pos, gmap = synth.tiny_mosaic(40, 90, seed, founders=3, switch=0.08, flip=0.02)
+    rows = pack(hap)
+    as_map = pos.astype(np.float64)
+    gen = oracle.ihs(rows, 40, pos, as_map)
+    phys = oracle.ihs(rows, 40, pos, gmap[::-1].copy(), p=oracle.params(use_physical_map=1))
+    for f in ("status", "n1", "stop", "digest", "ihh1", "ihh0"):
+        assert np.array_equal(gen[f], phys[f]), f
+    ok = ~np.isnan(gen["lnratio"])
+    assert np.array_equal(gen["lnratio"][ok], phys["lnratio"][ok])
+
+
 def test_gap_after_stop_is_not_seen():
     k = 3
     hap, pos, gmap = line_case(k, m=8, gap_at=5, gap_bp=500_000)
@@ -462,3 +502,51 @@ def test_bad_arguments_rejected():
         oracle.ihs(rows, 4, pos, gmap, p=oracle.params(ehh_cut=(1, 0)))
     with pytest.raises(ValueError):
         oracle.xpehh(rows, 1, 4, pos, gmap)
+
+
+# ------------------------------------------------------------ standardisation (Eq. 7, Eq. 11)
+def test_normalize_two_scores_per_bin():
+    """Two scores a < b in a bin: mean (a+b)/2, sample SD (b-a)/sqrt(2), so the
+    standardised scores are -+1/sqrt(2) whatever a and b are."""
+    n, nbins = 100, 10
+    n1 = np.array([12, 17, 55, 58, 91, 99])          # bins 1, 1, 5, 5, 9, 9
+    score = np.array([-3.0, 5.0, 0.25, 0.5, 7.0, -7.0])
+    st = np.zeros(6, dtype=np.int8)
+    r = oracle.normalize(score, st, n1, n, nbins)
+    want = np.array([-1, 1, -1, 1, 1, -1]) / np.sqrt(2.0)
+    np.testing.assert_allclose(r["score"], want, rtol=1e-15)
+    assert r["count"].tolist() == [0, 2, 0, 0, 0, 2, 0, 0, 0, 2]
+
+
+def test_normalize_bin_edges_and_undefined():
+    n, nbins = 100, 10
+    # 9/100 -> bin 0; 10/100 -> bin 1 (floor at the edge); 100/100 -> bin 9 (clamped)
+    n1 = np.array([9, 10, 100, 100, 50, 50, 50, 30])
+    st = np.array([0, 0, 0, 0, 0, 0, 2, 0], dtype=np.int8)      # one UNDEFINED marker
+    score = np.array([1.0, 2.0, 3.0, 3.0, 1.0, 4.0, 9.0, 6.0])
+    r = oracle.normalize(score, st, n1, n, nbins)
+    assert r["count"].tolist() == [1, 1, 0, 1, 0, 2, 0, 0, 0, 2]
+    assert np.isnan(r["score"][[0, 1, 7]]).all()        # singleton bins: no SD
+    assert np.isnan(r["score"][[2, 3]]).all()           # constant bin: SD 0
+    assert np.isnan(r["score"][6])                      # not OK
+    np.testing.assert_allclose(r["score"][[4, 5]], [-1 / np.sqrt(2), 1 / np.sqrt(2)], rtol=1e-15)
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_normalize_invariants(seed):
+    """Within every bin the standardised scores have mean 0 and sample SD 1,
+    and a positive affine map of the raw scores leaves them unchanged."""
+    rng = np.random.default_rng(seed)
+    m, n = 5000, 700
+    n1 = rng.integers(35, 666, size=m)
+    st = np.where(rng.random(m) < 0.9, 0, 3).astype(np.int8)
+    score = rng.normal(0.3, 1.7, size=m) + 0.01 * n1
+    for nbins in (1, 7, 50):
+        r = oracle.normalize(score, st, n1, n, nbins)
+        bins = np.zeros(m, int) if nbins == 1 else np.minimum(nbins - 1, (n1 * nbins) // n)
+        for b in range(nbins):
+            v = r["score"][(st == 0) & (bins == b)]
+            if v.size >= 2:
+                assert abs(v.mean()) < 1e-12 and abs(v.std(ddof=1) - 1.0) < 1e-12
+        r2 = oracle.normalize(2.5 * score - 11.0, st, n1, n, nbins)
+        np.testing.assert_allclose(r2["score"], r["score"], rtol=0, atol=1e-12)
