@@ -130,6 +130,8 @@ typedef struct {
                                   buffer stays near 12 GiB); sizes the slot buffer */
     int32_t sweep_threads;     /* sweep schedule: threads per sorting CTA, 256 or 512
                                   (0 = 256 up to 6144 haplotypes, else 512) */
+    int32_t sweep_split_tile;  /* sweep schedule: lanes per split walk, 32 or 16 (two walks
+                                  per warp) (0 = default) */
 } selscan_launch;
 
 /* iHS outputs: device arrays of length m (one record per marker). */

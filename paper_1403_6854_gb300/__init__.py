@@ -50,7 +50,8 @@ class selscan_launch(ctypes.Structure):
                 ("cores_per_fetch", ctypes.c_int32), ("min_ctas_per_sm", ctypes.c_int32),
                 ("walk_begin_event", ctypes.c_void_p), ("walk_end_event", ctypes.c_void_p),
                 ("big_group_entries", ctypes.c_int32), ("sweep_warmup", ctypes.c_int32),
-                ("sweep_stage_cores", ctypes.c_int32), ("sweep_threads", ctypes.c_int32)]
+                ("sweep_stage_cores", ctypes.c_int32), ("sweep_threads", ctypes.c_int32),
+                ("sweep_split_tile", ctypes.c_int32)]
 
 
 class selscan_ihs_out(ctypes.Structure):
@@ -173,7 +174,7 @@ def make_launch(schedule: int = SCHED_DEFAULT, warps_per_cta: int = 0, ctas_per_
                 smem_entries: int = 0, probe_steps: int = 0, window_rows: int = 0,
                 cores_per_fetch: int = 0, min_ctas_per_sm: int = 0, big_group_entries: int = 0,
                 sweep_warmup: int = 0, sweep_stage_cores: int = 0, sweep_threads: int = 0,
-                events=None) -> selscan_launch:
+                sweep_split_tile: int = 0, events=None) -> selscan_launch:
     """events: optional (begin, end) torch.cuda.Event pair bracketing the walk kernels."""
     L = selscan_launch(schedule, warps_per_cta, ctas_per_sm, smem_entries, probe_steps,
                        window_rows, cores_per_fetch, min_ctas_per_sm)
@@ -181,6 +182,7 @@ def make_launch(schedule: int = SCHED_DEFAULT, warps_per_cta: int = 0, ctas_per_
     L.sweep_warmup = sweep_warmup
     L.sweep_stage_cores = sweep_stage_cores
     L.sweep_threads = sweep_threads
+    L.sweep_split_tile = sweep_split_tile
     if events is not None:
         L.walk_begin_event = ctypes.c_void_p(events[0].cuda_event)
         L.walk_end_event = ctypes.c_void_p(events[1].cuda_event)

@@ -20,6 +20,7 @@ constexpr int kDefaultProbeSteps = 48;
 constexpr int kDefaultBigGroup = 32;
 constexpr int kMaxHaplotypes = 65000;
 constexpr int kDefaultSweepWarmup = 2048;
+constexpr int kDefaultSplitTile = 32;
 constexpr size_t kSweepSlotBudget = (size_t)12 << 30;  // bytes of sweep slots per scan
 constexpr size_t kMaxSmemPerCta = 227 * 1024;
 
@@ -28,8 +29,9 @@ struct SweepPlan {
     long long B;
     size_t state_bytes, slot_bytes;
     int split_bytes;
+    int split_tile;           // lanes per split walk (32 or 16)
     int walk_ctas;
-    size_t wscratch_bytes;    // per split-walk warp
+    size_t wscratch_bytes;    // per split-walk tile
 };
 
 struct Plan {
@@ -94,7 +96,9 @@ SweepPlan make_sweep_plan(int n_total, long long m, int mode, const selscan_laun
     }
     w.nstages = (int)((w.B + w.R - 1) / w.R);
     w.split_bytes = (int)split_smem_per_warp(n_total, xp);
-    w.walk_ctas = split_walk_ctas(n_total, xp);
+    w.split_tile = (L && (L->sweep_split_tile == 16 || L->sweep_split_tile == 32))
+                       ? L->sweep_split_tile : kDefaultSplitTile;
+    w.walk_ctas = split_walk_ctas(n_total, xp, w.split_tile);
     w.wscratch_bytes = split_scratch_per_warp(n_total);
     return w;
 }
@@ -185,7 +189,8 @@ Layout make_layout(int n_total, long long m, int mode, int nslots, const SweepPl
         l.sweep_head = o;     o += 256;
         l.sweep_state = o;    o += up256((size_t)2 * sw->nch * sw->state_bytes);
         l.sweep_slots = o;    o += up256((size_t)2 * sw->nch * sw->R * sw->slot_bytes);
-        l.sweep_wscratch = o; o += (size_t)sw->walk_ctas * kSplitWarps * sw->wscratch_bytes;
+        l.sweep_wscratch = o;
+        o += (size_t)sw->walk_ctas * (kSplitWarps * 32 / sw->split_tile) * sw->wscratch_bytes;
     }
     l.total = o;
     return l;
@@ -249,7 +254,7 @@ int run_scan(int mode, const uint64_t *hap, int64_t ld, int32_t nA, int32_t nB, 
         return SELSCAN_ERR_UNSUPPORTED;
     const bool sweep = plan.schedule == SELSCAN_SCHED_SWEEP;
     if (sweep && (sweep_smem_bytes(n_total, (nA + 63) / 64 + (nB + 63) / 64, plan.sw.threads) > kMaxSmemPerCta ||
-                  (size_t)plan.sw.split_bytes * kSplitWarps > kMaxSmemPerCta))
+                  (size_t)plan.sw.split_bytes * (kSplitWarps * 32 / plan.sw.split_tile) > kMaxSmemPerCta))
         return SELSCAN_ERR_UNSUPPORTED;
     const Layout l = make_layout(n_total, m, mode, plan.nslots, sweep ? &plan.sw : nullptr);
     if (!workspace || ws_bytes < l.total || ((uintptr_t)workspace & 255)) return SELSCAN_ERR_WORKSPACE;
@@ -302,6 +307,7 @@ int run_scan(int mode, const uint64_t *hap, int64_t ld, int32_t nA, int32_t nB, 
         w.slots = ws + l.sweep_slots;
         w.slot_bytes = plan.sw.slot_bytes;
         w.split_bytes = plan.sw.split_bytes;
+        w.split_tile = plan.sw.split_tile;
         w.wscratch = ws + l.sweep_wscratch;
         w.wscratch_bytes = plan.sw.wscratch_bytes;
         w.walk_ctas = plan.sw.walk_ctas;

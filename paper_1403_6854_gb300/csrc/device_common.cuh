@@ -69,7 +69,7 @@ __device__ __forceinline__ void run_item(const ScanArgs &a, const ItemSink &sk, 
     const int sel = NPOP == 2 ? 0 : (q < 2 ? 0 : 1);
     WalkOut o = walk<NPOP>(a, core, dir, sel, b, nullptr, 0, max_steps, wpar);
     if (lane != 0) return;
-    if (o.status == W_UNFINISHED) {
+    if (o.status == WALK_UNFINISHED) {
         const unsigned long long slot = atomicAdd(&sk.q->n2, 1ull);
         sk.list2[slot] = item;
         sk.key2[slot] = bucket_of(o.key);

@@ -117,8 +117,9 @@ struct SweepArgs {
     unsigned short *st;      // per chunk and direction: sorted order, run lengths
     unsigned char *slots;    // [2][nch][R] slots of slot_bytes
     size_t slot_bytes;
-    int split_bytes;         // shared memory of one split-walk warp
-    unsigned char *wscratch; // per split-walk warp: window staging and step lists
+    int split_bytes;         // shared memory of one split-walk tile
+    int split_tile;          // lanes per split walk: 32 (a warp) or 16 (two walks per warp)
+    unsigned char *wscratch; // per split-walk tile: window staging and step lists
     size_t wscratch_bytes;
     int walk_ctas;           // persistent split-walk grid
     unsigned long long *walk_head;   // slot counter of the current walk launch
@@ -129,7 +130,7 @@ size_t sweep_slot_bytes(int n, int xpehh);
 size_t sweep_state_bytes(int n, int T);
 size_t split_smem_per_warp(int n, int xpehh);
 size_t split_scratch_per_warp(int n);
-int split_walk_ctas(int n, int xpehh);
+int split_walk_ctas(int n, int xpehh, int tile);
 cudaError_t launch_sweep_path(const SweepArgs &w, cudaStream_t s);
 
 }  // namespace selscan

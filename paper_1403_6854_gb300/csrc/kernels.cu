@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(128) walk_plain_kernel(ScanArgs a, ItemSink sk
     slot = __shfl_sync(FULLMASK, slot, 0);
     if (slot < 0) {                       // cannot happen: nslots >= resident warps
         if (lane == 0) {
-            sk.item_status[core * (NPOP == 2 ? 2 : 4) + warp] = (int8_t)W_UNFINISHED;
+            sk.item_status[core * (NPOP == 2 ? 2 : 4) + warp] = (int8_t)WALK_UNFINISHED;
             atomicExch(sc.err, SELSCAN_ERR_INTERNAL);
         }
         return;
@@ -426,8 +426,8 @@ __global__ void __launch_bounds__(192) ehh_trace_kernel(ScanArgs a, long long lo
     WalkOut o = walk<1>(a, locus, dir, w, b, S + (size_t)q * cap, cap, 0, wpar);
     if (lane == 0) {
         long long steps = 0;
-        if (o.status == W_OK) steps = o.stop + 1;
-        else if (o.status == W_EDGE || o.status == W_GAP) steps = o.stop;
+        if (o.status == WALK_OK) steps = o.stop + 1;
+        else if (o.status == WALK_EDGE || o.status == WALK_GAP) steps = o.stop;
         len[q] = steps;
         stop[q] = o.stop;
         status[q] = (int8_t)o.status;

@@ -27,6 +27,8 @@
 //    the cutoff and the trapezoid exactly as the per-step walk does, with S(i)
 //    from the boundaries of step i.  A walk that would step beyond its
 //    chunk's history is handed to the per-step walk kernel (second pass).
+#include <cooperative_groups.h>
+#include <cooperative_groups/reduce.h>
 #include <limits.h>
 
 #include "../../include/selscan.h"
@@ -429,36 +431,38 @@ __device__ __forceinline__ unsigned count_a(const SplitSmem &s, int x)
 
 // Group the boundaries t with lo <= M[t] < lo + 64 by step: one pass over M
 // (8 values per 16-byte load, four loads in flight per lane) collects them
-// with their rank inside their step, then they are placed by step.
-__device__ void build_window(const SplitSmem &s, const unsigned *M32, int n, int lo,
-                             unsigned long long *stage, unsigned short *list)
+// with their rank inside their step, then they are placed by step.  Done by
+// one tile of G lanes.
+template <int G, typename Tile>
+__device__ void build_window(const Tile &tile, const SplitSmem &s, const unsigned *M32, int n,
+                             int lo, unsigned long long *stage, unsigned short *list)
 {
-    const int lane = threadIdx.x & 31;
+    const int lane = tile.thread_rank();
     const unsigned ltm = (1u << lane) - 1u;
     const uint4 *M4 = (const uint4 *)M32;
-    for (int q = lane; q < 64; q += 32) s.cnt[q] = 0u;
-    __syncwarp();
+    for (int q = lane; q < 64; q += G) s.cnt[q] = 0u;
+    tile.sync();
     const int n4 = (n + 7) >> 3;
     unsigned K = 0;
-    for (int base = 0; base < n4; base += 128) {
+    for (int base = 0; base < n4; base += 4 * G) {
         uint4 q[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            const int idx = base + u * 32 + lane;
+            const int idx = base + u * G + lane;
             q[u] = idx < n4 ? __ldg(M4 + idx) : make_uint4(~0u, ~0u, ~0u, ~0u);
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            const int t0 = (base + u * 32 + lane) * 8;
+            const int t0 = (base + u * G + lane) * 8;
             const unsigned wv[4] = {q[u].x, q[u].y, q[u].z, q[u].w};
-            // one ballot per 16-bit pair of the 8 values in hand
+            // one ballot per value of the 8 in hand
 #pragma unroll 1
             for (int h = 0; h < 8; ++h) {
                 const unsigned ww = (h >> 1) == 0 ? wv[0] : (h >> 1) == 1 ? wv[1] : (h >> 1) == 2 ? wv[2] : wv[3];
                 const int t = t0 + h;
                 const unsigned d = ((h & 1) ? (ww >> 16) : (ww & 0xFFFFu)) - (unsigned)lo;
                 const bool in = t < n && d < 64u;
-                const unsigned bal = __ballot_sync(FULLMASK, in);
+                const unsigned bal = tile.ballot(in);
                 if (in) {
                     const unsigned r = atomicAdd(s.cnt + d, 1u);
                     stage[K + __popc(bal & ltm)] =
@@ -468,24 +472,32 @@ __device__ void build_window(const SplitSmem &s, const unsigned *M32, int n, int
             }
         }
     }
-    __syncwarp();
-    const unsigned a = s.cnt[2 * lane], b = s.cnt[2 * lane + 1];
-    unsigned incl = a + b;
+    tile.sync();
+    // exclusive offsets of the 64 step counts: 64 / G consecutive counts per lane
+    constexpr int C = 64 / G;
+    unsigned own = 0;
 #pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const unsigned v = __shfl_up_sync(FULLMASK, incl, d);
+    for (int j = 0; j < C; ++j) own += s.cnt[C * lane + j];
+    unsigned incl = own;
+#pragma unroll
+    for (int d = 1; d < G; d <<= 1) {
+        const unsigned v = tile.shfl_up(incl, d);
         if (lane >= d) incl += v;
     }
-    const unsigned excl = incl - a - b;
-    s.off[2 * lane] = excl;
-    s.off[2 * lane + 1] = excl + a;
-    if (lane == 31) s.off[64] = incl;
-    __syncwarp();
-    for (unsigned j = lane; j < K; j += 32) {
+    unsigned run = incl - own;
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+        const unsigned c = s.cnt[C * lane + j];
+        s.off[C * lane + j] = run;
+        run += c;
+    }
+    if (lane == G - 1) s.off[64] = incl;
+    tile.sync();
+    for (unsigned j = lane; j < K; j += G) {
         const unsigned long long e = stage[j];
         list[s.off[(unsigned)(e >> 16) & 63u] + (unsigned)(e >> 32)] = (unsigned short)(e & 0xFFFFu);
     }
-    __syncwarp();
+    tile.sync();
 }
 
 struct ClassWalk {
@@ -530,34 +542,35 @@ __device__ __forceinline__ void split_terms(const SplitSmem &s, int b, int n, in
     }
 }
 
-// Steps that part more than 32 pairs (a few per walk): kept out of line so
+// Steps that part more than G pairs (a few per walk): kept out of line so
 // that the common one-round path stays small in the instruction cache.
-template <int NPOP>
-__device__ __noinline__ void split_many(const SplitSmem &s, const unsigned short *list, unsigned j0,
-                                        unsigned j1, int n, int n0, int &d0, int &d1, int &d2)
+template <int NPOP, int G, typename Tile>
+__device__ __noinline__ void split_many(const Tile &tile, const SplitSmem &s,
+                                        const unsigned short *list, unsigned j0, unsigned j1, int n,
+                                        int n0, int &d0, int &d1, int &d2)
 {
-    const int lane = threadIdx.x & 31;
-    for (unsigned j = j0 + lane; j < j1; j += 32) {
+    const int lane = tile.thread_rank();
+    for (unsigned j = j0 + lane; j < j1; j += G) {
         const int b = list[j];
         atomicOr(s.N + (b >> 5), 1u << (b & 31));
         atomicOr(s.SN + (b >> 10), 1u << ((b >> 5) & 31));
     }
-    __syncwarp();
-    for (unsigned j = j0 + lane; j < j1; j += 32)
+    tile.sync();
+    for (unsigned j = j0 + lane; j < j1; j += G)
         split_terms<NPOP>(s, (int)list[j], n, n0, d0, d1, d2);
-    __syncwarp();
-    for (unsigned j = j0 + lane; j < j1; j += 32) {
+    tile.sync();
+    for (unsigned j = j0 + lane; j < j1; j += G) {
         const int b = list[j];
         atomicOr(s.O + (b >> 5), 1u << (b & 31));
         atomicOr(s.SO + (b >> 10), 1u << ((b >> 5) & 31));
     }
-    __syncwarp();
-    for (unsigned j = j0 + lane; j < j1; j += 32) {
+    tile.sync();
+    for (unsigned j = j0 + lane; j < j1; j += G) {
         const int b = list[j];
         s.N[b >> 5] = 0u;
         s.SN[b >> 10] = 0u;
     }
-    __syncwarp();
+    tile.sync();
 }
 
 }  // namespace
@@ -572,19 +585,23 @@ size_t split_smem_per_warp(int n, int xpehh)
 
 size_t split_scratch_per_warp(int n) { return (((size_t)n * 10) + 255) & ~(size_t)255; }
 
-// Persistent: each warp takes slots of this stage (both directions) from a
+// Persistent: each tile of G lanes (a warp, or half a warp so that one warp
+// walks two cores at once) takes slots of this stage (both directions) from a
 // counter and walks the cores in them.
 #ifndef SPLIT_MIN_CTAS
 #define SPLIT_MIN_CTAS 3
 #endif
-template <int NPOP>
+template <int NPOP, int G>
 __global__ void __launch_bounds__(kSplitWarps * 32, SPLIT_MIN_CTAS) split_walk_kernel(SweepArgs w)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    namespace cg = cooperative_groups;
+    const cg::thread_block_tile<G> tile = cg::tiled_partition<G>(cg::this_thread_block());
+    constexpr int TPC = kSplitWarps * 32 / G;            // tiles per CTA
+    const int lane = tile.thread_rank(), tix = threadIdx.x / G;
     const int n = w.n;
-    SplitSmem s = split_smem(smem + (size_t)warp * w.split_bytes, n, NPOP == 2);
-    unsigned char *scr = w.wscratch + ((size_t)blockIdx.x * kSplitWarps + warp) * w.wscratch_bytes;
+    SplitSmem s = split_smem(smem + (size_t)tix * w.split_bytes, n, NPOP == 2);
+    unsigned char *scr = w.wscratch + ((size_t)blockIdx.x * TPC + tix) * w.wscratch_bytes;
     unsigned long long *stage = (unsigned long long *)scr;
     unsigned short *list = (unsigned short *)(scr + (size_t)n * 8);
     const long long per_dir = (long long)w.nch * w.R;
@@ -592,7 +609,7 @@ __global__ void __launch_bounds__(kSplitWarps * 32, SPLIT_MIN_CTAS) split_walk_k
     for (;;) {
         unsigned long long gs = 0;
         if (lane == 0) gs = atomicAdd(w.walk_head, 1ull);
-        gs = __shfl_sync(FULLMASK, gs, 0);
+        gs = tile.shfl(gs, 0);
         if (gs >= (unsigned long long)(2 * per_dir)) break;
         // slot counts are below 2^31 (2 x chunks x stage cores): 32-bit decode
         const unsigned gsl = (unsigned)gs;
@@ -623,32 +640,32 @@ __global__ void __launch_bounds__(kSplitWarps * 32, SPLIT_MIN_CTAS) split_walk_k
         const int hz = ((const int *)slot)[1];
         const unsigned *M32 = (const unsigned *)(slot + 16);
 
-        for (int q = lane; q < s.nw; q += 32) { s.O[q] = 0u; s.N[q] = 0u; }
-        for (int q = lane; q < s.ns; q += 32) { s.SO[q] = 0u; s.SN[q] = 0u; }
+        for (int q = lane; q < s.nw; q += G) { s.O[q] = 0u; s.N[q] = 0u; }
+        for (int q = lane; q < s.ns; q += G) { s.SO[q] = 0u; s.SN[q] = 0u; }
         if (NPOP == 2) {
             const unsigned *isA = (const unsigned *)(slot + 16 + (((size_t)n * 2 + 15) & ~(size_t)15));
             unsigned carry = 0u;
-            for (int base = 0; base < s.nw; base += 32) {
+            for (int base = 0; base < s.nw; base += G) {
                 const int q = base + lane;
                 const unsigned v = q < s.nw ? __ldg(isA + q) : 0u;
                 const unsigned pc = (unsigned)__popc(v);
                 unsigned incl = pc;
 #pragma unroll
-                for (int d = 1; d < 32; d <<= 1) {
-                    const unsigned u = __shfl_up_sync(FULLMASK, incl, d);
+                for (int d = 1; d < G; d <<= 1) {
+                    const unsigned u = tile.shfl_up(incl, d);
                     if (lane >= d) incl += u;
                 }
                 if (q < s.nw) { s.isA[q] = v; s.PA[q] = carry + incl - pc; }
-                carry += __shfl_sync(FULLMASK, incl, 31);
+                carry += tile.shfl(incl, G - 1);
             }
         }
-        __syncwarp();
+        tile.sync();
         if (lane < 3) {                           // run starts before step 1: 0, n0, n
             const int mk = lane == 0 ? 0 : (lane == 1 ? n0 : n);
             atomicOr(s.O + (mk >> 5), 1u << (mk & 31));
             atomicOr(s.SO + (mk >> 10), 1u << ((mk >> 5) & 31));
         }
-        __syncwarp();
+        tile.sync();
 
         // ---- step 0 (the core marker splits the sample into its allele classes)
         constexpr int NWK = NPOP == 2 ? 1 : 2;    // walks handled by this warp
@@ -681,20 +698,20 @@ __global__ void __launch_bounds__(kSplitWarps * 32, SPLIT_MIN_CTAS) split_walk_k
             cw[q].dig = cw[q].S;
             cw[q].acc = 0.0;
             cw[q].stop = 0;
-            cw[q].status = cw[q].D == 0ull ? W_UNDEFINED : W_OK;
+            cw[q].status = cw[q].D == 0ull ? WALK_UNDEFINED : WALK_OK;
             cw[q].active = cw[q].D != 0ull;
             any |= cw[q].active;
         }
 
         const long long step = dir ? 1 : -1;
-        double gq = 0.0;        // this lane's step of the current 32-step block:
+        double gq = 0.0;        // this lane's step of the current G-step block:
                                 // map step g >= 0, -1 past the array end, -2 a gap abort
         int lo = 1;
-        if (any) build_window(s, M32, n, lo, stage, list);
-        int fin = W_OK;                           // how the still-active walks end
+        if (any) build_window<G>(tile, s, M32, n, lo, stage, list);
+        int fin = WALK_OK;                           // how the still-active walks end
         long long i = 1;
         for (; any; ++i) {
-            if (((i - 1) & 31) == 0) {            // gaps and map steps of the next 32 steps
+            if (((i - 1) & (G - 1)) == 0) {       // gaps and map steps of the next G steps
                 const long long xl = k + step * (i + lane), xp = xl - step;
                 if (xl < 0 || xl >= m) gq = -1.0;
                 else {
@@ -713,46 +730,46 @@ __global__ void __launch_bounds__(kSplitWarps * 32, SPLIT_MIN_CTAS) split_walk_k
                     }
                 }
             }
-            const double g = __shfl_sync(FULLMASK, gq, (int)((i - 1) & 31));
-            if (g < 0.0) { fin = g == -1.0 ? W_EDGE : W_GAP; break; }
-            if (i > (long long)hz) { fin = W_UNFINISHED; break; }
+            const double g = tile.shfl(gq, (int)((i - 1) & (G - 1)));
+            if (g < 0.0) { fin = g == -1.0 ? WALK_EDGE : WALK_GAP; break; }
+            if (i > (long long)hz) { fin = WALK_UNFINISHED; break; }
             if (i >= lo + 64) {
                 lo += 64;
-                build_window(s, M32, n, lo, stage, list);
+                build_window<G>(tile, s, M32, n, lo, stage, list);
             }
             // ---- the boundaries that part at this step
             const unsigned j0 = s.off[i - lo], j1 = s.off[i - lo + 1];
             int d0 = 0, d1 = 0, d2 = 0;
             if (j1 > j0) {
                 // new run starts first, then their reductions, then merge
-                if (j1 - j0 <= 32u) {             // one boundary per lane, loaded once
+                if (j1 - j0 <= (unsigned)G) {     // one boundary per lane, loaded once
                     bool has = lane < (int)(j1 - j0);
                     const int b = has ? (int)list[j0 + lane] : 0;
                     // an iHS class whose walk has ended needs its runs no more
                     if (NPOP == 1) has = has && (b < n0 ? cw[0].active : cw[NWK - 1].active);
                     const unsigned bw = 1u << (b & 31), sw = 1u << ((b >> 5) & 31);
-                    if (__ballot_sync(FULLMASK, has) != 0u) {
+                    if (tile.ballot(has) != 0u) {
                     if (has) {
                         atomicOr(s.N + (b >> 5), bw);
                         atomicOr(s.SN + (b >> 10), sw);
                     }
-                    __syncwarp();
+                    tile.sync();
                     if (has) split_terms<NPOP>(s, b, n, n0, d0, d1, d2);
-                    __syncwarp();
+                    tile.sync();
                     if (has) {
                         atomicOr(s.O + (b >> 5), bw);
                         atomicOr(s.SO + (b >> 10), sw);
                         s.N[b >> 5] = 0u;
                         s.SN[b >> 10] = 0u;
                     }
-                    __syncwarp();
+                    tile.sync();
                     }
                 } else {
-                    split_many<NPOP>(s, list, j0, j1, n, n0, d0, d1, d2);
+                    split_many<NPOP, G>(tile, s, list, j0, j1, n, n0, d0, d1, d2);
                 }
-                d0 = __reduce_add_sync(FULLMASK, d0);
-                d1 = __reduce_add_sync(FULLMASK, d1);
-                if (NPOP == 2) d2 = __reduce_add_sync(FULLMASK, d2);
+                d0 = cg::reduce(tile, d0, cg::plus<int>());
+                d1 = cg::reduce(tile, d1, cg::plus<int>());
+                if (NPOP == 2) d2 = cg::reduce(tile, d2, cg::plus<int>());
             }
             const unsigned long long ii = (unsigned long long)(i + 1);
             if (NPOP == 2) {
@@ -802,7 +819,7 @@ __global__ void __launch_bounds__(kSplitWarps * 32, SPLIT_MIN_CTAS) split_walk_k
                 const uint32_t item = NPOP == 2 ? (uint32_t)(k * 2 + dir)
                                                 : (uint32_t)(k * 4 + (q_ == 1 ? 0 : 2) + dir);
                 if (q.active) {
-                    if (fin == W_UNFINISHED) {
+                    if (fin == WALK_UNFINISHED) {
                         const unsigned long long slot2 = atomicAdd(&sk.q->n2, 1ull);
                         sk.list2[slot2] = item;
                         sk.key2[slot2] = bucket_of((float)((double)q.S / (double)q.D));
@@ -825,20 +842,28 @@ __global__ void __launch_bounds__(kSplitWarps * 32, SPLIT_MIN_CTAS) split_walk_k
                 }
             }
         }
-        __syncwarp();
+        tile.sync();
     }
 }
 
-int split_walk_ctas(int n, int xpehh)
+template <int G>
+static void (*walk_kernel_for(int xpehh))(SweepArgs)
 {
-    // resident CTAs of the persistent walker (registers allow 4 per SM)
+    return xpehh ? split_walk_kernel<2, G> : split_walk_kernel<1, G>;
+}
+
+static void (*walk_kernel(int xpehh, int tile))(SweepArgs)
+{
+    return tile == 16 ? walk_kernel_for<16>(xpehh) : walk_kernel_for<32>(xpehh);
+}
+
+int split_walk_ctas(int n, int xpehh, int tile)
+{
+    // resident CTAs of the persistent walker
     int per_sm = 0;
-    const size_t smem = split_smem_per_warp(n, xpehh) * kSplitWarps;
-    cudaError_t e;
-    if (xpehh) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, split_walk_kernel<2>,
-                                                                 kSplitWarps * 32, smem);
-    else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, split_walk_kernel<1>,
-                                                           kSplitWarps * 32, smem);
+    const size_t smem = split_smem_per_warp(n, xpehh) * (kSplitWarps * 32 / tile);
+    const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_sm, walk_kernel(xpehh, tile), kSplitWarps * 32, smem);
     if (e != cudaSuccess || per_sm < 1) per_sm = 1;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -861,8 +886,8 @@ cudaError_t launch_sweep_path(const SweepArgs &w0, cudaStream_t s)
               : sweep_kernel<512, 32>;
     cudaError_t e = cudaFuncSetAttribute(sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm);
     if (e != cudaSuccess) return e;
-    const size_t wsm = (size_t)w.split_bytes * kSplitWarps;
-    void (*walk)(SweepArgs) = w.a.nB > 0 ? split_walk_kernel<2> : split_walk_kernel<1>;
+    const size_t wsm = (size_t)w.split_bytes * (kSplitWarps * 32 / w.split_tile);
+    void (*walk)(SweepArgs) = walk_kernel(w.a.nB > 0, w.split_tile);
     if ((e = cudaFuncSetAttribute(walk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsm)) !=
         cudaSuccess)
         return e;

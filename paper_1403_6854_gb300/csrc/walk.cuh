@@ -36,7 +36,7 @@ namespace selscan {
 
 // Internal walk outcomes (the first five equal the public locus codes).
 enum : int {
-    W_OK = 0, W_UNDEFINED = 2, W_EDGE = 3, W_GAP = 4, W_UNFINISHED = 5
+    WALK_OK = 0, WALK_UNDEFINED = 2, WALK_EDGE = 3, WALK_GAP = 4, WALK_UNFINISHED = 5
 };
 
 
@@ -559,7 +559,7 @@ __device__ __forceinline__ void split_step(const ScanArgs &a, unsigned row_sa, c
 // NPOP 1: sel 0 = carriers of allele 1, 1 = carriers of allele 0, 2 = all.
 // NPOP 2: both populations pooled.  trace (optional): S(i) for i < tcap
 // (NPOP 1: the sample's S; NPOP 2: the pooled S).  max_steps > 0 ends a walk
-// still running after that many steps with W_UNFINISHED.
+// still running after that many steps with WALK_UNFINISHED.
 // win_parity: the warp's two mbarrier phase bits, carried from walk to walk.
 template <int NPOP>
 __device__ WalkOut walk(const ScanArgs &a, long long core, int dir, int sel, const WarpBufs &b,
@@ -568,7 +568,7 @@ __device__ WalkOut walk(const ScanArgs &a, long long core, int dir, int sel, con
 {
     const int lane = threadIdx.x & 31;
     WalkOut o;
-    o.status = W_OK;
+    o.status = WALK_OK;
     o.stop = 0;
     o.ihh[0] = o.ihh[1] = 0.0;
     o.dig[0] = o.dig[1] = o.dig[2] = 0ull;
@@ -619,7 +619,7 @@ __device__ WalkOut walk(const ScanArgs &a, long long core, int dir, int sel, con
     const unsigned long long Dstop = NPOP == 2 ? DP : D0;
     o.D = Dstop;
     if (Dstop == 0ull) {                   // fewer than two haplotypes: nothing to walk
-        o.status = W_UNDEFINED;
+        o.status = WALK_UNDEFINED;
         return o;
     }
     unsigned long long S0 = D0, S1 = D1, SP = DP;
@@ -647,9 +647,9 @@ __device__ WalkOut walk(const ScanArgs &a, long long core, int dir, int sel, con
     unsigned row_sa = 0u, pos_sa = 0u, gm_sa = 0u; // shared addresses of the current x
     for (long long i = 1;; ++i) {
         const long long x = core + step * i;
-        if (x < 0 || x >= a.m) { o.status = W_EDGE; o.stop = (int)i; break; }
+        if (x < 0 || x >= a.m) { o.status = WALK_EDGE; o.stop = (int)i; break; }
         if (max_steps > 0 && i > max_steps) {
-            o.status = W_UNFINISHED;
+            o.status = WALK_UNFINISHED;
             o.stop = (int)i;
             o.key = (float)((double)(NPOP == 2 ? SP : S0) / (double)Dstop);
             break;
@@ -662,7 +662,7 @@ __device__ WalkOut walk(const ScanArgs &a, long long core, int dir, int sel, con
             bi ^= 1;
             left = R;
             if (!(bi ? win_wait(b, wb[1], 1) : win_wait(b, wb[0], 0))) {
-                o.status = W_UNDEFINED;
+                o.status = WALK_UNDEFINED;
                 o.stop = (int)i;
                 break;
             }
@@ -676,7 +676,7 @@ __device__ WalkOut walk(const ScanArgs &a, long long core, int dir, int sel, con
         const unsigned prev_off = dir ? (unsigned)-8 : 8u;
         const long long bp = dir ? lds64(pos_sa) - lds64(pos_sa + prev_off)
                                  : lds64(pos_sa + prev_off) - lds64(pos_sa);
-        if (bp > a.max_gap) { o.status = W_GAP; o.stop = (int)i; break; }
+        if (bp > a.max_gap) { o.status = WALK_GAP; o.stop = (int)i; break; }
         double g = a.physical ? (double)bp
                  : (dir ? ldsf64(gm_sa) - ldsf64(gm_sa + prev_off) : ldsf64(gm_sa + prev_off) - ldsf64(gm_sa));
         if (bp > a.gap_scale) g = g * ((double)a.gap_scale / (double)bp);
@@ -707,7 +707,7 @@ __device__ WalkOut walk(const ScanArgs &a, long long core, int dir, int sel, con
     // drain copies still in flight before the buffers serve the next walk
     const bool d0 = win_wait(b, wb[0], 0);
     const bool d1 = win_wait(b, wb[1], 1);
-    if (!d0 || !d1) o.status = W_UNDEFINED;
+    if (!d0 || !d1) o.status = WALK_UNDEFINED;
     win_parity[0] = wb[0].parity;
     win_parity[1] = wb[1].parity;
     if (NPOP == 2) {

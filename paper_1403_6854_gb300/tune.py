@@ -20,7 +20,7 @@ from typing import Callable, Dict, List, Optional
 
 SHAPE_FIELDS = ("schedule", "warps_per_cta", "smem_entries", "window_rows", "cores_per_fetch",
                 "probe_steps", "min_ctas_per_sm", "big_group_entries", "sweep_warmup",
-                "sweep_stage_cores", "sweep_threads")
+                "sweep_stage_cores", "sweep_threads", "sweep_split_tile")
 
 SWEEP_MAX_N = 16383
 SWEEP_CANDIDATES: List[Dict] = [

@@ -18,7 +18,9 @@ pytestmark = pytest.mark.gpu
 
 SHAPES = [dict(), dict(sweep_warmup=16, sweep_stage_cores=7), dict(sweep_warmup=40, sweep_stage_cores=1),
           dict(sweep_warmup=300, sweep_stage_cores=4096), dict(sweep_threads=512),
-          dict(sweep_threads=256, sweep_warmup=64, sweep_stage_cores=33)]
+          dict(sweep_threads=256, sweep_warmup=64, sweep_stage_cores=33),
+          dict(sweep_split_tile=16), dict(sweep_split_tile=16, sweep_warmup=16, sweep_stage_cores=5),
+          dict(sweep_split_tile=32)]
 
 
 @pytest.fixture(scope="module")
@@ -86,7 +88,8 @@ def test_small_shapes(sg, n, m):
     rows = synth.pack(hap)
     for p in (oracle.params(maf=(0, 1)), oracle.params()):
         ref = oracle.ihs(rows, n, pos, gmap, p=p)
-        for kw in (dict(), dict(sweep_warmup=16, sweep_stage_cores=3)):
+        for kw in (dict(), dict(sweep_warmup=16, sweep_stage_cores=3),
+                   dict(sweep_split_tile=16, sweep_warmup=16)):
             got = run_ihs(sg, rows, n, pos, gmap, launch=sweep(sg, **kw),
                           params=sg.selscan_default_params(maf=(p.maf_num, p.maf_den)))
             assert_ihs_equal(got, ref)
