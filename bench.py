@@ -215,6 +215,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--ref-budget", type=float, default=15.0)
+    ap.add_argument("--tables", action="store_true",
+                    help="instead of the main line: the paper's runtime-table workloads "
+                         "(stand-ins) timed on the GPU and, on a bounded sample, the oracle")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -223,6 +226,9 @@ def main():
 
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.tables:
+        run_tables(args)
         return
 
     import torch
@@ -398,6 +404,76 @@ def main():
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+# the paper's 16-thread selscan times (s) of its runtime tables, as context
+PAPER_16_THREADS_S = {"IHS250": 58, "IHS500": 150, "IHS1000": 380, "IHS2000": 752, "CEU22": 33,
+                      "XP250": 25, "XP500": 67, "XP1000": 180, "XP2000": 493, "CEUYRI22": 52}
+
+
+def run_tables(args):
+    """One JSON line: per runtime-table workload (stand-ins of the same shape),
+    the GPU scan time with the default launch and the oracle's rate on a random
+    sample of cores (about 3 s of host time), extrapolated to the whole scan."""
+    import torch
+    import synth
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1403_6854_gb300 as sg
+    import oracle
+    rows_out = []
+    names = ["IHS250", "IHS500", "IHS1000", "IHS2000", "CEU22",
+             "XP250", "XP500", "XP1000", "XP2000", "CEUYRI22"]
+    threads = os.cpu_count() or 1
+    for name in names:
+        sp = synth.spec({"CEU22": "chr22", "CEUYRI22": "xpehh"}.get(name, name))
+        d = synth.generate(sp)
+        hap, pos, gmap = sg.to_device(d.rows, d.pos, d.gmap)
+        nA = sp.pops[0].n
+        nB = sp.pops[1].n if sp.mode == "xpehh" else 0
+
+        def call(o):
+            kw = dict(workspace=None if o is None else o["_workspace"], out=o)
+            if sp.mode == "ihs":
+                return sg.selscan_ihs(hap, nA, pos, gmap, **kw)
+            return sg.selscan_xpehh(hap, nA, nB, pos, gmap, **kw)
+        o = call(None)
+        torch.cuda.synchronize()
+        best = 1e30
+        for _ in range(5):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            o = call(o)
+            b.record()
+            torch.cuda.synchronize()
+            best = min(best, a.elapsed_time(b))
+        st = o["status"].cpu().numpy()
+        cores = int((st != sg.LOCUS_MAF_FILTERED).sum())
+        # oracle on a random sample, growing until ~3 s of host time
+        rng = np.random.default_rng(7)
+        walked = np.flatnonzero(st != sg.LOCUS_MAF_FILTERED)
+        k, spent, done = 16, 0.0, 0
+        while spent < 3.0 and done < walked.size:
+            pick = np.sort(rng.choice(walked, size=min(k, walked.size), replace=False))
+            t0 = time.perf_counter()
+            if sp.mode == "ihs":
+                oracle.ihs(d.rows, nA, d.pos, d.gmap, cores=pick, threads=threads)
+            else:
+                oracle.xpehh(d.rows, nA, nB, d.pos, d.gmap, cores=pick, threads=threads)
+            spent = time.perf_counter() - t0
+            done = pick.size
+            k *= 2
+        orate = done / spent if spent > 0 else 0.0
+        rows_out.append({"dataset": name, "shape": f"{nA}{'+' + str(nB) if nB else ''} x {sp.m}",
+                         "gpu_ms": best, "core_loci": cores,
+                         "gpu_core_loci_per_s": cores / (best / 1e3),
+                         "oracle_core_loci_per_s": orate, "oracle_threads": threads,
+                         "oracle_sample_cores": done,
+                         "paper_selscan_16_threads_s": PAPER_16_THREADS_S[name]})
+    print(json.dumps({"tables": rows_out, "data": "seeded stand-ins of the same shapes (mosaic of "
+                      "100 founders on 4 Mbp; chr22-shaped configs for CEU22 / CEUYRI22)",
+                      "note": "the paper's times are on its 12-core Xeon and are context only"}),
+          flush=True)
 
 
 def run_extras(sg, torch, synth, d, hap, pos, gmap, n, ws):

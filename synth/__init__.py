@@ -213,7 +213,22 @@ def spec(name: str, seed: int = 0) -> ScanSpec:
             sweeps.append(((k + 0.5) / ns * L, width, freq))
         return ScanSpec(name, "ihs", m, L, seed, [PopSpec(5000, 200, sweeps)],
                         map_rate=1.2, map_spread=0.5)
+    if name in TABLE_SHAPES:
+        # stand-ins for the paper's runtime-table data sets: its sample sizes and
+        # SNP counts on a 4 Mbp neutral region (no sweep), 1 cM/Mb map
+        mode, nA, nB, m = TABLE_SHAPES[name]
+        pops = [PopSpec(nA, 100)] + ([PopSpec(nB, 100)] if mode == "xpehh" else [])
+        return ScanSpec(name, mode, m, 4_000_000, seed, pops)
     raise KeyError(name)
+
+
+# name: (mode, n or n_A, n_B, SNPs) of the data sets of the paper's runtime tables
+TABLE_SHAPES = {
+    "IHS250": ("ihs", 250, 0, 9_625), "IHS500": ("ihs", 500, 0, 10_646),
+    "IHS1000": ("ihs", 1000, 0, 11_655), "IHS2000": ("ihs", 2000, 0, 12_724),
+    "XP250": ("xpehh", 125, 125, 12_920), "XP500": ("xpehh", 250, 250, 14_989),
+    "XP1000": ("xpehh", 500, 500, 17_142), "XP2000": ("xpehh", 1000, 1000, 19_567),
+}
 
 
 def _log_uniform(u: float, lo: float, hi: float) -> float:
