@@ -516,6 +516,23 @@ def run_extras(sg, torch, synth, d, hap, pos, gmap, n, ws):
     b.record()
     torch.cuda.synchronize()
     ms = a.elapsed_time(b) / reps
+    # XPEHH at scale (sorted sweep): 2,500 + 2,500 haplotypes x 1,000,000 SNPs
+    x1 = synth.generate(synth.spec("xpehh1m"))
+    xh1, xp1, xg1 = sg.to_device(x1.rows, x1.pos, x1.gmap)
+    o1 = sg.selscan_xpehh(xh1, 2500, 2500, xp1, xg1)
+    torch.cuda.synchronize()
+    a1, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a1.record()
+    o1 = sg.selscan_xpehh(xh1, 2500, 2500, xp1, xg1, workspace=o1["_workspace"], out=o1)
+    b1.record()
+    torch.cuda.synchronize()
+    sg.check(o1)
+    ms1 = a1.elapsed_time(b1)
+    ex["xpehh_1m"] = {"workload": "XPEHH at scale: pop A 2,500 (200 founders, 20 planted sweeps) / "
+                                  "pop B 2,500 (150 founders) haplotypes x 1,000,000 SNPs",
+                      "value": x1.spec.m / (ms1 / 1e3), "unit": "core loci/s", "ms_per_scan": ms1,
+                      "ok_loci": int((o1["status"] == 0).sum())}
+    del o1, xh1, xp1, xg1
     ex["xpehh"] = {"workload": "XPEHH: pop A 204 / pop B 210 haplotypes x 22,147 SNPs",
                    "value": x.spec.m / (ms / 1e3), "unit": "core loci/s", "ms_per_scan": ms}
     return ex

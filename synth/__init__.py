@@ -213,6 +213,18 @@ def spec(name: str, seed: int = 0) -> ScanSpec:
             sweeps.append(((k + 0.5) / ns * L, width, freq))
         return ScanSpec(name, "ihs", m, L, seed, [PopSpec(5000, 200, sweeps)],
                         map_rate=1.2, map_spread=0.5)
+    if name in ("xpehh1m", "xpehh200k"):
+        # XPEHH at scale: A carries the 1M recipe's sweeps, B (other founders)
+        # none; 2,500 + 2,500 haplotypes on 1M SNPs, or 1,000 + 1,000 on 200k
+        m, L, ns, nA = ((1_000_000, 250_000_000, 20, 2500) if name == "xpehh1m"
+                        else (200_000, 50_000_000, 4, 1000))
+        sweeps = []
+        for k in range(ns):
+            width = 50_000.0 + 450_000.0 * uniform(seed, 1, k)
+            freq = 0.3 + 0.6 * uniform(seed, 2, k)
+            sweeps.append(((k + 0.5) / ns * L, width, freq))
+        return ScanSpec(name, "xpehh", m, L, seed, [PopSpec(nA, 200, sweeps), PopSpec(nA, 150)],
+                        map_rate=1.2, map_spread=0.5)
     if name in TABLE_SHAPES:
         # stand-ins for the paper's runtime-table data sets: its sample sizes and
         # SNP counts on a 4 Mbp neutral region (no sweep), 1 cM/Mb map

@@ -177,3 +177,17 @@ def test_haplotype_limit(sg, n):
     ref = oracle.ihs(rows, n, pos, gmap, cores=cores)
     got = run_ihs(sg, rows, n, pos, gmap, launch=sweep(sg, sweep_warmup=32, sweep_stage_cores=16))
     assert_ihs_equal(got, ref, idx=cores)
+
+
+def test_xpehh_at_scale_sampled_cores(sg):
+    """1,000 + 1,000 haplotypes x 200,000 SNPs with four planted sweeps in A:
+    the default launch takes the sorted sweep; sampled cores (including the
+    sweep centres) match the oracle."""
+    d = synth.generate(synth.spec("xpehh200k"))
+    got = run_xpehh(sg, d.rows, 1000, 1000, d.pos, d.gmap)
+    rng = np.random.default_rng(1)
+    centres = np.searchsorted(d.pos, [(k + 0.5) / 4 * 50_000_000 for k in range(4)])
+    cores = np.unique(np.concatenate([rng.choice(d.spec.m, 24, replace=False), centres]))
+    ref = oracle.xpehh(d.rows, 1000, 1000, d.pos, d.gmap, cores=cores)
+    assert_xpehh_equal(got, ref, idx=cores)
+    assert np.array_equal(np.isfinite(got["lnratio"]), got["status"] == 0)
