@@ -308,6 +308,18 @@ int selscan_pack(const uint8_t *hap01, int32_t n, int64_t m, int32_t hap_major,
  * arguments.  Host only: no device work. */
 int32_t selscan_launch_count(int32_t n_total, int64_t m, int32_t mode, const selscan_launch *launch);
 
+/* Read a TPED haplotype file (host code; no device work): one line per
+ * marker with the chromosome, marker id, genetic position (map units),
+ * physical position and then the n phased alleles coded 0 / 1 (Section 1.1),
+ * separated by white space; blank lines are skipped.  Two calls: with
+ * rows == NULL it only sets *n and *m; then with host buffers rows [m][ld]
+ * (ld >= ceil(n / 64), filled bit-packed with pad bits 0 -- the layout of
+ * selscan_ihs), pos_bp [m] and gmap [m], and *n, *m as returned.
+ * SELSCAN_ERR_INVALID_ARG for an unreadable file, a malformed line or a
+ * line of another width (*err_line = its 1-based marker-line index). */
+int selscan_read_tped(const char *path, int32_t *n, int64_t *m, uint64_t *rows, int64_t ld,
+                      int64_t *pos_bp, double *gmap, int64_t *err_line);
+
 /* Static description of a return or error code. */
 const char *selscan_strerror(int code);
 

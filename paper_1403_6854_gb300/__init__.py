@@ -80,7 +80,7 @@ EXPORTS = ("selscan_default_params", "selscan_workspace_bytes", "selscan_ihs", "
            "selscan_ehh", "selscan_ehh_noalloc", "selscan_pack", "selscan_strerror",
            "selscan_batch_item_bytes", "selscan_batch_workspace_bytes", "selscan_batch_prepare",
            "selscan_batch_run", "selscan_batch_finalize", "selscan_launch_count",
-           "selscan_normalize", "selscan_normalize_workspace_bytes")
+           "selscan_normalize", "selscan_normalize_workspace_bytes", "selscan_read_tped")
 EHH_NOALLOC_MAX_N = 8192
 
 _lib = None
@@ -132,6 +132,10 @@ def load_library():
     lib.selscan_batch_run.argtypes = [ctypes.POINTER(selscan_scan), ctypes.c_int32, _P, _P, _P,
                                       ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, _P,
                                       ctypes.c_size_t, _P]
+    lib.selscan_read_tped.restype = ctypes.c_int
+    lib.selscan_read_tped.argtypes = [ctypes.c_char_p, ctypes.POINTER(ctypes.c_int32),
+                                      ctypes.POINTER(ctypes.c_int64), _P, ctypes.c_int64, _P, _P,
+                                      ctypes.POINTER(ctypes.c_int64)]
     lib.selscan_normalize_workspace_bytes.restype = ctypes.c_size_t
     lib.selscan_normalize_workspace_bytes.argtypes = [ctypes.c_int32]
     lib.selscan_normalize.restype = ctypes.c_int
@@ -187,6 +191,27 @@ def make_launch(schedule: int = SCHED_DEFAULT, warps_per_cta: int = 0, ctas_per_
         L.walk_begin_event = ctypes.c_void_p(events[0].cuda_event)
         L.walk_end_event = ctypes.c_void_p(events[1].cuda_event)
     return L
+
+
+def selscan_read_tped(path: str, ld: Optional[int] = None):
+    """TPED file -> (packed rows uint64 [m, ld], positions int64 [m], map float64 [m], n)
+    on the host, ready for to_device / selscan_ihs."""
+    import numpy as np
+    lib = load_library()
+    n, m, bad = ctypes.c_int32(0), ctypes.c_int64(0), ctypes.c_int64(0)
+    rc = lib.selscan_read_tped(path.encode(), ctypes.byref(n), ctypes.byref(m), None, 0, None,
+                               None, ctypes.byref(bad))
+    if rc != OK:
+        raise SelscanError(rc, f"selscan_read_tped: {path}, marker line {bad.value}")
+    ld = ld or (n.value + 63) // 64
+    rows = np.zeros((m.value, ld), dtype=np.uint64)
+    pos = np.zeros(m.value, dtype=np.int64)
+    gmap = np.zeros(m.value, dtype=np.float64)
+    rc = lib.selscan_read_tped(path.encode(), ctypes.byref(n), ctypes.byref(m), rows.ctypes.data, ld,
+                               pos.ctypes.data, gmap.ctypes.data, ctypes.byref(bad))
+    if rc != OK:
+        raise SelscanError(rc, f"selscan_read_tped: {path}, marker line {bad.value}")
+    return rows, pos, gmap, n.value
 
 
 def selscan_normalize(score: torch.Tensor, status: torch.Tensor, n1: torch.Tensor, n: int,

@@ -10,7 +10,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libselscan_gb300.so")
-SOURCES = ["api.cu", "kernels.cu", "batch.cu", "noalloc.cu", "sweep.cu", "normalize.cu"]
+SOURCES = ["api.cu", "kernels.cu", "batch.cu", "noalloc.cu", "sweep.cu", "normalize.cu", "tped.cpp"]
 HEADERS = ["walk.cuh", "internal.h", "device_common.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
@@ -41,7 +41,7 @@ def build(force: bool = False, ptxas_verbose: bool = False, quiet: bool = True) 
     procs = []
     objs = []
     for s in SOURCES:
-        obj = os.path.join(BUILD, s.replace(".cu", ".o"))
+        obj = os.path.join(BUILD, os.path.splitext(s)[0] + ".o")
         objs.append(obj)
         cmd = [NVCC, "-c", os.path.join(CSRC, s), "-o", obj] + _flags(ptxas_verbose)
         procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
