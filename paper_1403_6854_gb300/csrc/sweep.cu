@@ -181,9 +181,12 @@ __global__ void __launch_bounds__(T, T == 512 ? 2 : 3) sweep_kernel(SweepArgs w)
         const unsigned *Pc = P0 + cur * np;
         const unsigned *row = R0 + rb * W32r;
         // pass 1: alleles, the new run lengths as far as this segment decides
-        // them, and the segment summary
-        unsigned vmask = 0u, all = kInf16, mn0 = kInf16, mn1 = kInf16, hp0 = 0u, hp1 = 0u;
-        unsigned f0min = kInf16, f1min = kInf16, f0bi = 0u, f1bi = 0u;
+        // them, and the segment summary.  Both tails live in one word (allele
+        // 0 low, 1 high).  Run lengths stay at most 65,000 (a chunk plus its
+        // warm-up spans at most 65,000 markers), so adding one to each half
+        // never carries.  The first element of each allele in the segment gets
+        // its prefix tail after placement.
+        unsigned vmask = 0u, allw = 0xFFFFFFFFu, mn01 = 0xFFFFFFFFu;
 #pragma unroll
         for (int e = 0; e < EMAX; e += 2) {
             if (e < E) {
@@ -191,30 +194,21 @@ __global__ void __launch_bounds__(T, T == 512 ? 2 : 3) sweep_kernel(SweepArgs w)
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     const unsigned pv = h ? q.y : q.x;
-                    const unsigned bi = pv & 0xFFFFu, mv = pv >> 16;
-                    const unsigned v = (row[bi >> 5] >> (bi & 31u)) & 1u;
+                    const unsigned wd = row[(pv & 0xFFFFu) >> 5];
+                    const unsigned v = __funnelshift_r(wd, wd, pv) & 1u;   // bit pv % 32
                     vmask |= v << (e + h);
-                    all = min(all, mv);
-                    mn0 = min(mn0, mv);
-                    mn1 = min(mn1, mv);
-                    const unsigned mnv = v ? mn1 : mn0;
-                    const unsigned hpv = v ? hp1 : hp0;
-                    if (!hpv) {                  // first of its allele in the segment
-                        if (v) { f1min = mnv; f1bi = bi; }
-                        else { f0min = mnv; f0bi = bi; }
-                    }
-                    const unsigned out = min(mnv + 1u, kInf16);
-                    if (CACHE) val[e + h] = bi | (out << 16);
-                    mn1 = v ? kInf16 : mn1;
-                    mn0 = v ? mn0 : kInf16;
-                    hp1 |= v;
-                    hp0 |= v ^ 1u;
+                    allw = min(allw, pv);                 // high half: the segment minimum
+                    mn01 = __vminu2(mn01, __byte_perm(pv, 0u, 0x3232u));
+                    if (CACHE) val[e + h] = __byte_perm(pv, mn01 + 0x00010001u, v ? 0x7610u : 0x5410u);
+                    mn01 |= v ? 0xFFFF0000u : 0x0000FFFFu;
                 }
             }
         }
-        const unsigned zeros = (unsigned)E - (unsigned)__popc(vmask);
-        unsigned p0 = mn0 | (mn1 << 16);
-        unsigned p1 = all | (zeros << 16) | (hp0 << 30) | (hp1 << 31);
+        const unsigned ones = (unsigned)__popc(vmask);
+        const unsigned zeros = (unsigned)E - ones;
+        const unsigned hp0 = zeros != 0u, hp1 = ones != 0u;
+        unsigned p0 = mn01;
+        unsigned p1 = (allw >> 16) | (zeros << 16) | (hp0 << 30) | (hp1 << 31);
         // warp inclusive scan
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
@@ -249,13 +243,14 @@ __global__ void __launch_bounds__(T, T == 512 ? 2 : 3) sweep_kernel(SweepArgs w)
         unsigned z = zs, o = os;
         unsigned *Pn = P0 + (cur ^ 1) * np;
         if (CACHE) {
+            // allele-0 elements go to zs + (elements so far) - (ones so far)
+            const unsigned zk = zs + os;
 #pragma unroll
             for (int e = 0; e < EMAX; ++e) {
                 if (e < E) {
                     const unsigned one = (vmask >> e) & 1u;
-                    Pn[one ? o : z] = val[CACHE ? e : 0];
+                    Pn[one ? o : zk + (unsigned)e - o] = val[CACHE ? e : 0];
                     o += one;
-                    z += one ^ 1u;
                 }
             }
         }
@@ -284,13 +279,17 @@ __global__ void __launch_bounds__(T, T == 512 ? 2 : 3) sweep_kernel(SweepArgs w)
                 Pn[p] = (q & 0xFFFFu) | (out << 16);
             }
         } else {
-            if (hp0) {                            // first allele-0 element of the segment
-                const unsigned out = ((x1 >> 30) & 1u) ? min(min(x0 & 0xFFFFu, f0min) + 1u, kInf16) : 0u;
-                Pn[zs] = f0bi | (out << 16);
+            // the first allele-0 / allele-1 element of the segment (placed at zs
+            // / os): 1 + the minimum over the prefix tail and its own span
+            if (hp0) {
+                const unsigned u = Pn[zs];
+                const unsigned out = ((x1 >> 30) & 1u) ? min((x0 & 0xFFFFu) + 1u, u >> 16) : 0u;
+                Pn[zs] = (u & 0xFFFFu) | (out << 16);
             }
             if (hp1) {
-                const unsigned out = (x1 >> 31) ? min(min(x0 >> 16, f1min) + 1u, kInf16) : 0u;
-                Pn[os] = f1bi | (out << 16);
+                const unsigned u = Pn[os];
+                const unsigned out = (x1 >> 31) ? min((x0 >> 16) + 1u, u >> 16) : 0u;
+                Pn[os] = (u & 0xFFFFu) | (out << 16);
             }
         }
 #pragma unroll
