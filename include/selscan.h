@@ -126,8 +126,8 @@ typedef struct {
                                   16..16384 (0 = 2048); walks longer than this may take the
                                   second pass */
     int32_t sweep_stage_cores; /* sweep schedule: cores per chunk between walk launches,
-                                  1..4096 (0 = the whole chunk, capped so that the slot
-                                  buffer stays near 12 GiB); sizes the slot buffer */
+                                  1..8192 (0 = the whole chunk, capped so that the slot
+                                  buffer stays near 24 GiB); sizes the slot buffer */
     int32_t sweep_threads;     /* sweep schedule: threads per sorting CTA, 256 or 512
                                   (0 = 256 up to 6144 haplotypes, else 512) */
     int32_t sweep_split_tile;  /* sweep schedule: lanes per split walk, 32 or 16 (two walks

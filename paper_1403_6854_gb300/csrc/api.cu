@@ -21,7 +21,7 @@ constexpr int kDefaultBigGroup = 32;
 constexpr int kMaxHaplotypes = 65000;
 constexpr int kDefaultSweepWarmup = 2048;
 constexpr int kDefaultSplitTile = 32;
-constexpr size_t kSweepSlotBudget = (size_t)12 << 30;  // bytes of sweep slots per scan
+constexpr size_t kSweepSlotBudget = (size_t)24 << 30;  // bytes of sweep slots per scan
 constexpr size_t kMaxSmemPerCta = 227 * 1024;
 
 struct SweepPlan {
@@ -64,7 +64,7 @@ SweepPlan make_sweep_plan(int n_total, long long m, int mode, const selscan_laun
     if (w.L < 16) w.L = 16;
     if (w.L > 16384) w.L = 16384;
     w.R = (L && L->sweep_stage_cores > 0) ? L->sweep_stage_cores : 0;
-    if (w.R > 4096) w.R = 4096;
+    if (w.R > 8192) w.R = 8192;
     // 256-thread CTAs (3 per SM) up to 24 elements per thread, else 512 (2 per SM)
     const int want = L ? L->sweep_threads : 0;
     w.threads = (want == 256 || want == 512) ? want : (n_total <= 256 * 24 ? 256 : 512);
@@ -90,7 +90,7 @@ SweepPlan make_sweep_plan(int n_total, long long m, int mode, const selscan_laun
         // else as many cores as fit (fewer, longer stages launch less)
         const long long fit = (long long)(kSweepSlotBudget / ((size_t)2 * w.nch * w.slot_bytes));
         long long r = w.B < fit ? w.B : fit;
-        if (r > 4096) r = 4096;
+        if (r > 8192) r = 8192;
         if (r < 16) r = 16;
         w.R = (int)r;
     }
@@ -256,6 +256,7 @@ int run_scan(int mode, const uint64_t *hap, int64_t ld, int32_t nA, int32_t nB, 
     if (sweep && (sweep_smem_bytes(n_total, (nA + 63) / 64 + (nB + 63) / 64, plan.sw.threads) > kMaxSmemPerCta ||
                   (size_t)plan.sw.split_bytes * (kSplitWarps * 32 / plan.sw.split_tile) > kMaxSmemPerCta))
         return SELSCAN_ERR_UNSUPPORTED;
+    if (sweep && (plan.sw.slot_bytes & 15)) return SELSCAN_ERR_UNSUPPORTED;   // slots are read in 16-byte units
     const Layout l = make_layout(n_total, m, mode, plan.nslots, sweep ? &plan.sw : nullptr);
     if (!workspace || ws_bytes < l.total || ((uintptr_t)workspace & 255)) return SELSCAN_ERR_WORKSPACE;
     cudaStream_t s = (cudaStream_t)stream;

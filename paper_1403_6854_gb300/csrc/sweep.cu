@@ -40,6 +40,8 @@ namespace selscan {
 namespace {
 
 constexpr unsigned kInf16 = 0xFFFFu;
+constexpr int kSlotListCap = 1024;          // first-window boundaries kept per slot
+constexpr int kSplitListSmem = 1024;        // window list entries a walking warp keeps on chip
 
 __host__ __device__ inline int sweep_e(int n, int T)
 {
@@ -78,17 +80,31 @@ __device__ __forceinline__ unsigned bit_index(const SweepArgs &w, int h)
 
 }  // namespace
 
+// Slot of one core: header {n0, history horizon, W1, 0}, the run lengths M
+// (u16 per sorted position), for XPEHH the population-A flags of the sorted
+// positions, then the first window: W1 + 1 step offsets (u16) and its
+// boundaries ordered by step (u16 positions).  The window is the longest run
+// of steps 1..W1 (W1 <= 64) whose boundaries fit slot_list_cap(n) entries.
+namespace {
+__host__ __device__ inline int slot_list_cap(int n) { return n < kSlotListCap ? n : kSlotListCap; }
+__host__ __device__ inline size_t slot_isa_at(int n) { return 16 + (((size_t)n * 2 + 15) & ~(size_t)15); }
+__host__ __device__ inline size_t slot_off_at(int n, int xpehh)
+{
+    return slot_isa_at(n) + (xpehh ? (((size_t)split_nw(n) * 4 + 15) & ~(size_t)15) : 0);
+}
+__host__ __device__ inline size_t slot_list_at(int n, int xpehh) { return slot_off_at(n, xpehh) + 144; }
+}  // namespace
+
 size_t sweep_smem_bytes(int n, int W, int T)
 {
     const int W32 = ((2 * W) + 4) & ~3;
-    return (size_t)sweep_npad(n, T) * 4 * 2 + (size_t)W32 * 4 * 2 + T / 32 * 8;
+    return (size_t)sweep_npad(n, T) * 4 * 2 + (size_t)W32 * 4 * 2 + T / 32 * 8 + 2 * 65 * 4;
 }
 
 size_t sweep_slot_bytes(int n, int xpehh)
 {
-    size_t b = 16 + (((size_t)n * 2 + 15) & ~(size_t)15);
-    if (xpehh) b += ((size_t)split_nw(n) * 4 + 15) & ~(size_t)15;
-    return b;
+    // a multiple of 16 bytes: every slot's M region is read and written in 16-byte units
+    return slot_list_at(n, xpehh) + (((size_t)slot_list_cap(n) * 2 + 15) & ~(size_t)15);
 }
 
 size_t sweep_state_bytes(int n, int T) { return (size_t)sweep_npad(n, T) * 4; }
@@ -118,6 +134,8 @@ __global__ void __launch_bounds__(T, T == 512 ? 2 : 3) sweep_kernel(SweepArgs w)
     unsigned *P0 = (unsigned *)smem;             // buffer b at P0 + b * np
     unsigned *R0 = P0 + 2 * np;                  // row buffer r at R0 + r * W32r
     unsigned *wsum = R0 + 2 * W32r;
+    unsigned *hcnt = wsum + 2 * NW;              // a core's first window: per-step counts,
+    unsigned *hoff = hcnt + 65;                  // then cursors and (at [64]) W1
 
     const int dir = blockIdx.x / w.nch;          // 0: walks toward lower indices
     const int c = blockIdx.x % w.nch;
@@ -158,6 +176,7 @@ __global__ void __launch_bounds__(T, T == 512 ? 2 : 3) sweep_kernel(SweepArgs w)
     }
     const unsigned *hap32 = (const unsigned *)w.a.hap;
     const long long ld32 = 2 * w.a.ld;
+    for (int t = tid; t < 64; t += T) hcnt[t] = 0u;
     for (int t = tid; t < W32; t += T) R0[t] = hap32[xfirst * ld32 + t];
     if (tid < W32r - W32) {
         R0[W32 + tid] = 0xFFFFFFFFu;
@@ -303,6 +322,7 @@ __global__ void __launch_bounds__(T, T == 512 ? 2 : 3) sweep_kernel(SweepArgs w)
         if (is_core && cst != (int)SELSCAN_LOCUS_MAF_FILTERED) {
             const int r = dir == 0 ? (int)(x - klo) : (int)(khi - 1 - x);
             unsigned char *slot = w.slots + ((size_t)(dir * w.nch + c) * w.R + r) * w.slot_bytes;
+            const int xp = w.a.nB > 0;
             if (tid == 0) {
                 int *hdr = (int *)slot;
                 hdr[0] = (int)n0;
@@ -313,17 +333,22 @@ __global__ void __launch_bounds__(T, T == 512 ? 2 : 3) sweep_kernel(SweepArgs w)
             }
             const unsigned *Ps = P0 + cur * np;
             // run lengths, 8 per 16-byte store (np is a multiple of 512, the
-            // slot's M region a multiple of 16 bytes; values past n are never read)
+            // slot's M region a multiple of 16 bytes; values past n are never
+            // read), counting the boundaries of each of steps 1..64 (M in [1, 64])
             const uint4 *P4 = (const uint4 *)Ps;
             uint4 *M4 = (uint4 *)(slot + 16);
             for (int t = tid; t < (n + 7) / 8; t += T) {
                 const uint4 a = P4[2 * t], b = P4[2 * t + 1];
                 M4[t] = make_uint4((a.x >> 16) | (a.y & 0xFFFF0000u), (a.z >> 16) | (a.w & 0xFFFF0000u),
                                    (b.x >> 16) | (b.y & 0xFFFF0000u), (b.z >> 16) | (b.w & 0xFFFF0000u));
+                const unsigned e8[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    if (e8[j] - 0x10000u < 0x400000u && 8 * t + j < n) atomicAdd(hcnt + (e8[j] >> 16) - 1, 1u);
             }
-            if (w.a.nB > 0) {                    // population of each sorted position
+            if (xp) {                            // population of each sorted position
                 const unsigned limA = 64u * (unsigned)w.a.WA;
-                unsigned *isA = (unsigned *)(slot + 16 + (((size_t)n * 2 + 15) & ~(size_t)15));
+                unsigned *isA = (unsigned *)(slot + slot_isa_at(n));
                 const int nw = split_nw(n);
                 for (int q = tid; q < nw; q += T) {
                     unsigned word = 0u;
@@ -333,6 +358,48 @@ __global__ void __launch_bounds__(T, T == 512 ? 2 : 3) sweep_kernel(SweepArgs w)
                     }
                     isA[q] = word;
                 }
+            }
+            __syncthreads();
+            // the first window: the longest run of steps from step 1 on whose
+            // boundaries fit the slot's list
+            unsigned short *soff = (unsigned short *)(slot + slot_off_at(n, xp));
+            if (warp == 0) {
+                const unsigned c0 = hcnt[2 * lane], c1 = hcnt[2 * lane + 1];
+                unsigned incl = c0 + c1;
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    const unsigned v = __shfl_up_sync(FULLMASK, incl, d);
+                    if (lane >= d) incl += v;
+                }
+                const unsigned ex = incl - c0 - c1;
+                const unsigned cap = (unsigned)slot_list_cap(n);
+                // steps 2 lane + 1 and 2 lane + 2 end at offsets ex + c0 and incl
+                const unsigned w1 = __popc(__ballot_sync(FULLMASK, ex + c0 <= cap)) +
+                                    __popc(__ballot_sync(FULLMASK, incl <= cap));
+                soff[2 * lane] = (unsigned short)min(ex, 0xFFFFu);
+                soff[2 * lane + 1] = (unsigned short)min(ex + c0, 0xFFFFu);
+                if (lane == 31) soff[64] = (unsigned short)min(incl, 0xFFFFu);
+                hoff[2 * lane] = ex;
+                hoff[2 * lane + 1] = ex + c0;
+                hcnt[2 * lane] = 0u;
+                hcnt[2 * lane + 1] = 0u;
+                if (lane == 0) {
+                    hoff[64] = w1;
+                    ((int *)slot)[2] = (int)w1;
+                    ((int *)slot)[3] = 0;
+                }
+            }
+            __syncthreads();
+            // place the window's boundaries by step
+            const unsigned lim = hoff[64] << 16;
+            unsigned short *slist = (unsigned short *)(slot + slot_list_at(n, xp));
+            for (int t = tid; t < (n + 7) / 8; t += T) {
+                const uint4 a = P4[2 * t], b = P4[2 * t + 1];
+                const unsigned e8[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    if (e8[j] - 0x10000u < lim && 8 * t + j < n)
+                        slist[atomicAdd(hoff + (e8[j] >> 16) - 1, 1u)] = (unsigned short)(8 * t + j);
             }
         }
         if (!more) break;
@@ -355,6 +422,7 @@ namespace {
 struct SplitSmem {
     unsigned *O, *N, *SO, *SN;
     unsigned *cnt, *off;
+    unsigned short *lst;                  // the current window's list, when it fits
     unsigned *isA, *PA;
     int nw, ns;
 };
@@ -373,6 +441,7 @@ __device__ inline SplitSmem split_smem(unsigned char *base, int n, int xpehh)
     s.off = p; p += 65;
     s.isA = xpehh ? p : nullptr;
     s.PA = xpehh ? p + s.nw : nullptr;
+    s.lst = (unsigned short *)(p + (xpehh ? 2 * s.nw : 0));
     return s;
 }
 
@@ -428,51 +497,14 @@ __device__ __forceinline__ unsigned count_a(const SplitSmem &s, int x)
     return s.PA[x >> 5] + (unsigned)__popc(s.isA[x >> 5] & ((1u << (x & 31)) - 1u));
 }
 
-// Group the boundaries t with lo <= M[t] < lo + 64 by step: one pass over M
-// (8 values per 16-byte load, four loads in flight per lane) collects them
-// with their rank inside their step, then they are placed by step.  Done by
-// one tile of G lanes.
+// Offsets of the 64 step counts and placement of the K staged boundaries
+// (position | step in window << 16 | rank in step << 32) by step.
 template <int G, typename Tile>
-__device__ void build_window(const Tile &tile, const SplitSmem &s, const unsigned *M32, int n,
-                             int lo, unsigned long long *stage, unsigned short *list)
+__device__ const unsigned short *place_window(const Tile &tile, const SplitSmem &s, unsigned K,
+                                             const unsigned long long *stage, unsigned short *list)
 {
     const int lane = tile.thread_rank();
-    const unsigned ltm = (1u << lane) - 1u;
-    const uint4 *M4 = (const uint4 *)M32;
-    for (int q = lane; q < 64; q += G) s.cnt[q] = 0u;
     tile.sync();
-    const int n4 = (n + 7) >> 3;
-    unsigned K = 0;
-    for (int base = 0; base < n4; base += 4 * G) {
-        uint4 q[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int idx = base + u * G + lane;
-            q[u] = idx < n4 ? __ldg(M4 + idx) : make_uint4(~0u, ~0u, ~0u, ~0u);
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int t0 = (base + u * G + lane) * 8;
-            const unsigned wv[4] = {q[u].x, q[u].y, q[u].z, q[u].w};
-            // one ballot per value of the 8 in hand
-#pragma unroll 1
-            for (int h = 0; h < 8; ++h) {
-                const unsigned ww = (h >> 1) == 0 ? wv[0] : (h >> 1) == 1 ? wv[1] : (h >> 1) == 2 ? wv[2] : wv[3];
-                const int t = t0 + h;
-                const unsigned d = ((h & 1) ? (ww >> 16) : (ww & 0xFFFFu)) - (unsigned)lo;
-                const bool in = t < n && d < 64u;
-                const unsigned bal = tile.ballot(in);
-                if (in) {
-                    const unsigned r = atomicAdd(s.cnt + d, 1u);
-                    stage[K + __popc(bal & ltm)] =
-                        (unsigned long long)t | ((unsigned long long)d << 16) | ((unsigned long long)r << 32);
-                }
-                K += __popc(bal);
-            }
-        }
-    }
-    tile.sync();
-    // exclusive offsets of the 64 step counts: 64 / G consecutive counts per lane
     constexpr int C = 64 / G;
     unsigned own = 0;
 #pragma unroll
@@ -492,12 +524,80 @@ __device__ void build_window(const Tile &tile, const SplitSmem &s, const unsigne
     }
     if (lane == G - 1) s.off[64] = incl;
     tile.sync();
+    // the list goes to shared memory when it fits, else to the global scratch
+    unsigned short *dst = K <= (unsigned)kSplitListSmem ? s.lst : list;
     for (unsigned j = lane; j < K; j += G) {
         const unsigned long long e = stage[j];
-        list[s.off[(unsigned)(e >> 16) & 63u] + (unsigned)(e >> 32)] = (unsigned short)(e & 0xFFFFu);
+        dst[s.off[(unsigned)(e >> 16) & 63u] + (unsigned)(e >> 32)] = (unsigned short)(e & 0xFFFFu);
     }
     tile.sync();
+    return dst;
 }
+
+// Group the boundaries t with lo <= M[t] < lo + 64 by step: one pass over M
+// (8 values per 16-byte load, four loads in flight per lane) marks the values
+// in the window with two integer operations per 16-bit half; only the marked
+// ones are ranked inside their step and staged, then placed by step.  Done by one tile of G lanes.  Window starts
+// stay below 65,001 (run lengths are at most 65,000), so the all-ones fill
+// past the slot's end is never marked.
+template <int G, typename Tile>
+__device__ const unsigned short *build_window(const Tile &tile, const SplitSmem &s, const unsigned *M32,
+                                              int n, int lo, unsigned long long *stage,
+                                              unsigned short *list)
+{
+    const int lane = tile.thread_rank();
+    const uint4 *M4 = (const uint4 *)M32;
+    const unsigned short *M16 = (const unsigned short *)M32;
+    for (int q = lane; q < 64; q += G) s.cnt[q] = 0u;
+    tile.sync();
+    const int n4 = (n + 7) >> 3;
+    const unsigned ulo = (unsigned)lo, uhi = (unsigned)lo << 16;
+    unsigned K = 0;
+    for (int base = 0; base < n4; base += 4 * G) {
+        uint4 q[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int idx = base + u * G + lane;
+            q[u] = idx < n4 ? __ldg(M4 + idx) : make_uint4(~0u, ~0u, ~0u, ~0u);
+        }
+        // bit 8u + v: value v of this lane's u-th group of eight is in the window
+        unsigned hit = 0u;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const unsigned wv[4] = {q[u].x, q[u].y, q[u].z, q[u].w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (((wv[j] - ulo) & 0xFFC0u) == 0u) hit |= 1u << (8 * u + 2 * j);
+                if (((wv[j] - uhi) & 0xFFC00000u) == 0u) hit |= 1u << (8 * u + 2 * j + 1);
+            }
+        }
+        if (base + 4 * G > n4 && (n & 7)) {      // the last group holds values past n
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (base + u * G + lane == n4 - 1) hit &= ~(((0xFFu << (n & 7)) & 0xFFu) << (8 * u));
+        }
+        if (tile.ballot(hit != 0u) == 0u) continue;
+        const unsigned c = (unsigned)__popc(hit);
+        unsigned incl = c;
+#pragma unroll
+        for (int d = 1; d < G; d <<= 1) {
+            const unsigned v = tile.shfl_up(incl, d);
+            if (lane >= d) incl += v;
+        }
+        unsigned at = K + incl - c;
+        while (hit) {
+            const int bb = __ffs(hit) - 1;
+            hit &= hit - 1u;
+            const int t = (base + (bb >> 3) * G + lane) * 8 + (bb & 7);
+            const unsigned d = (unsigned)__ldg(M16 + t) - ulo;
+            const unsigned r = atomicAdd(s.cnt + d, 1u);
+            stage[at++] = (unsigned long long)t | ((unsigned long long)d << 16) | ((unsigned long long)r << 32);
+        }
+        K += tile.shfl(incl, G - 1);
+    }
+    return place_window<G>(tile, s, K, stage, list);
+}
+
 
 struct ClassWalk {
     unsigned long long D, S, prev, dig, numD;   // numD = cut_num * D
@@ -579,6 +679,7 @@ size_t split_smem_per_warp(int n, int xpehh)
     const int nw = split_nw(n), ns = (nw + 31) >> 5;
     size_t b = (size_t)nw * 4 * 2 + (size_t)ns * 4 * 2 + 64 * 4 + 65 * 4;
     if (xpehh) b += (size_t)nw * 4 * 2;
+    b += (size_t)kSplitListSmem * 2;
     return (b + 15) & ~(size_t)15;
 }
 
@@ -637,12 +738,13 @@ __global__ void __launch_bounds__(kSplitWarps * 32, SPLIT_MIN_CTAS) split_walk_k
         const unsigned char *slot = w.slots + (size_t)gslot * w.slot_bytes;
         const int n0 = ((const int *)slot)[0];
         const int hz = ((const int *)slot)[1];
+        const int w1 = ((const int *)slot)[2];
         const unsigned *M32 = (const unsigned *)(slot + 16);
 
         for (int q = lane; q < s.nw; q += G) { s.O[q] = 0u; s.N[q] = 0u; }
         for (int q = lane; q < s.ns; q += G) { s.SO[q] = 0u; s.SN[q] = 0u; }
         if (NPOP == 2) {
-            const unsigned *isA = (const unsigned *)(slot + 16 + (((size_t)n * 2 + 15) & ~(size_t)15));
+            const unsigned *isA = (const unsigned *)(slot + slot_isa_at(n));
             unsigned carry = 0u;
             for (int base = 0; base < s.nw; base += G) {
                 const int q = base + lane;
@@ -705,8 +807,23 @@ __global__ void __launch_bounds__(kSplitWarps * 32, SPLIT_MIN_CTAS) split_walk_k
         const long long step = dir ? 1 : -1;
         double gq = 0.0;        // this lane's step of the current G-step block:
                                 // map step g >= 0, -1 past the array end, -2 a gap abort
-        int lo = 1;
-        if (any) build_window<G>(tile, s, M32, n, lo, stage, list);
+        // steps [lo, lo + wlen) are grouped in cl: first the slot's window
+        // (steps 1..w1), then windows of 64 steps found in M
+        int lo = 1, wlen = w1 > 0 ? w1 : 64;
+        const unsigned short *cl = s.lst;
+        if (any) {
+            if (w1 > 0) {                        // the slot's list, copied on chip
+                const unsigned short *so = (const unsigned short *)(slot + slot_off_at(n, NPOP == 2));
+                const unsigned *sl = (const unsigned *)(slot + slot_list_at(n, NPOP == 2));
+                for (int q = lane; q <= w1; q += G) s.off[q] = so[q];
+                const int kw = ((int)so[w1] + 1) >> 1;
+#pragma unroll 4
+                for (int q = lane; q < kw; q += G) ((unsigned *)s.lst)[q] = __ldg(sl + q);
+                tile.sync();
+            } else {
+                cl = build_window<G>(tile, s, M32, n, lo, stage, list);
+            }
+        }
         int fin = WALK_OK;                           // how the still-active walks end
         long long i = 1;
         for (; any; ++i) {
@@ -732,9 +849,10 @@ __global__ void __launch_bounds__(kSplitWarps * 32, SPLIT_MIN_CTAS) split_walk_k
             const double g = tile.shfl(gq, (int)((i - 1) & (G - 1)));
             if (g < 0.0) { fin = g == -1.0 ? WALK_EDGE : WALK_GAP; break; }
             if (i > (long long)hz) { fin = WALK_UNFINISHED; break; }
-            if (i >= lo + 64) {
-                lo += 64;
-                build_window<G>(tile, s, M32, n, lo, stage, list);
+            if (i >= lo + wlen) {
+                lo += wlen;
+                wlen = 64;
+                cl = build_window<G>(tile, s, M32, n, lo, stage, list);
             }
             // ---- the boundaries that part at this step
             const unsigned j0 = s.off[i - lo], j1 = s.off[i - lo + 1];
@@ -743,7 +861,7 @@ __global__ void __launch_bounds__(kSplitWarps * 32, SPLIT_MIN_CTAS) split_walk_k
                 // new run starts first, then their reductions, then merge
                 if (j1 - j0 <= (unsigned)G) {     // one boundary per lane, loaded once
                     bool has = lane < (int)(j1 - j0);
-                    const int b = has ? (int)list[j0 + lane] : 0;
+                    const int b = has ? (int)cl[j0 + lane] : 0;
                     // an iHS class whose walk has ended needs its runs no more
                     if (NPOP == 1) has = has && (b < n0 ? cw[0].active : cw[NWK - 1].active);
                     const unsigned bw = 1u << (b & 31), sw = 1u << ((b >> 5) & 31);
@@ -764,7 +882,7 @@ __global__ void __launch_bounds__(kSplitWarps * 32, SPLIT_MIN_CTAS) split_walk_k
                     tile.sync();
                     }
                 } else {
-                    split_many<NPOP, G>(tile, s, list, j0, j1, n, n0, d0, d1, d2);
+                    split_many<NPOP, G>(tile, s, cl, j0, j1, n, n0, d0, d1, d2);
                 }
                 d0 = cg::reduce(tile, d0, cg::plus<int>());
                 d1 = cg::reduce(tile, d1, cg::plus<int>());
