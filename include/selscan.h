@@ -123,7 +123,7 @@ typedef struct {
     int32_t big_group_entries; /* groups with at least this many 32-bit words are split by the
                                   whole warp, smaller ones one lane each (0 = 32) */
     int32_t sweep_warmup;      /* sweep schedule: markers sorted before a chunk's first core,
-                                  16..16384 (0 = 2048); walks longer than this may take the
+                                  16..16384 (0 = 1536); walks longer than this may take the
                                   second pass */
     int32_t sweep_stage_cores; /* sweep schedule: cores per chunk between walk launches,
                                   1..8192 (0 = the whole chunk, capped so that the slot

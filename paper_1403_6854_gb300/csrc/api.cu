@@ -19,7 +19,7 @@ constexpr int kDefaultSmemEntries = 512;
 constexpr int kDefaultProbeSteps = 48;
 constexpr int kDefaultBigGroup = 32;
 constexpr int kMaxHaplotypes = 65000;
-constexpr int kDefaultSweepWarmup = 2048;
+constexpr int kDefaultSweepWarmup = 1536;
 constexpr int kDefaultSplitTile = 32;
 constexpr size_t kSweepSlotBudget = (size_t)24 << 30;  // bytes of sweep slots per scan
 constexpr size_t kMaxSmemPerCta = 227 * 1024;

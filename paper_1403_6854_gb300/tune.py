@@ -26,9 +26,9 @@ SWEEP_MAX_N = 16383
 SWEEP_CANDIDATES: List[Dict] = [
     dict(schedule=1, warps_per_cta=4),          # per-step in-order, for short chromosomes
     dict(schedule=3),
+    dict(schedule=3, sweep_warmup=2048),        # longer histories: fewer walks handed to
+    dict(schedule=3, sweep_warmup=4096),        # the per-step second pass
     dict(schedule=3, sweep_threads=512),
-    dict(schedule=3, sweep_threads=256, sweep_warmup=4096),
-    dict(schedule=3, sweep_threads=512, sweep_warmup=1024),
 ]
 
 DEFAULT_CANDIDATES: List[Dict] = [
