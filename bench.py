@@ -215,6 +215,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--ref-budget", type=float, default=15.0)
+    ap.add_argument("--complexity", action="store_true",
+                    help="sample-size and SNP-density sweeps of both exact forms, with log-log slopes")
     ap.add_argument("--tables", action="store_true",
                     help="instead of the main line: the paper's runtime-table workloads "
                          "(stand-ins) timed on the GPU and, on a bounded sample, the oracle")
@@ -229,6 +231,9 @@ def main():
         return
     if args.tables:
         run_tables(args)
+        return
+    if args.complexity:
+        run_complexity(args)
         return
 
     import torch
@@ -474,6 +479,65 @@ def run_tables(args):
                       "100 founders on 4 Mbp; chr22-shaped configs for CEU22 / CEUYRI22)",
                       "note": "the paper's times are on its 12-core Xeon and are context only"}),
           flush=True)
+
+
+def loglog_slope(x, y) -> float:
+    """Least-squares slope of log y against log x."""
+    lx, ly = np.log(np.asarray(x, dtype=np.float64)), np.log(np.asarray(y, dtype=np.float64))
+    return float(np.polyfit(lx, ly, 1)[0])
+
+
+COMPLEXITY_N = (250, 500, 1000, 2000, 5000)          # at 5,000 SNPs / Mb
+COMPLEXITY_D = (1250, 2500, 5000, 10000, 20000)      # SNPs / Mb, at n = 1,000
+
+
+def run_complexity(args):
+    """One JSON line: GPU scan time of both exact forms (per-step partition
+    refinement, sorted sweep) and the walk steps over a sample-size sweep and
+    a SNP-density sweep on a 20 Mb neutral region, with log-log slopes (the
+    paper reports O(N D^2) for its per-step algorithm)."""
+    import torch
+    import synth
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1403_6854_gb300 as sg
+    shapes = [("per_step", sg.make_launch(sg.SCHED_IN_ORDER)), ("sorted_sweep", sg.make_launch(sg.SCHED_SWEEP))]
+
+    def point(n, dens):
+        sp = synth.complexity_spec(n, dens)
+        d = synth.generate(sp)
+        hap, pos, gmap = sg.to_device(d.rows, d.pos, d.gmap)
+        row = {"n": n, "snps_per_mb": dens, "m": sp.m}
+        for name, L in shapes:
+            o = sg.selscan_ihs(hap, n, pos, gmap, launch=L)
+            torch.cuda.synchronize()
+            best = 1e30
+            for _ in range(5):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                o = sg.selscan_ihs(hap, n, pos, gmap, launch=L, workspace=o["_workspace"], out=o)
+                b.record()
+                torch.cuda.synchronize()
+                best = min(best, a.elapsed_time(b))
+            row[name + "_ms"] = best
+        st = o["status"].cpu().numpy()
+        walked = st != sg.LOCUS_MAF_FILTERED
+        row["core_loci"] = int(walked.sum())
+        row["walk_steps"] = int(o["stop"].cpu().numpy()[walked].astype(np.int64).sum())
+        del o, hap, pos, gmap
+        return row
+
+    n_pts = [point(n, 5000) for n in COMPLEXITY_N]
+    d_pts = [point(1000, dd) for dd in COMPLEXITY_D]
+    fits = {}
+    for key, pts, xk in (("vs_n", n_pts, "n"), ("vs_density", d_pts, "snps_per_mb")):
+        xs = [p[xk] for p in pts]
+        fits[key] = {f: loglog_slope(xs, [p[f] for p in pts])
+                     for f in ("per_step_ms", "sorted_sweep_ms", "walk_steps", "core_loci")}
+    print(json.dumps({"complexity": {"n_sweep": n_pts, "density_sweep": d_pts, "loglog_slopes": fits},
+                      "data": "seeded neutral mosaics (100 founders, 20 Mbp, 1 cM/Mb)",
+                      "note": "the paper reports O(N D^2) for selscan (N haploid samples, D SNP "
+                              "density); slopes are d log(y) / d log(x)"}), flush=True)
 
 
 def run_extras(sg, torch, synth, d, hap, pos, gmap, n, ws):

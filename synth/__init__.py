@@ -234,6 +234,17 @@ def spec(name: str, seed: int = 0) -> ScanSpec:
     raise KeyError(name)
 
 
+def complexity_spec(n: int, snps_per_mb: int, len_bp: int = 20_000_000, seed: int = 0) -> ScanSpec:
+    """Neutral iHS region for the complexity sweeps over sample size and SNP
+    density: a 100-founder mosaic on ``len_bp`` with a 1 cM/Mb map.  The
+    per-marker allele noise is scaled by 5,000 / density so that the noise per
+    Mb, and with it the physical length of a walk, does not depend on the
+    density (a walk then spans a number of markers proportional to it)."""
+    m = int(round(snps_per_mb * len_bp / 1e6))
+    pop = PopSpec(n, 100, flip_prob=FLIP_PROB * 5000.0 / snps_per_mb)
+    return ScanSpec(f"cplx_n{n}_d{snps_per_mb}", "ihs", m, len_bp, seed, [pop])
+
+
 # name: (mode, n or n_A, n_B, SNPs) of the data sets of the paper's runtime tables
 TABLE_SHAPES = {
     "IHS250": ("ihs", 250, 0, 9_625), "IHS500": ("ihs", 500, 0, 10_646),

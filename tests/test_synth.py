@@ -1,5 +1,6 @@
 """Seeded input generator: determinism, layout and the planted structure."""
 import numpy as np
+import pytest
 
 import synth
 
@@ -57,3 +58,24 @@ def test_served_requests_in_range():
         for p in s.pops:
             assert 100 <= p.n <= 5000
         assert s.mode in ("ihs", "xpehh")
+
+
+def test_complexity_spec_scales_noise_with_density():
+    a, b = synth.complexity_spec(1000, 2500), synth.complexity_spec(1000, 10000)
+    assert (a.m, b.m) == (50_000, 200_000) and a.len_bp == b.len_bp == 20_000_000
+    # allele noise per Mb is the same at both densities
+    assert a.pops[0].flip_prob * 2500 == pytest.approx(b.pops[0].flip_prob * 10000)
+    d = synth.generate(synth.complexity_spec(64, 100, len_bp=1_000_000))
+    assert d.rows.shape == (100, 1) and np.all(np.diff(d.pos) > 0)
+
+
+def test_loglog_slope():
+    import importlib.util
+    import os
+    spec = importlib.util.spec_from_file_location(
+        "bench_mod", os.path.join(os.path.dirname(os.path.dirname(__file__)), "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    x = [250, 500, 1000, 2000]
+    assert bench.loglog_slope(x, [7.0 * v ** 2 for v in x]) == pytest.approx(2.0)
+    assert bench.loglog_slope(x, [3.0 for _ in x]) == pytest.approx(0.0, abs=1e-12)
