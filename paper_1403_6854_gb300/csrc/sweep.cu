@@ -445,7 +445,6 @@ __device__ inline SplitSmem split_smem(unsigned char *base, int n, int xpehh)
     return s;
 }
 
-__device__ __forceinline__ unsigned long long c2(unsigned long long k) { return k * (k - 1ull) / 2ull; }
 __device__ __forceinline__ int c2i(unsigned k) { return (int)(k * (k - 1u) / 2u); }
 
 // last set position < b in O (| N)
@@ -599,8 +598,11 @@ __device__ const unsigned short *build_window(const Tile &tile, const SplitSmem 
 }
 
 
+// Pair counts fit 32 bits (C(16383, 2) < 2^32); the digest and the cutoff
+// product are 64-bit.
 struct ClassWalk {
-    unsigned long long D, S, prev, dig, numD;   // numD = cut_num * D
+    unsigned D, S, prev;
+    unsigned long long dig, numD;   // numD = cut_num * D
     double acc;
     int status, stop;
     bool active;
@@ -771,23 +773,24 @@ __global__ void __launch_bounds__(kSplitWarps * 32, SPLIT_MIN_CTAS) split_walk_k
         // ---- step 0 (the core marker splits the sample into its allele classes)
         constexpr int NWK = NPOP == 2 ? 1 : 2;    // walks handled by this warp
         ClassWalk cw[NWK];
-        unsigned long long SA = 0, SB = 0, pA = 0, pB = 0, dA = 0, dB = 0, DA = 0, DB = 0;
+        unsigned SA = 0, SB = 0, pA = 0, pB = 0, DA = 0, DB = 0;
+        unsigned long long dA = 0, dB = 0;
         double accB = 0.0;
         if (NPOP == 2) {
             const unsigned nA = (unsigned)w.a.nA, nB = (unsigned)w.a.nB;
             const unsigned a0 = count_a(s, n0), a1 = nA - a0;
             const unsigned b0 = (unsigned)n0 - a0, b1 = nB - b0;
-            SA = c2(a0) + c2(a1);
-            SB = c2(b0) + c2(b1);
-            DA = c2(nA);
-            DB = c2(nB);
-            cw[0].D = c2((unsigned long long)n);
-            cw[0].S = c2((unsigned long long)n0) + c2((unsigned long long)(n - n0));
+            SA = (unsigned)(c2i(a0) + c2i(a1));
+            SB = (unsigned)(c2i(b0) + c2i(b1));
+            DA = (unsigned)c2i(nA);
+            DB = (unsigned)c2i(nB);
+            cw[0].D = (unsigned)c2i((unsigned)n);
+            cw[0].S = (unsigned)(c2i((unsigned)n0) + c2i((unsigned)(n - n0)));
             pA = SA; pB = SB;
             dA = SA; dB = SB;
         } else {
-            cw[0].D = c2((unsigned long long)n0);              // allele 0: positions [0, n0)
-            cw[1].D = c2((unsigned long long)(n - n0));        // allele 1: positions [n0, n)
+            cw[0].D = (unsigned)c2i((unsigned)n0);             // allele 0: positions [0, n0)
+            cw[1].D = (unsigned)c2i((unsigned)(n - n0));       // allele 1: positions [n0, n)
             cw[0].S = cw[0].D;
             cw[1].S = cw[1].D;
         }
@@ -799,8 +802,8 @@ __global__ void __launch_bounds__(kSplitWarps * 32, SPLIT_MIN_CTAS) split_walk_k
             cw[q].dig = cw[q].S;
             cw[q].acc = 0.0;
             cw[q].stop = 0;
-            cw[q].status = cw[q].D == 0ull ? WALK_UNDEFINED : WALK_OK;
-            cw[q].active = cw[q].D != 0ull;
+            cw[q].status = cw[q].D == 0u ? WALK_UNDEFINED : WALK_OK;
+            cw[q].active = cw[q].D != 0u;
             any |= cw[q].active;
         }
 
@@ -825,7 +828,7 @@ __global__ void __launch_bounds__(kSplitWarps * 32, SPLIT_MIN_CTAS) split_walk_k
             }
         }
         int fin = WALK_OK;                           // how the still-active walks end
-        long long i = 1;
+        int i = 1;                              // walks stay below 2^31 steps (a chunk history)
         for (; any; ++i) {
             if (((i - 1) & (G - 1)) == 0) {       // gaps and map steps of the next G steps
                 const long long xl = k + step * (i + lane), xp = xl - step;
@@ -848,7 +851,7 @@ __global__ void __launch_bounds__(kSplitWarps * 32, SPLIT_MIN_CTAS) split_walk_k
             }
             const double g = tile.shfl(gq, (int)((i - 1) & (G - 1)));
             if (g < 0.0) { fin = g == -1.0 ? WALK_EDGE : WALK_GAP; break; }
-            if (i > (long long)hz) { fin = WALK_UNFINISHED; break; }
+            if (i > hz) { fin = WALK_UNFINISHED; break; }
             if (i >= lo + wlen) {
                 lo += wlen;
                 wlen = 64;
@@ -888,15 +891,15 @@ __global__ void __launch_bounds__(kSplitWarps * 32, SPLIT_MIN_CTAS) split_walk_k
                 d1 = cg::reduce(tile, d1, cg::plus<int>());
                 if (NPOP == 2) d2 = cg::reduce(tile, d2, cg::plus<int>());
             }
-            const unsigned long long ii = (unsigned long long)(i + 1);
+            const unsigned ii = (unsigned)(i + 1);
             if (NPOP == 2) {
-                SA = (unsigned long long)((long long)SA + d0);
-                SB = (unsigned long long)((long long)SB + d1);
+                SA += (unsigned)d0;                  // the decrements are negative: S stays >= 0
+                SB += (unsigned)d1;
                 ClassWalk &q = cw[0];
-                q.S = (unsigned long long)((long long)q.S + d2);
-                dA += ii * SA;
-                dB += ii * SB;
-                q.dig += ii * q.S;
+                q.S += (unsigned)d2;
+                dA += (unsigned long long)ii * SA;
+                dB += (unsigned long long)ii * SB;
+                q.dig += (unsigned long long)ii * q.S;
                 const bool stop = (unsigned long long)w.a.cut_den * q.S < q.numD;
                 if (stop && !w.a.crossing) { q.stop = (int)i; q.active = false; }
                 else {
@@ -913,8 +916,8 @@ __global__ void __launch_bounds__(kSplitWarps * 32, SPLIT_MIN_CTAS) split_walk_k
                 for (int c_ = 0; c_ < 2; ++c_) {
                     ClassWalk &q = cw[c_];
                     if (!q.active) continue;
-                    q.S = (unsigned long long)((long long)q.S + (c_ ? d1 : d0));
-                    q.dig += ii * q.S;
+                    q.S += (unsigned)(c_ ? d1 : d0);
+                    q.dig += (unsigned long long)ii * q.S;
                     const bool stop = (unsigned long long)w.a.cut_den * q.S < q.numD;
                     if (stop && !w.a.crossing) { q.stop = (int)i; q.active = false; continue; }
                     if (lane == 0) q.acc += (double)(q.prev + q.S) * g;
