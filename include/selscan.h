@@ -129,7 +129,8 @@ typedef struct {
                                   1..8192 (0 = the whole chunk, capped so that the slot
                                   buffer stays near 24 GiB); sizes the slot buffer */
     int32_t sweep_threads;     /* sweep schedule: threads per sorting CTA, 256 or 512
-                                  (0 = 256 up to 6144 haplotypes, else 512) */
+                                  (0 = 256 up to 6144 haplotypes, else 512); samples above
+                                  8192 haplotypes always take 512 */
     int32_t sweep_split_tile;  /* sweep schedule: lanes per split walk, 32 or 16 (two walks
                                   per warp) (0 = default) */
 } selscan_launch;

@@ -68,7 +68,8 @@ SweepPlan make_sweep_plan(int n_total, long long m, int mode, const selscan_laun
     // 256-thread CTAs (3 per SM) up to 24 elements per thread, else 512 (2 per SM)
     const int want = L ? L->sweep_threads : 0;
     w.threads = (want == 256 || want == 512) ? want : (n_total <= 256 * 24 ? 256 : 512);
-    if (w.threads == 256 && n_total > 256 * 64) w.threads = 512;
+    // a thread's allele bits live in one 32-bit word: at most 32 elements per thread
+    if (w.threads == 256 && n_total > 256 * 32) w.threads = 512;
     // chunks: the resident sweep CTAs split over both directions, each chunk
     // at least as long as its warm-up
     const long long per = w.L > 256 ? w.L : 256;

@@ -46,7 +46,7 @@ constexpr int kSplitListSmem = 1024;        // window list entries a walking war
 __host__ __device__ inline int sweep_e(int n, int T)
 {
     int e = (n + T - 1) / T;
-    return (e + 1) & ~1;                    // even: elements are read in pairs
+    return (e + 3) & ~3;                    // a multiple of 4: elements are read 4 at a time
 }
 __host__ __device__ inline int sweep_npad(int n, int T) { return sweep_e(n, T) * T; }
 __host__ __device__ inline int split_nw(int n) { return (n + 32) >> 5; }   // bits 0..n
@@ -207,12 +207,15 @@ __global__ void __launch_bounds__(T, T == 512 ? 2 : 3) sweep_kernel(SweepArgs w)
         // its prefix tail after placement.
         unsigned vmask = 0u, allw = 0xFFFFFFFFu, mn01 = 0xFFFFFFFFu;
 #pragma unroll
-        for (int e = 0; e < EMAX; e += 2) {
+        for (int e = 0; e < EMAX; e += 4) {
             if (e < E) {
-                const uint2 q = *(const uint2 *)(Pc + base + e);
+                // 16-byte loads: a thread's segment starts at 16 E bytes, and
+                // eight lanes at that stride cover distinct banks
+                const uint4 q = *(const uint4 *)(Pc + base + e);
+                const unsigned q4[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const unsigned pv = h ? q.y : q.x;
+                for (int h = 0; h < 4; ++h) {
+                    const unsigned pv = q4[h];
                     const unsigned wd = row[(pv & 0xFFFFu) >> 5];
                     const unsigned v = __funnelshift_r(wd, wd, pv) & 1u;   // bit pv % 32
                     vmask |= v << (e + h);
@@ -999,7 +1002,7 @@ cudaError_t launch_sweep_path(const SweepArgs &w0, cudaStream_t s)
     void (*sweep)(SweepArgs);
     if (w.threads == 256)
         sweep = E <= 8 ? sweep_kernel<256, 8> : E <= 16 ? sweep_kernel<256, 16>
-              : E <= 24 ? sweep_kernel<256, 24> : sweep_kernel<256, 64>;
+              : E <= 24 ? sweep_kernel<256, 24> : sweep_kernel<256, 32>;
     else
         sweep = E <= 4 ? sweep_kernel<512, 4> : E <= 8 ? sweep_kernel<512, 8>
               : E <= 16 ? sweep_kernel<512, 16> : E <= 24 ? sweep_kernel<512, 24>

@@ -141,10 +141,11 @@ def test_identical_haplotypes_and_long_walks(sg):
         assert_ihs_equal(run_ihs(sg, rows, n, pos, gmap, launch=sweep(sg, **kw)), ref)
 
 
-@pytest.mark.parametrize("n,threads", [(6000, 256), (6000, 512), (9000, 0)])
+@pytest.mark.parametrize("n,threads", [(6000, 256), (6000, 512), (9000, 0), (9000, 256), (13000, 0)])
 def test_elements_per_thread(sg, n, threads):
-    """Samples near the register-cached limit of each CTA width, and one that
-    re-reads its elements from shared memory."""
+    """Samples near the register-cached limit of each CTA width, ones that
+    re-read their elements from shared memory, and a 256-thread request above
+    32 elements per thread (taken by 512 threads)."""
     m = 90
     hap, pos, gmap = synth.tiny_mosaic(n, m, n + threads, founders=5, switch=0.05, flip=0.003)
     rows = synth.pack(hap)
