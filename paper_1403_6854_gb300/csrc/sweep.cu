@@ -417,13 +417,13 @@ __global__ void __launch_bounds__(T, T == 512 ? 2 : 3) sweep_kernel(SweepArgs w)
 // ---- the split walk ----------------------------------------------------------
 namespace {
 
-// Per-warp shared memory: run starts before this step (O) and set at this
-// step (N) as bitmaps over positions 0..n, one summary bit per non-zero
-// word (SO, SN), step counts / offsets of the current 64-step window, and
+// Per-warp shared memory: run starts before this step (O) and all run starts
+// including this step's (A) as bitmaps over positions 0..n, one summary bit
+// per non-zero word (SO, SA), step counts / offsets of the current window, and
 // for XPEHH the population-A flags of the sorted positions with their
 // per-word prefix counts.
 struct SplitSmem {
-    unsigned *O, *N, *SO, *SN;
+    unsigned *O, *A, *SO, *SA;
     unsigned *cnt, *off;
     unsigned short *lst;                  // the current window's list, when it fits
     unsigned *isA, *PA;
@@ -437,9 +437,9 @@ __device__ inline SplitSmem split_smem(unsigned char *base, int n, int xpehh)
     s.ns = (s.nw + 31) >> 5;
     unsigned *p = (unsigned *)base;
     s.O = p; p += s.nw;
-    s.N = p; p += s.nw;
+    s.A = p; p += s.nw;
     s.SO = p; p += s.ns;
-    s.SN = p; p += s.ns;
+    s.SA = p; p += s.ns;
     s.cnt = p; p += 64;
     s.off = p; p += 65;
     s.isA = xpehh ? p : nullptr;
@@ -450,44 +450,40 @@ __device__ inline SplitSmem split_smem(unsigned char *base, int n, int xpehh)
 
 __device__ __forceinline__ int c2i(unsigned k) { return (int)(k * (k - 1u) / 2u); }
 
-// last set position < b in O (| N)
-template <bool WITH_N>
+// last set position < b among all run starts (ALL: A) or the old ones (O)
+template <bool ALL>
 __device__ __forceinline__ int prev_set(const SplitSmem &s, int b)
 {
+    const unsigned *B = ALL ? s.A : s.O, *S = ALL ? s.SA : s.SO;
     const int wd = b >> 5;
-    unsigned bits = s.O[wd] | (WITH_N ? s.N[wd] : 0u);
-    bits &= (1u << (b & 31)) - 1u;
+    const unsigned bits = B[wd] & ((1u << (b & 31)) - 1u);
     if (bits) return (wd << 5) + 31 - __clz(bits);
     for (int sw = wd - 1; sw >= 0;) {
         const int q = sw >> 5;
-        unsigned sb = s.SO[q] | (WITH_N ? s.SN[q] : 0u);
-        sb &= 0xFFFFFFFFu >> (31 - (sw & 31));
+        const unsigned sb = S[q] & (0xFFFFFFFFu >> (31 - (sw & 31)));
         if (sb) {
             const int ww = (q << 5) + 31 - __clz(sb);
-            const unsigned word = s.O[ww] | (WITH_N ? s.N[ww] : 0u);
-            return (ww << 5) + 31 - __clz(word);
+            return (ww << 5) + 31 - __clz(B[ww]);
         }
         sw = (q << 5) - 1;
     }
     return 0;                         // position 0 is always set
 }
 
-// first set position > b in O (| N)
-template <bool WITH_N>
+// first set position > b among all run starts (ALL: A) or the old ones (O)
+template <bool ALL>
 __device__ __forceinline__ int next_set(const SplitSmem &s, int b, int n)
 {
+    const unsigned *B = ALL ? s.A : s.O, *S = ALL ? s.SA : s.SO;
     const int wd = b >> 5;
-    unsigned bits = s.O[wd] | (WITH_N ? s.N[wd] : 0u);
-    bits &= ~((2u << (b & 31)) - 1u);
+    const unsigned bits = B[wd] & ~((2u << (b & 31)) - 1u);
     if (bits) return (wd << 5) + __ffs(bits) - 1;
     for (int sw = wd + 1; sw < s.nw;) {
         const int q = sw >> 5;
-        unsigned sb = s.SO[q] | (WITH_N ? s.SN[q] : 0u);
-        sb &= 0xFFFFFFFFu << (sw & 31);
+        const unsigned sb = S[q] & (0xFFFFFFFFu << (sw & 31));
         if (sb) {
             const int ww = (q << 5) + __ffs(sb) - 1;
-            const unsigned word = s.O[ww] | (WITH_N ? s.N[ww] : 0u);
-            return (ww << 5) + __ffs(word) - 1;
+            return (ww << 5) + __ffs(B[ww]) - 1;
         }
         sw = (q + 1) << 5;
     }
@@ -656,8 +652,8 @@ __device__ __noinline__ void split_many(const Tile &tile, const SplitSmem &s,
     const int lane = tile.thread_rank();
     for (unsigned j = j0 + lane; j < j1; j += G) {
         const int b = list[j];
-        atomicOr(s.N + (b >> 5), 1u << (b & 31));
-        atomicOr(s.SN + (b >> 10), 1u << ((b >> 5) & 31));
+        atomicOr(s.A + (b >> 5), 1u << (b & 31));
+        atomicOr(s.SA + (b >> 10), 1u << ((b >> 5) & 31));
     }
     tile.sync();
     for (unsigned j = j0 + lane; j < j1; j += G)
@@ -668,13 +664,6 @@ __device__ __noinline__ void split_many(const Tile &tile, const SplitSmem &s,
         atomicOr(s.O + (b >> 5), 1u << (b & 31));
         atomicOr(s.SO + (b >> 10), 1u << ((b >> 5) & 31));
     }
-    tile.sync();
-    for (unsigned j = j0 + lane; j < j1; j += G) {
-        const int b = list[j];
-        s.N[b >> 5] = 0u;
-        s.SN[b >> 10] = 0u;
-    }
-    tile.sync();
 }
 
 }  // namespace
@@ -746,8 +735,8 @@ __global__ void __launch_bounds__(kSplitWarps * 32, SPLIT_MIN_CTAS) split_walk_k
         const int w1 = ((const int *)slot)[2];
         const unsigned *M32 = (const unsigned *)(slot + 16);
 
-        for (int q = lane; q < s.nw; q += G) { s.O[q] = 0u; s.N[q] = 0u; }
-        for (int q = lane; q < s.ns; q += G) { s.SO[q] = 0u; s.SN[q] = 0u; }
+        for (int q = lane; q < s.nw; q += G) { s.O[q] = 0u; s.A[q] = 0u; }
+        for (int q = lane; q < s.ns; q += G) { s.SO[q] = 0u; s.SA[q] = 0u; }
         if (NPOP == 2) {
             const unsigned *isA = (const unsigned *)(slot + slot_isa_at(n));
             unsigned carry = 0u;
@@ -770,6 +759,8 @@ __global__ void __launch_bounds__(kSplitWarps * 32, SPLIT_MIN_CTAS) split_walk_k
             const int mk = lane == 0 ? 0 : (lane == 1 ? n0 : n);
             atomicOr(s.O + (mk >> 5), 1u << (mk & 31));
             atomicOr(s.SO + (mk >> 10), 1u << ((mk >> 5) & 31));
+            atomicOr(s.A + (mk >> 5), 1u << (mk & 31));
+            atomicOr(s.SA + (mk >> 10), 1u << ((mk >> 5) & 31));
         }
         tile.sync();
 
@@ -873,19 +864,18 @@ __global__ void __launch_bounds__(kSplitWarps * 32, SPLIT_MIN_CTAS) split_walk_k
                     const unsigned bw = 1u << (b & 31), sw = 1u << ((b >> 5) & 31);
                     if (tile.ballot(has) != 0u) {
                     if (has) {
-                        atomicOr(s.N + (b >> 5), bw);
-                        atomicOr(s.SN + (b >> 10), sw);
+                        atomicOr(s.A + (b >> 5), bw);
+                        atomicOr(s.SA + (b >> 10), sw);
                     }
                     tile.sync();
                     if (has) split_terms<NPOP>(s, b, n, n0, d0, d1, d2);
                     tile.sync();
+                    // this step's starts become old ones; the next step reads O
+                    // only after its own sync
                     if (has) {
                         atomicOr(s.O + (b >> 5), bw);
                         atomicOr(s.SO + (b >> 10), sw);
-                        s.N[b >> 5] = 0u;
-                        s.SN[b >> 10] = 0u;
                     }
-                    tile.sync();
                     }
                 } else {
                     split_many<NPOP, G>(tile, s, cl, j0, j1, n, n0, d0, d1, d2);
