@@ -683,7 +683,7 @@ size_t split_scratch_per_warp(int n) { return (((size_t)n * 10) + 255) & ~(size_
 // walks two cores at once) takes slots of this stage (both directions) from a
 // counter and walks the cores in them.
 #ifndef SPLIT_MIN_CTAS
-#define SPLIT_MIN_CTAS 3
+#define SPLIT_MIN_CTAS 4
 #endif
 template <int NPOP, int G>
 __global__ void __launch_bounds__(kSplitWarps * 32, SPLIT_MIN_CTAS) split_walk_kernel(SweepArgs w)
