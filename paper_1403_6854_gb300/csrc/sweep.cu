@@ -19,13 +19,15 @@
 //    marker by marker (a stable partition by allele; the new run length of a
 //    neighbour pair is 1 + the minimum over the old pairs it spans).  At every
 //    core of the stage it writes M, the class boundary n0 (and, for XPEHH, the
-//    population of each sorted position) to a slot.  A chunk starts `warmup`
+//    population of each sorted position) to a slot, with the boundaries of
+//    the first walk steps already grouped by step.  A chunk starts `warmup`
 //    markers before its first core, so its sort is exact for walks that stay
 //    within that history.
 //  * split_walk_kernel: one warp per slot runs the walk steps of that core
 //    (both allele classes of iHS, or the pooled XPEHH walk): gaps, the map,
 //    the cutoff and the trapezoid exactly as the per-step walk does, with S(i)
-//    from the boundaries of step i.  A walk that would step beyond its
+//    from the boundaries of step i (from the slot's first window, then from
+//    64-step windows it finds in M).  A walk that would step beyond its
 //    chunk's history is handed to the per-step walk kernel (second pass).
 #include <cooperative_groups.h>
 #include <cooperative_groups/reduce.h>
@@ -535,9 +537,9 @@ __device__ const unsigned short *place_window(const Tile &tile, const SplitSmem 
 // Group the boundaries t with lo <= M[t] < lo + 64 by step: one pass over M
 // (8 values per 16-byte load, four loads in flight per lane) marks the values
 // in the window with two integer operations per 16-bit half; only the marked
-// ones are ranked inside their step and staged, then placed by step.  Done by one tile of G lanes.  Window starts
-// stay below 65,001 (run lengths are at most 65,000), so the all-ones fill
-// past the slot's end is never marked.
+// ones are ranked inside their step and staged, then placed by step.  Done by
+// one tile of G lanes.  Window starts stay below 65,001 (run lengths are at
+// most 65,000), so the all-ones fill past the slot's end is never marked.
 template <int G, typename Tile>
 __device__ const unsigned short *build_window(const Tile &tile, const SplitSmem &s, const unsigned *M32,
                                               int n, int lo, unsigned long long *stage,
