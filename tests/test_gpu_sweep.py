@@ -141,6 +141,28 @@ def test_identical_haplotypes_and_long_walks(sg):
         assert_ihs_equal(run_ihs(sg, rows, n, pos, gmap, launch=sweep(sg, **kw)), ref)
 
 
+def test_first_window_shorter_than_64_steps(sg):
+    """3,000 haplotypes, half i.i.d. and half near-copies of one sequence: the
+    i.i.d. half parts more than 1,024 neighbour pairs within the first dozen
+    steps, so the slot's first window stops short of 64 steps (each step at
+    most doubles the runs, so it still covers 9 or more), while the copies keep
+    one class's walks going for about a hundred steps through windows the
+    walker builds itself from the first window's end on."""
+    n, m = 3000, 300
+    rng = np.random.Generator(np.random.PCG64(77))
+    hap = np.empty((m, n), dtype=np.uint8)
+    hap[:, :1500] = rng.random((m, 1500)) < 0.5
+    base = (rng.random(m) < 0.5).astype(np.uint8)
+    hap[:, 1500:] = base[:, None] ^ (rng.random((m, 1500)) < 0.01)
+    _, pos, gmap = synth.tiny_mosaic(4, m, 78)
+    rows = synth.pack(hap)
+    cores = np.array([60, 150, 151, 240])
+    ref = oracle.ihs(rows, n, pos, gmap, cores=cores)
+    assert ref["stop"].max() > 64                         # walks outlive a 64-step window
+    for kw in (dict(), dict(sweep_warmup=40, sweep_stage_cores=7)):
+        assert_ihs_equal(run_ihs(sg, rows, n, pos, gmap, launch=sweep(sg, **kw)), ref, idx=cores)
+
+
 @pytest.mark.parametrize("n,threads", [(6000, 256), (6000, 512), (9000, 0), (9000, 256), (13000, 0)])
 def test_elements_per_thread(sg, n, threads):
     """Samples near the register-cached limit of each CTA width, ones that
