@@ -304,6 +304,13 @@ int selscan_normalize(const double *score, const int8_t *status, const int32_t *
 int selscan_pack(const uint8_t *hap01, int32_t n, int64_t m, int32_t hap_major,
                  uint64_t *rows, int64_t ld, void *stream);
 
+/* The schedule a default launch (NULL, or schedule SELSCAN_SCHED_DEFAULT)
+ * takes for a scan of n_total haplotypes (n_A + n_B for XPEHH) and m
+ * markers: SELSCAN_SCHED_SWEEP for m >= 32768 + 4 n_total and at most 16383
+ * haplotypes, else SELSCAN_SCHED_IN_ORDER; -1 for bad arguments (mode
+ * SELSCAN_MODE_IHS or SELSCAN_MODE_XPEHH).  Host only: no device work. */
+int32_t selscan_default_schedule(int32_t n_total, int64_t m, int32_t mode);
+
 /* Kernel launches one selscan_ihs / selscan_xpehh call makes with this
  * launch shape (mode SELSCAN_MODE_IHS or SELSCAN_MODE_XPEHH), or -1 for bad
  * arguments.  Host only: no device work. */

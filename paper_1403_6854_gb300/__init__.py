@@ -80,6 +80,7 @@ EXPORTS = ("selscan_default_params", "selscan_workspace_bytes", "selscan_ihs", "
            "selscan_ehh", "selscan_ehh_noalloc", "selscan_pack", "selscan_strerror",
            "selscan_batch_item_bytes", "selscan_batch_workspace_bytes", "selscan_batch_prepare",
            "selscan_batch_run", "selscan_batch_finalize", "selscan_launch_count",
+           "selscan_default_schedule",
            "selscan_normalize", "selscan_normalize_workspace_bytes", "selscan_read_tped")
 EHH_NOALLOC_MAX_N = 8192
 
@@ -143,6 +144,8 @@ def load_library():
                                       _P, _P, _P, _P, _P, ctypes.c_size_t, _P]
     lib.selscan_launch_count.restype = ctypes.c_int32
     lib.selscan_launch_count.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, _P]
+    lib.selscan_default_schedule.restype = ctypes.c_int32
+    lib.selscan_default_schedule.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_int32]
     lib.selscan_batch_finalize.restype = ctypes.c_int
     lib.selscan_batch_finalize.argtypes = [ctypes.POINTER(selscan_scan), _P]
     lib.selscan_strerror.restype = ctypes.c_char_p
@@ -236,6 +239,11 @@ def selscan_normalize(score: torch.Tensor, status: torch.Tensor, n1: torch.Tenso
         raise SelscanError(rc, "selscan_normalize")
     out["_workspace"] = ws
     return out
+
+
+def selscan_default_schedule(n_total: int, m: int, mode: int) -> int:
+    """Schedule a default launch takes for this scan shape (-1: bad arguments)."""
+    return int(load_library().selscan_default_schedule(n_total, m, mode))
 
 
 def selscan_launch_count(n_total: int, m: int, mode: int,

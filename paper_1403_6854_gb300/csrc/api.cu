@@ -22,6 +22,8 @@ constexpr int kMaxHaplotypes = 65000;
 constexpr int kDefaultSweepWarmup = 1536;
 constexpr int kDefaultSplitTile = 32;
 constexpr size_t kSweepSlotBudget = (size_t)24 << 30;  // bytes of sweep slots per scan
+constexpr long long kSweepMinMarkers = 32768;          // default sweep: m >= this +
+constexpr long long kSweepMinPerHaplotype = 4;         // this x n
 constexpr size_t kMaxSmemPerCta = 227 * 1024;
 
 struct SweepPlan {
@@ -104,15 +106,26 @@ SweepPlan make_sweep_plan(int n_total, long long m, int mode, const selscan_laun
     return w;
 }
 
+// The schedule of a default launch: the sorted sweep once the chromosome is
+// long enough for its chunks' sequential sorts (each about B + warm-up
+// markers, n elements per marker) to cost less than walking every step, the
+// in-order per-step schedule otherwise.  The crossover depends on the walk
+// lengths: on mosaics of n / 25 founders (long walks) about 7k markers at
+// n = 100, 12k at 1,000, 23k at 2,000 and 30k at 5,000; on a 22k-marker
+// chromosome with short walks the per-step walk is still 2-4x faster.  The
+// rule sits above both.
+int default_schedule(int mode, long long n_total, long long m)
+{
+    if (mode == SELSCAN_MODE_EHH || n_total < 2 || n_total > kSweepMaxN) return SELSCAN_SCHED_IN_ORDER;
+    return m >= kSweepMinMarkers + kSweepMinPerHaplotype * n_total ? SELSCAN_SCHED_SWEEP
+                                                                   : SELSCAN_SCHED_IN_ORDER;
+}
+
 Plan make_plan(int mode, long long ld, const selscan_launch *L, int n_total = 0, long long m = 0)
 {
     Plan p;
-    // default: the sorted sweep once the chromosome is long enough for its
-    // chunks' sequential sorts (each about B + warm-up markers) to cost less
-    // than walking every step; the in-order per-step schedule otherwise
-    p.schedule = (L && L->schedule != SELSCAN_SCHED_DEFAULT)
-                     ? L->schedule
-                     : (m >= 64ll * kDefaultSweepWarmup ? SELSCAN_SCHED_SWEEP : SELSCAN_SCHED_IN_ORDER);
+    p.schedule = (L && L->schedule != SELSCAN_SCHED_DEFAULT) ? L->schedule
+                                                              : default_schedule(mode, n_total, m);
     if (p.schedule < 0 || p.schedule > SELSCAN_SCHED_SWEEP) p.schedule = -1;
     memset(&p.sw, 0, sizeof(p.sw));
     if (p.schedule == SELSCAN_SCHED_SWEEP) {
@@ -359,6 +372,12 @@ size_t selscan_workspace_bytes(int32_t n_total, int64_t m, int32_t mode, const s
     const int nslots = mode == SELSCAN_MODE_EHH ? p.nslots : device_sms() * 64;
     return make_layout(n_total, m, mode, nslots,
                        p.schedule == SELSCAN_SCHED_SWEEP ? &p.sw : nullptr).total;
+}
+
+int32_t selscan_default_schedule(int32_t n_total, int64_t m, int32_t mode)
+{
+    if (n_total < 2 || m < 1 || (mode != SELSCAN_MODE_IHS && mode != SELSCAN_MODE_XPEHH)) return -1;
+    return default_schedule(mode, n_total, m);
 }
 
 int32_t selscan_launch_count(int32_t n_total, int64_t m, int32_t mode, const selscan_launch *launch)

@@ -168,8 +168,9 @@ class GpuExecutor:
     alternate between two streams so that one tick's tail overlaps the next
     tick's start; a scan is finalised after every tick that touched it.
 
-    Long requests (at least `whole_min_markers` markers and at most 16383
-    haplotypes) do not take ticks: each runs as one whole-scan call with the
+    Long requests (those a default launch sorts, `selscan_default_schedule`,
+    or with at least `whole_min_markers` markers when that is given, and at
+    most 16383 haplotypes) do not take ticks: each runs as one whole-scan call with the
     sorted-sweep schedule on one of `whole_streams` side streams, its results
     copied to pinned host memory behind it, so it completes asynchronously
     next to the ticks.  Its footprint includes the sweep's workspace (stages
@@ -177,13 +178,13 @@ class GpuExecutor:
 
     WHOLE_MAX_N = 16383
 
-    def __init__(self, device="cuda", whole_min_markers: int = 131072, whole_streams: int = 3,
+    def __init__(self, device="cuda", whole_min_markers: Optional[int] = None, whole_streams: int = 3,
                  whole_stage_cores: int = 256):
         import torch
         import paper_1403_6854_gb300 as sg
         self.torch, self.sg = torch, sg
         self.device = torch.device(device)
-        self.whole_min = int(whole_min_markers)
+        self.whole_min = None if whole_min_markers is None else int(whole_min_markers)
         self.whole_stage = int(whole_stage_cores)
         self.wstreams = [torch.cuda.Stream(self.device) for _ in range(max(1, whole_streams))]
         self.wk = 0
@@ -196,7 +197,12 @@ class GpuExecutor:
 
     # ------------------------------------------------------------ whole scans
     def is_whole(self, req: Request) -> bool:
-        return self.whole_min > 0 and req.m >= self.whole_min and req.n_total <= self.WHOLE_MAX_N
+        if req.n_total > self.WHOLE_MAX_N:
+            return False
+        if self.whole_min is None:
+            mode = self.sg.MODE_IHS if req.mode == "ihs" else self.sg.MODE_XPEHH
+            return self.sg.selscan_default_schedule(req.n_total, req.m, mode) == self.sg.SCHED_SWEEP
+        return self.whole_min > 0 and req.m >= self.whole_min
 
     def _whole_launch(self):
         return self.sg.make_launch(self.sg.SCHED_SWEEP, sweep_stage_cores=self.whole_stage)

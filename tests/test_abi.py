@@ -120,3 +120,20 @@ def test_batch_limits(sg):
                                  None) == sg.ERR_INVALID_ARG
     # a scan that fails its checks (all-zero struct) launches nothing
     assert lib.selscan_batch_prepare(scans, None) == sg.ERR_INVALID_ARG
+
+
+def test_default_schedule_rule(sg):
+    """A default launch sorts once m >= 32768 + 4 n (at most 16383 haplotypes);
+    host-only, so it runs without a GPU."""
+    I, X = sg.MODE_IHS, sg.MODE_XPEHH
+    assert sg.selscan_default_schedule(5000, 52768, I) == sg.SCHED_SWEEP
+    assert sg.selscan_default_schedule(5000, 52767, I) == sg.SCHED_IN_ORDER
+    assert sg.selscan_default_schedule(100, 33168, I) == sg.SCHED_SWEEP
+    assert sg.selscan_default_schedule(100, 33167, I) == sg.SCHED_IN_ORDER
+    assert sg.selscan_default_schedule(204, 22147, I) == sg.SCHED_IN_ORDER      # chr22-shaped
+    assert sg.selscan_default_schedule(414, 22147, X) == sg.SCHED_IN_ORDER
+    assert sg.selscan_default_schedule(2500 + 2500, 1_000_000, X) == sg.SCHED_SWEEP
+    assert sg.selscan_default_schedule(16383, 10_000_000, I) == sg.SCHED_SWEEP
+    assert sg.selscan_default_schedule(16384, 10_000_000, I) == sg.SCHED_IN_ORDER
+    for bad in ((1, 100000, I), (100, 0, I), (100, 100000, 7)):
+        assert sg.selscan_default_schedule(*bad) == -1

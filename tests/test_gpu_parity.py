@@ -58,16 +58,22 @@ def test_plain_all_cores(sg, plain):
     assert_ihs_equal(got, ref)
 
 
-def test_chr22_all_cores(sg, chr22):
-    got = run_ihs(sg, chr22.rows, 204, chr22.pos, chr22.gmap)
+@pytest.mark.parametrize("schedule", ["default", "sweep"])
+def test_chr22_all_cores(sg, chr22, schedule):
+    """The default launch and the sorted sweep (the per-step walk is covered
+    against the oracle by the default)."""
+    L = None if schedule == "default" else sg.make_launch(sg.SCHED_SWEEP)
+    got = run_ihs(sg, chr22.rows, 204, chr22.pos, chr22.gmap, launch=L)
     ref = oracle.ihs(chr22.rows, 204, chr22.pos, chr22.gmap)
     assert_ihs_equal(got, ref)
     # the planted gaps made both abort kinds appear
     assert (ref["status"] == oracle.ABORT_GAP).any() and (ref["status"] == oracle.ABORT_EDGE).any()
 
 
-def test_xpehh_all_cores(sg, xp):
-    got = run_xpehh(sg, xp.rows, 204, 210, xp.pos, xp.gmap)
+@pytest.mark.parametrize("schedule", ["default", "sweep"])
+def test_xpehh_all_cores(sg, xp, schedule):
+    L = None if schedule == "default" else sg.make_launch(sg.SCHED_SWEEP)
+    got = run_xpehh(sg, xp.rows, 204, 210, xp.pos, xp.gmap, launch=L)
     ref = oracle.xpehh(xp.rows, 204, 210, xp.pos, xp.gmap)
     assert_xpehh_equal(got, ref)
 
