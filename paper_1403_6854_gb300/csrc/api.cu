@@ -267,7 +267,7 @@ int run_scan(int mode, const uint64_t *hap, int64_t ld, int32_t nA, int32_t nB, 
     if (smem_per_warp(plan.cap_s, plan.tcap_s, plan.rowcap, plan.poscap) * (size_t)plan.wpc > kMaxSmemPerCta)
         return SELSCAN_ERR_UNSUPPORTED;
     const bool sweep = plan.schedule == SELSCAN_SCHED_SWEEP;
-    if (sweep && (sweep_smem_bytes(n_total, (nA + 63) / 64 + (nB + 63) / 64, plan.sw.threads) > kMaxSmemPerCta ||
+    if (sweep && (sweep_smem_bytes(n_total, (nA + 63) / 64 + (nB + 63) / 64, plan.sw.threads, plan.sw.R) > kMaxSmemPerCta ||
                   (size_t)plan.sw.split_bytes * (kSplitWarps * 32 / plan.sw.split_tile) > kMaxSmemPerCta))
         return SELSCAN_ERR_UNSUPPORTED;
     if (sweep && (plan.sw.slot_bytes & 15)) return SELSCAN_ERR_UNSUPPORTED;   // slots are read in 16-byte units

@@ -125,7 +125,7 @@ struct SweepArgs {
     unsigned long long *walk_head;   // slot counter of the current walk launch
 };
 
-size_t sweep_smem_bytes(int n, int W, int T);
+size_t sweep_smem_bytes(int n, int W, int T, int R);
 size_t sweep_slot_bytes(int n, int xpehh);
 size_t sweep_state_bytes(int n, int T);
 size_t split_smem_per_warp(int n, int xpehh);

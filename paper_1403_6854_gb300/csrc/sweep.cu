@@ -42,6 +42,7 @@ namespace selscan {
 namespace {
 
 constexpr unsigned kInf16 = 0xFFFFu;
+constexpr int kRowRing = 4;                 // rows in flight ahead of the sort (cp.async)
 constexpr int kSlotListCap = 1024;          // first-window boundaries kept per slot
 constexpr int kSplitListSmem = 1024;        // window list entries a walking warp keeps on chip
 
@@ -74,6 +75,17 @@ __device__ __forceinline__ void compose(unsigned lA, unsigned lB, unsigned &rA, 
 constexpr unsigned kId0 = 0xFFFFFFFFu;
 constexpr unsigned kId1 = 0x0000FFFFu;
 
+// Asynchronous global -> shared copies of 8 bytes (rows start on 8-byte
+// boundaries whatever their stride), in per-thread commit groups.
+__device__ __forceinline__ void cp_async8(void *smem_dst, const void *gsrc)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
 __device__ __forceinline__ unsigned bit_index(const SweepArgs &w, int h)
 {
     // position of haplotype h (pooled numbering, A first) in the row's bits
@@ -97,10 +109,11 @@ __host__ __device__ inline size_t slot_off_at(int n, int xpehh)
 __host__ __device__ inline size_t slot_list_at(int n, int xpehh) { return slot_off_at(n, xpehh) + 144; }
 }  // namespace
 
-size_t sweep_smem_bytes(int n, int W, int T)
+size_t sweep_smem_bytes(int n, int W, int T, int R)
 {
     const int W32 = ((2 * W) + 4) & ~3;
-    return (size_t)sweep_npad(n, T) * 4 * 2 + (size_t)W32 * 4 * 2 + T / 32 * 8 + 2 * 65 * 4;
+    return (size_t)sweep_npad(n, T) * 4 * 2 + (size_t)W32 * 4 * kRowRing + T / 32 * 8 + 2 * 65 * 4 +
+           (size_t)((R + 31) / 32) * 4;
 }
 
 size_t sweep_slot_bytes(int n, int xpehh)
@@ -134,10 +147,11 @@ __global__ void __launch_bounds__(T, T == 512 ? 2 : 3) sweep_kernel(SweepArgs w)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr int NW = T / 32;
     unsigned *P0 = (unsigned *)smem;             // buffer b at P0 + b * np
-    unsigned *R0 = P0 + 2 * np;                  // row buffer r at R0 + r * W32r
-    unsigned *wsum = R0 + 2 * W32r;
+    unsigned *R0 = P0 + 2 * np;                  // row ring: slot r at R0 + r * W32r
+    unsigned *wsum = R0 + kRowRing * W32r;
     unsigned *hcnt = wsum + 2 * NW;              // a core's first window: per-step counts,
     unsigned *hoff = hcnt + 65;                  // then cursors and (at [64]) W1
+    unsigned *cbits = hoff + 65;                 // the stage's cores that pass the filter
 
     const int dir = blockIdx.x / w.nch;          // 0: walks toward lower indices
     const int c = blockIdx.x % w.nch;
@@ -176,31 +190,46 @@ __global__ void __launch_bounds__(T, T == 512 ? 2 : 3) sweep_kernel(SweepArgs w)
     } else {
         for (int t = tid; t < np; t += T) P0[t] = st[t];
     }
-    const unsigned *hap32 = (const unsigned *)w.a.hap;
-    const long long ld32 = 2 * w.a.ld;
+    const unsigned long long *hap64 = (const unsigned long long *)w.a.hap;
+    const long long ld = w.a.ld;
+    const int W = w.a.W;
+    const long long nq = (xlast - xfirst) * step + 1;   // markers of this launch
+    // row q (in sweep order) goes to ring slot q % kRowRing, kRowRing - 1 rows ahead
+    auto fetch_row = [&](long long q) {
+        if (q < nq) {
+            unsigned *dst = R0 + (q & (kRowRing - 1)) * W32r;
+            const unsigned long long *src = hap64 + (xfirst + q * step) * ld;
+            for (int t = tid; t < W; t += T) cp_async8(dst + 2 * t, src + t);
+        }
+        cp_async_commit();
+    };
+    for (int q = 0; q < kRowRing; ++q) fetch_row(q);
     for (int t = tid; t < 64; t += T) hcnt[t] = 0u;
-    for (int t = tid; t < W32; t += T) R0[t] = hap32[xfirst * ld32 + t];
-    if (tid < W32r - W32) {
-        R0[W32 + tid] = 0xFFFFFFFFu;
-        R0[W32r + W32 + tid] = 0xFFFFFFFFu;
+    for (int r = 0; r < kRowRing; ++r)          // the padding elements' all-ones word
+        if (tid < W32r - W32) R0[r * W32r + W32 + tid] = 0xFFFFFFFFu;
+    {
+        const int nrc = (int)(khi - klo);
+        for (int r0 = 0; r0 < nrc; r0 += T) {
+            const int r = r0 + tid;
+            const bool v = r < nrc && w.sk.core_status[klo + r] != (int8_t)SELSCAN_LOCUS_MAF_FILTERED;
+            const unsigned bits = __ballot_sync(FULLMASK, v);
+            if (lane == 0 && r0 + warp * 32 < nrc) cbits[(r0 >> 5) + warp] = bits;
+        }
     }
+    cp_async_wait<kRowRing - 1>();               // row 0
     __syncthreads();
 
-    int cur = 0, rb = 0;
+    int cur = 0;
     const int base = tid * E;
     unsigned val[CACHE ? EMAX : 1];
-    for (long long x = xfirst;; x += step) {
+    long long q = 0;
+    for (long long x = xfirst;; x += step, ++q) {
         const bool more = x != xlast;
-        unsigned rnext[3];                       // the next row, loaded while this one is sorted
-#pragma unroll
-        for (int j = 0; j < 3; ++j)
-            rnext[j] = more && tid + j * T < W32 ? __ldg(hap32 + (x + step) * ld32 + tid + j * T) : 0u;
         const bool is_core = x >= klo && x < khi;
-        int cst = 0;
-        if (is_core) cst = w.sk.core_status[x];
+        const bool wr = is_core && ((cbits[(x - klo) >> 5] >> ((x - klo) & 31)) & 1u);
 
         const unsigned *Pc = P0 + cur * np;
-        const unsigned *row = R0 + rb * W32r;
+        const unsigned *row = R0 + (q & (kRowRing - 1)) * W32r;
         // pass 1: alleles, the new run lengths as far as this segment decides
         // them, and the segment summary.  Both tails live in one word (allele
         // 0 low, 1 high).  Run lengths stay at most 65,000 (a chunk plus its
@@ -244,6 +273,7 @@ __global__ void __launch_bounds__(T, T == 512 ? 2 : 3) sweep_kernel(SweepArgs w)
         if (lane == 0) { x0 = kId0; x1 = kId1; }
         if (lane == 31) { wsum[2 * warp] = p0; wsum[2 * warp + 1] = p1; }
         __syncthreads();
+        fetch_row(q + kRowRing);                  // every thread is done with this row's slot
         // every warp scans the warp totals: its own prefix and the block total
         unsigned q0 = lane < NW ? wsum[2 * lane] : kId0;
         unsigned q1 = lane < NW ? wsum[2 * lane + 1] : kId1;
@@ -316,15 +346,12 @@ __global__ void __launch_bounds__(T, T == 512 ? 2 : 3) sweep_kernel(SweepArgs w)
                 Pn[os] = (u & 0xFFFFu) | (out << 16);
             }
         }
-#pragma unroll
-        for (int j = 0; j < 3; ++j)
-            if (more && tid + j * T < W32) R0[(rb ^ 1) * W32r + tid + j * T] = rnext[j];
+        cp_async_wait<kRowRing - 1>();           // row q + 1 has landed
         __syncthreads();
         cur ^= 1;
-        rb ^= 1;
 
         // ---- a core of this stage: hand its sorted state to the walk
-        if (is_core && cst != (int)SELSCAN_LOCUS_MAF_FILTERED) {
+        if (wr) {
             const int r = dir == 0 ? (int)(x - klo) : (int)(khi - 1 - x);
             unsigned char *slot = w.slots + ((size_t)(dir * w.nch + c) * w.R + r) * w.slot_bytes;
             const int xp = w.a.nB > 0;
@@ -989,7 +1016,7 @@ int split_walk_ctas(int n, int xpehh, int tile)
 cudaError_t launch_sweep_path(const SweepArgs &w0, cudaStream_t s)
 {
     SweepArgs w = w0;
-    const size_t ssm = sweep_smem_bytes(w.n, w.a.W, w.threads);
+    const size_t ssm = sweep_smem_bytes(w.n, w.a.W, w.threads, w.R);
     const int E = sweep_e(w.n, w.threads);
     void (*sweep)(SweepArgs);
     if (w.threads == 256)
