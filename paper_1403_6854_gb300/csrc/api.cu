@@ -67,17 +67,24 @@ SweepPlan make_sweep_plan(int n_total, long long m, int mode, const selscan_laun
     if (w.L > 16384) w.L = 16384;
     w.R = (L && L->sweep_stage_cores > 0) ? L->sweep_stage_cores : 0;
     if (w.R > 8192) w.R = 8192;
-    // 256-thread CTAs (3 per SM) up to 24 elements per thread, else 512 (2 per SM)
+    // sorting CTA width: small samples take narrow CTAs (a marker's scan and
+    // barriers then span one to four warps): 32 threads up to 512 haplotypes,
+    // 64 up to 1,024, 128 up to 2,048 (at most 16 elements per thread), 256 up
+    // to 6,144 (24), else 512
     const int want = L ? L->sweep_threads : 0;
-    w.threads = (want == 256 || want == 512) ? want : (n_total <= 256 * 24 ? 256 : 512);
+    if (want == 32 || want == 64 || want == 128 || want == 256 || want == 512) w.threads = want;
+    else w.threads = n_total <= 32 * 16 ? 32 : n_total <= 64 * 16 ? 64 : n_total <= 128 * 16 ? 128
+                   : n_total <= 256 * 24 ? 256 : 512;
     // a thread's allele bits live in one 32-bit word: at most 32 elements per thread
-    if (w.threads == 256 && n_total > 256 * 32) w.threads = 512;
-    // chunks: the resident sweep CTAs split over both directions, each chunk
-    // at least as long as its warm-up
+    while (w.threads < 512 && n_total > w.threads * 32) w.threads *= 2;
+    // chunks: the resident sweep CTAs split over both directions (three
+    // 256-thread CTAs per SM, two of 512, sixteen warps of the narrow widths),
+    // each chunk at least as long as its warm-up
     const long long per = w.L > 256 ? w.L : 256;
     long long nch = (m + per - 1) / per;
     const int sms = device_sms();
-    const int nmax = w.threads == 256 ? (3 * sms) / 2 : sms;
+    const int per_sm = w.threads == 512 ? 2 : (w.threads == 256 ? 3 : 512 / w.threads);
+    const int nmax = (per_sm * sms) / 2;
     if (nch > nmax) nch = nmax;
     if (nch < 1) nch = 1;
     // run lengths are 16-bit: a chunk plus its warm-up stays below 65,000 markers

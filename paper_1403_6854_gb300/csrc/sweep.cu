@@ -134,7 +134,7 @@ size_t sweep_state_bytes(int n, int T) { return (size_t)sweep_npad(n, T) * 4; }
 // bounds the elements per thread, up to 24 stay in registers between the
 // two passes.
 template <int T, int EMAX>
-__global__ void __launch_bounds__(T, T == 512 ? 2 : 3) sweep_kernel(SweepArgs w)
+__global__ void __launch_bounds__(T, T == 512 ? 2 : (T == 256 ? 3 : 512 / T)) sweep_kernel(SweepArgs w)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr bool CACHE = EMAX <= 24;
@@ -1022,10 +1022,16 @@ cudaError_t launch_sweep_path(const SweepArgs &w0, cudaStream_t s)
     if (w.threads == 256)
         sweep = E <= 8 ? sweep_kernel<256, 8> : E <= 16 ? sweep_kernel<256, 16>
               : E <= 24 ? sweep_kernel<256, 24> : sweep_kernel<256, 32>;
-    else
+    else if (w.threads == 512)
         sweep = E <= 4 ? sweep_kernel<512, 4> : E <= 8 ? sweep_kernel<512, 8>
               : E <= 16 ? sweep_kernel<512, 16> : E <= 24 ? sweep_kernel<512, 24>
               : sweep_kernel<512, 32>;
+    else if (w.threads == 128)
+        sweep = E <= 8 ? sweep_kernel<128, 8> : E <= 16 ? sweep_kernel<128, 16> : sweep_kernel<128, 32>;
+    else if (w.threads == 64)
+        sweep = E <= 8 ? sweep_kernel<64, 8> : E <= 16 ? sweep_kernel<64, 16> : sweep_kernel<64, 32>;
+    else
+        sweep = E <= 8 ? sweep_kernel<32, 8> : E <= 16 ? sweep_kernel<32, 16> : sweep_kernel<32, 32>;
     cudaError_t e = cudaFuncSetAttribute(sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm);
     if (e != cudaSuccess) return e;
     const size_t wsm = (size_t)w.split_bytes * (kSplitWarps * 32 / w.split_tile);

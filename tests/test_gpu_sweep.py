@@ -20,7 +20,8 @@ SHAPES = [dict(), dict(sweep_warmup=16, sweep_stage_cores=7), dict(sweep_warmup=
           dict(sweep_warmup=300, sweep_stage_cores=4096), dict(sweep_threads=512),
           dict(sweep_threads=256, sweep_warmup=64, sweep_stage_cores=33),
           dict(sweep_split_tile=16), dict(sweep_split_tile=16, sweep_warmup=16, sweep_stage_cores=5),
-          dict(sweep_split_tile=32)]
+          dict(sweep_split_tile=32), dict(sweep_threads=32), dict(sweep_threads=128),
+          dict(sweep_threads=64, sweep_warmup=40, sweep_stage_cores=9), dict(sweep_threads=256)]
 
 
 @pytest.fixture(scope="module")
@@ -163,11 +164,12 @@ def test_first_window_shorter_than_64_steps(sg):
         assert_ihs_equal(run_ihs(sg, rows, n, pos, gmap, launch=sweep(sg, **kw)), ref, idx=cores)
 
 
-@pytest.mark.parametrize("n,threads", [(6000, 256), (6000, 512), (9000, 0), (9000, 256), (13000, 0)])
+@pytest.mark.parametrize("n,threads", [(6000, 256), (6000, 512), (9000, 0), (9000, 256), (13000, 0),
+                                       (500, 0), (900, 32), (2000, 64), (3000, 64), (1500, 0)])
 def test_elements_per_thread(sg, n, threads):
     """Samples near the register-cached limit of each CTA width, ones that
-    re-read their elements from shared memory, and a 256-thread request above
-    32 elements per thread (taken by 512 threads)."""
+    re-read their elements from shared memory (more than 24 per thread), and
+    requests above 32 elements per thread (taken by the next wider CTA)."""
     m = 90
     hap, pos, gmap = synth.tiny_mosaic(n, m, n + threads, founders=5, switch=0.05, flip=0.003)
     rows = synth.pack(hap)
