@@ -129,9 +129,11 @@ typedef struct {
                                   1..8192 (0 = the whole chunk, capped so that the slot
                                   buffer stays near 24 GiB); sizes the slot buffer */
     int32_t sweep_threads;     /* sweep schedule: threads per sorting CTA, 32, 64, 128, 256
-                                  or 512 (0 = 32 up to 512 haplotypes, 64 up to 1024, 128
-                                  up to 2048, 256 up to 6144, else 512); a width is doubled
-                                  until it holds at most 32 haplotypes per thread */
+                                  or 512 (0 = the narrowest of 32 / 64 / 128 holding at most
+                                  8 haplotypes per thread, 16 on chromosomes with more
+                                  chunks than three 256-thread CTAs per SM hold; else 256
+                                  up to 6144 haplotypes, else 512); a width is doubled until
+                                  it holds at most 32 haplotypes per thread */
     int32_t sweep_split_tile;  /* sweep schedule: lanes per split walk, 32 or 16 (two walks
                                   per warp) (0 = default) */
 } selscan_launch;

@@ -67,22 +67,27 @@ SweepPlan make_sweep_plan(int n_total, long long m, int mode, const selscan_laun
     if (w.L > 16384) w.L = 16384;
     w.R = (L && L->sweep_stage_cores > 0) ? L->sweep_stage_cores : 0;
     if (w.R > 8192) w.R = 8192;
-    // sorting CTA width: small samples take narrow CTAs (a marker's scan and
-    // barriers then span one to four warps): 32 threads up to 512 haplotypes,
-    // 64 up to 1,024, 128 up to 2,048 (at most 16 elements per thread), 256 up
-    // to 6,144 (24), else 512
-    const int want = L ? L->sweep_threads : 0;
-    if (want == 32 || want == 64 || want == 128 || want == 256 || want == 512) w.threads = want;
-    else w.threads = n_total <= 32 * 16 ? 32 : n_total <= 64 * 16 ? 64 : n_total <= 128 * 16 ? 128
-                   : n_total <= 256 * 24 ? 256 : 512;
-    // a thread's allele bits live in one 32-bit word: at most 32 elements per thread
-    while (w.threads < 512 && n_total > w.threads * 32) w.threads *= 2;
-    // chunks: the resident sweep CTAs split over both directions (three
-    // 256-thread CTAs per SM, two of 512, sixteen warps of the narrow widths),
-    // each chunk at least as long as its warm-up
+    // chunks are at least as long as their warm-up
     const long long per = w.L > 256 ? w.L : 256;
     long long nch = (m + per - 1) / per;
     const int sms = device_sms();
+    // sorting CTA width, for a small sample the narrowest of 32 / 64 / 128 /
+    // 256 threads that keeps it at about g elements per thread: g = 8 while
+    // every chunk runs at once anyway (a marker's latency is what counts: one
+    // warp sorting 8 elements a lane beats eight warps sorting mostly padding,
+    // and loses with 16), g = 16 when the chromosome has more chunks than three
+    // 256-thread CTAs per SM hold (narrow CTAs then run more, shorter chunks at
+    // once).  Larger samples: 256 threads up to 6,144 haplotypes, else 512
+    const int want = L ? L->sweep_threads : 0;
+    const long long g = nch > (3ll * sms) / 2 ? 16 : 8;
+    if (want == 32 || want == 64 || want == 128 || want == 256 || want == 512) w.threads = want;
+    else if (n_total <= 128 * g)
+        w.threads = n_total <= 32 * g ? 32 : n_total <= 64 * g ? 64 : 128;
+    else w.threads = n_total <= 256 * 24 ? 256 : 512;
+    // a thread's allele bits live in one 32-bit word: at most 32 elements per thread
+    while (w.threads < 512 && n_total > w.threads * 32) w.threads *= 2;
+    // the resident sweep CTAs split over both directions: three 256-thread
+    // CTAs per SM, two of 512, sixteen warps of the narrow widths
     const int per_sm = w.threads == 512 ? 2 : (w.threads == 256 ? 3 : 512 / w.threads);
     const int nmax = (per_sm * sms) / 2;
     if (nch > nmax) nch = nmax;
