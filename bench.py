@@ -192,7 +192,7 @@ def run_reference(args, rank, world):
     }), flush=True)
 
 
-SWEEP_DRAM_BYTES_PER_CORE = 4.6175e9 / 125020
+SWEEP_DRAM_BYTES_PER_CORE = 4.6139e9 / 125020
 
 
 def main():
@@ -370,12 +370,12 @@ def main():
         achieved = walk_bytes / (walk_ms / 1e3) / 1e9
         # DRAM bytes of the sorted-sweep kernels from one ncu capture of the
         # 250k-marker case (dram__bytes_read.sum + dram__bytes_write.sum of
-        # sweep_kernel and split_walk_kernel: 4.62 GB over 125,020 core loci),
+        # sweep_kernel and split_walk_kernel: 4.61 GB over 125,020 core loci),
         # scaled by core loci
         traffic, traffic_note = None, "no capture for this schedule"
         if launch_fields.get("schedule") == 3:
             traffic = cores * SWEEP_DRAM_BYTES_PER_CORE
-            traffic_note = ("ncu capture of the 250k case, 36,930 DRAM bytes per core locus, "
+            traffic_note = ("ncu capture of the 250k case, 36,910 DRAM bytes per core locus, "
                             "scaled by core loci")
         line = {
             "metric": METRIC, "value": value, "unit": "core loci/s", "n_gpus": world,
