@@ -137,3 +137,19 @@ def test_default_schedule_rule(sg):
     assert sg.selscan_default_schedule(16384, 10_000_000, I) == sg.SCHED_IN_ORDER
     for bad in ((1, 100000, I), (100, 0, I), (100, 100000, 7)):
         assert sg.selscan_default_schedule(*bad) == -1
+
+
+def test_sweep_plan_shape_on_host(sg):
+    """Host-side plan of the default launch (152 SMs when no GPU answers): the
+    5,000 x 1M scan is one sweep stage (validate, select, sweep, split walk,
+    bucket x3, second pass, finalize) with its slots under the 24 GiB budget;
+    a chr22-shaped scan takes the per-step walk."""
+    I = sg.MODE_IHS
+    assert sg.selscan_launch_count(5000, 1_000_000, I) == 9
+    assert sg.selscan_launch_count(204, 22147, I) == 4
+    ws = sg.selscan_workspace_bytes(5000, 1_000_000, I)
+    assert 20 << 30 < ws < 26 << 30
+    # 64-core stages of chunks of about 4,400 cores (152 SMs: 228 chunks per
+    # direction) take about 69 stages, two launches each
+    k = sg.selscan_launch_count(5000, 1_000_000, I, sg.make_launch(sg.SCHED_SWEEP, sweep_stage_cores=64))
+    assert (k - 7) % 2 == 0 and 60 <= (k - 7) // 2 <= 80
