@@ -216,3 +216,17 @@ def test_xpehh_at_scale_sampled_cores(sg):
     ref = oracle.xpehh(d.rows, 1000, 1000, d.pos, d.gmap, cores=cores)
     assert_xpehh_equal(got, ref, idx=cores)
     assert np.array_equal(np.isfinite(got["lnratio"]), got["status"] == 0)
+
+
+def test_xpehh_1m_sampled_cores(sg):
+    """The bench's XPEHH workload at full size (2,500 + 2,500 haplotypes x
+    1,000,000 SNPs, 20 planted sweeps in A) in the launch the bench times (the
+    default: the sorted sweep): random cores match the oracle, and every locus
+    has a finite ratio exactly when it is OK."""
+    d = synth.generate(synth.spec("xpehh1m"))
+    got = run_xpehh(sg, d.rows, 2500, 2500, d.pos, d.gmap)
+    rng = np.random.default_rng(2)
+    cores = np.sort(rng.choice(d.spec.m, 24, replace=False))
+    ref = oracle.xpehh(d.rows, 2500, 2500, d.pos, d.gmap, cores=cores)
+    assert_xpehh_equal(got, ref, idx=cores)
+    assert np.array_equal(np.isfinite(got["lnratio"]), got["status"] == 0)
