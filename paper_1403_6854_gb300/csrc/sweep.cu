@@ -127,12 +127,14 @@ size_t sweep_state_bytes(int n, int T) { return (size_t)sweep_npad(n, T) * 4; }
 
 // ---- the sweep ---------------------------------------------------------------
 // Shared memory: two buffers of np packed elements (bit index of the haplotype
-// in the row | run length with its predecessor << 16), two row buffers with
-// one extra all-ones word, the warp totals.  Positions n..np-1 hold padding
-// elements whose allele is that all-ones word: they sort after every real
-// haplotype and never touch a real element's run length.  T threads; EMAX
-// bounds the elements per thread, up to 24 stay in registers between the
-// two passes.
+// in the row | run length with its predecessor << 16), a ring of kRowRing row
+// buffers (filled by cp.async, each with one extra all-ones word), the warp
+// totals, a core's first-window counts and offsets, and the stage's core
+// bitmap.  Positions n..np-1 hold padding elements whose allele is that
+// all-ones word: they sort after every real haplotype and never touch a real
+// element's run length.  T threads (32 to 512); EMAX bounds the elements per
+// thread (at most 32, one allele bit each in a 32-bit mask), up to 24 stay in
+// registers between the two passes.
 template <int T, int EMAX>
 __global__ void __launch_bounds__(T, T == 512 ? 2 : (T == 256 ? 3 : 512 / T)) sweep_kernel(SweepArgs w)
 {
