@@ -45,6 +45,11 @@
  * device (decreasing positions or map, a watchdog timeout) are written to the
  * output's `error` word (0 = none) instead.  Per-locus outcomes are status
  * codes, not errors.  No C++ exception crosses this boundary.
+ * SELSCAN_ERR_TIMEOUT in an error word voids every result of that launch:
+ * a warp whose bounded wait for its marker-window copies gave up stops taking
+ * walks (a late copy could still land in its buffers), so walks go unwritten;
+ * for selscan_batch_run that is every scan of the tick, whichever scan's word
+ * carries the code.
  *
  * Limits: n (iHS) and n_A + n_B (XPEHH) at most 65,000 haplotypes; m < 2^30
  * markers.
@@ -202,7 +207,9 @@ int selscan_xpehh(const uint64_t *hap, int64_t ld, int32_t nA, int32_t nB, int64
                   const selscan_launch *launch, void *stream);
 
 /* EHH decay around one locus (Eq. 1 and Eq. 3 at every step, Section 1.1),
- * S(i) recorded for i < capacity. */
+ * S(i) recorded for i < capacity.  SELSCAN_ERR_UNSUPPORTED when the six
+ * walks' shared-memory slices (their marker window holds rows of ld words)
+ * exceed one CTA's shared memory, e.g. ld above about 1,000 words. */
 int selscan_ehh(const uint64_t *hap, int64_t ld, int32_t n, int64_t m,
                 const int64_t *pos_bp, const double *gmap, int64_t locus,
                 const selscan_params *p, const selscan_ehh_out *out, int64_t capacity,
@@ -218,7 +225,9 @@ int selscan_ehh(const uint64_t *hap, int64_t ld, int32_t n, int64_t m,
  * is no workspace argument and nothing is allocated or freed.
  * - n above SELSCAN_EHH_NOALLOC_MAX_N is refused with SELSCAN_ERR_INVALID_ARG.
  * - The first call on each device looks up the array's device address (with
- *   that device current); make that first call before any stream capture.
+ *   that device current), and so does the first call after the device's
+ *   context was destroyed and re-created (cudaDeviceReset); make the first
+ *   call on a device before any stream capture.
  * - Every call on a device shares the one array, which keeps the last call's
  *   contents (each call initialises what it reads, so no clearing is needed);
  *   calls that overlap on the same GPU race, so order them on one stream. */

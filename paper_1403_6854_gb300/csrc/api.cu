@@ -12,6 +12,17 @@ int device_sms();
 
 using namespace selscan;
 
+namespace selscan {
+
+bool params_ok(const selscan_params *p)
+{
+    return p && p->ehh_cut_den > 0 && p->maf_den > 0 && p->gap_scale_bp > 0 && p->max_gap_bp >= 0 &&
+           (p->include_crossing_term == 0 || p->include_crossing_term == 1) &&
+           (p->use_physical_map == 0 || p->use_physical_map == 1);
+}
+
+}  // namespace selscan
+
 namespace {
 
 constexpr int kDefaultWarpsPerCta = 8;
@@ -52,12 +63,6 @@ struct Plan {
 
 inline size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-bool params_ok(const selscan_params *p)
-{
-    return p && p->ehh_cut_den > 0 && p->maf_den > 0 && p->gap_scale_bp > 0 && p->max_gap_bp >= 0 &&
-           (p->include_crossing_term == 0 || p->include_crossing_term == 1) &&
-           (p->use_physical_map == 0 || p->use_physical_map == 1);
-}
 
 SweepPlan make_sweep_plan(int n_total, long long m, int mode, const selscan_launch *L)
 {
@@ -254,7 +259,7 @@ ScanArgs make_args(const uint64_t *hap, int64_t ld, int nA, int nB, int64_t m, c
 Scratch make_scratch(unsigned char *ws, const Layout &l, int n_total, const Plan &p)
 {
     Scratch sc;
-    sc.base = ws + l.scratch;
+    sc.base = ws ? ws + l.scratch : nullptr;
     sc.per_warp = l.per_warp;
     sc.cap = list_cap(n_total);
     sc.tcap = table_cap(n_total);
@@ -358,6 +363,52 @@ int run_scan(int mode, const uint64_t *hap, int64_t ld, int32_t nA, int32_t nB, 
 
 }  // namespace
 
+namespace selscan {
+
+int ehh_prepare(const uint64_t *hap, int64_t ld, int32_t n, int64_t m, const int64_t *pos_bp,
+                const double *gmap, int64_t locus, const selscan_params *p,
+                const selscan_ehh_out *out, int64_t capacity, int32_t max_n, ScanArgs *a,
+                Scratch *sc, size_t *scratch_off, size_t *ws_need)
+{
+    if (!hap || !pos_bp || !gmap || !out || !params_ok(p)) return SELSCAN_ERR_INVALID_ARG;
+    if (n < 2 || n > max_n || n > kMaxHaplotypes || m < 1 || m >= (1ll << 30) ||
+        ld < (n + 63) / 64 || locus < 0 || locus >= m || capacity < 0)
+        return SELSCAN_ERR_INVALID_ARG;
+    if ((capacity > 0 && !out->S) || !out->len || !out->stop || !out->status || !out->ihh ||
+        !out->denom || !out->error)
+        return SELSCAN_ERR_INVALID_ARG;
+    const Plan plan = make_plan(SELSCAN_MODE_EHH, ld, nullptr);
+    // six walks, each with its on-chip slice (pool, table, marker window): a
+    // wide row stride can push the window past the per-CTA limit
+    if (smem_per_warp(plan.cap_s, plan.tcap_s, plan.rowcap, plan.poscap) * (size_t)plan.wpc >
+        kMaxSmemPerCta)
+        return SELSCAN_ERR_UNSUPPORTED;
+    const Layout l = make_layout(n, m, SELSCAN_MODE_EHH, plan.nslots);
+    *a = make_args(hap, ld, n, 0, m, pos_bp, gmap, p);
+    *sc = make_scratch(nullptr, l, n, plan);
+    sc->base = nullptr;
+    sc->err = out->error;
+    *scratch_off = l.scratch;
+    *ws_need = l.total;
+    return SELSCAN_OK;
+}
+
+int ehh_run(const ScanArgs &a, int64_t locus, const selscan_params *p, const Scratch &sc,
+            const selscan_ehh_out *out, int64_t capacity, void *stream)
+{
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaMemsetAsync(out->error, 0, sizeof(int32_t), s) != cudaSuccess) return SELSCAN_ERR_CUDA;
+    if (launch_validate(a.pos, a.gmap, a.m, out->error, s, !p->use_physical_map) != cudaSuccess)
+        return SELSCAN_ERR_CUDA;
+    if (launch_ehh(a, locus, sc, (unsigned long long *)out->S, capacity, (long long *)out->len,
+                   out->stop, out->status, out->ihh, (unsigned long long *)out->denom, s) !=
+        cudaSuccess)
+        return SELSCAN_ERR_CUDA;
+    return SELSCAN_OK;
+}
+
+}  // namespace selscan
+
 extern "C" {
 
 void selscan_default_params(selscan_params *p)
@@ -442,29 +493,15 @@ int selscan_ehh(const uint64_t *hap, int64_t ld, int32_t n, int64_t m, const int
                 const selscan_ehh_out *out, int64_t capacity, void *workspace, size_t ws_bytes,
                 void *stream)
 {
-    if (!hap || !pos_bp || !gmap || !out || !params_ok(p)) return SELSCAN_ERR_INVALID_ARG;
-    if (n < 2 || n > kMaxHaplotypes || m < 1 || m >= (1ll << 30) || ld < (n + 63) / 64 ||
-        locus < 0 || locus >= m || capacity < 0)
-        return SELSCAN_ERR_INVALID_ARG;
-    if ((capacity > 0 && !out->S) || !out->len || !out->stop || !out->status || !out->ihh ||
-        !out->denom || !out->error)
-        return SELSCAN_ERR_INVALID_ARG;
-    const Plan plan = make_plan(SELSCAN_MODE_EHH, ld, nullptr);
-    const Layout l = make_layout(n, m, SELSCAN_MODE_EHH, plan.nslots);
-    if (!workspace || ws_bytes < l.total || ((uintptr_t)workspace & 255)) return SELSCAN_ERR_WORKSPACE;
-    cudaStream_t s = (cudaStream_t)stream;
-    const ScanArgs a = make_args(hap, ld, n, 0, m, pos_bp, gmap, p);
-    Scratch sc = make_scratch((unsigned char *)workspace, l, n, plan);
-    sc.err = out->error;
-    if (cudaMemsetAsync(out->error, 0, sizeof(int32_t), s) != cudaSuccess) return SELSCAN_ERR_CUDA;
-    if (launch_validate((const long long *)pos_bp, gmap, m, out->error, s, !p->use_physical_map) !=
-        cudaSuccess)
-        return SELSCAN_ERR_CUDA;
-    if (launch_ehh(a, locus, sc, (unsigned long long *)out->S, capacity, (long long *)out->len,
-                   out->stop, out->status, out->ihh, (unsigned long long *)out->denom, s) !=
-        cudaSuccess)
-        return SELSCAN_ERR_CUDA;
-    return SELSCAN_OK;
+    ScanArgs a;
+    Scratch sc;
+    size_t scratch_off = 0, need = 0;
+    const int rc = ehh_prepare(hap, ld, n, m, pos_bp, gmap, locus, p, out, capacity, kMaxHaplotypes,
+                               &a, &sc, &scratch_off, &need);
+    if (rc != SELSCAN_OK) return rc;
+    if (!workspace || ws_bytes < need || ((uintptr_t)workspace & 255)) return SELSCAN_ERR_WORKSPACE;
+    sc.base = (unsigned char *)workspace + scratch_off;
+    return ehh_run(a, locus, p, sc, out, capacity, stream);
 }
 
 int selscan_pack(const uint8_t *hap01, int32_t n, int64_t m, int32_t hap_major, uint64_t *rows,

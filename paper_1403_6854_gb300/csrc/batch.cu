@@ -188,10 +188,13 @@ __global__ void __launch_bounds__(256, 2) walk_batch_kernel(const __grid_constan
         if (d.sk.core_status[c] == (int8_t)SELSCAN_LOCUS_MAF_FILTERED) continue;
         b.R = d.R;
         b.err = d.err;
+        // a timed-out window wait stops this warp (the tick's results are void)
         if (d.sk.mode == 1) {
-            for (int q = 0; q < 2; ++q) run_item<2>(d.a, d.sk, b, (uint32_t)(c * 2 + q), 0, wpar);
+            for (int q = 0; q < 2; ++q)
+                if (!run_item<2>(d.a, d.sk, b, (uint32_t)(c * 2 + q), 0, wpar)) return;
         } else {
-            for (int q = 0; q < 4; ++q) run_item<1>(d.a, d.sk, b, (uint32_t)(c * 4 + q), 0, wpar);
+            for (int q = 0; q < 4; ++q)
+                if (!run_item<1>(d.a, d.sk, b, (uint32_t)(c * 4 + q), 0, wpar)) return;
         }
     }
 }

@@ -57,8 +57,12 @@ __device__ __forceinline__ uint32_t bucket_of(float ehh)
     return (uint32_t)b;
 }
 
+// Runs one walk and stores its result.  Returns false if the warp must stop
+// taking walks: a bounded wait for its window copies gave up (the error word
+// holds SELSCAN_ERR_TIMEOUT), so a copy may still land in its buffers.  The
+// launch's results are then invalid as a whole (every scan of a batch tick).
 template <int NPOP>
-__device__ __forceinline__ void run_item(const ScanArgs &a, const ItemSink &sk, WarpBufs &b,
+__device__ __forceinline__ bool run_item(const ScanArgs &a, const ItemSink &sk, WarpBufs &b,
                                          uint32_t item, int max_steps, unsigned wpar[2])
 {
     const int lane = threadIdx.x & 31;
@@ -68,12 +72,13 @@ __device__ __forceinline__ void run_item(const ScanArgs &a, const ItemSink &sk, 
     const int dir = q & 1;
     const int sel = NPOP == 2 ? 0 : (q < 2 ? 0 : 1);
     WalkOut o = walk<NPOP>(a, core, dir, sel, b, nullptr, 0, max_steps, wpar);
-    if (lane != 0) return;
+    const bool go_on = !o.abandon;
+    if (lane != 0) return go_on;
     if (o.status == WALK_UNFINISHED) {
         const unsigned long long slot = atomicAdd(&sk.q->n2, 1ull);
         sk.list2[slot] = item;
         sk.key2[slot] = bucket_of(o.key);
-        return;
+        return go_on;
     }
     sk.item_status[item] = (int8_t)o.status;
     sk.stop[item] = o.stop;
@@ -87,6 +92,7 @@ __device__ __forceinline__ void run_item(const ScanArgs &a, const ItemSink &sk, 
         sk.item_ihh[item] = o.ihh[0];
         sk.digest[item] = o.dig[0];
     }
+    return go_on;
 }
 
 }  // namespace selscan

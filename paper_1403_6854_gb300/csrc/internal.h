@@ -4,6 +4,7 @@
 #include <stdint.h>
 #include <cuda_runtime.h>
 
+#include "../../include/selscan.h"
 #include "walk.cuh"
 
 namespace selscan {
@@ -99,6 +100,23 @@ int max_ctas_per_sm(int schedule, int warps_per_cta, size_t smem_bytes, int minb
 // Second pass of the per-step walk over the items queued in sink.list2.
 cudaError_t launch_pass2(const ScanArgs &a, const ItemSink &sink, const Scratch &sc,
                          int warps_per_cta, int ctas, int minb, cudaStream_t s);
+
+// ---- argument checks and the single-locus report (api.cu), shared by
+// selscan_ehh and selscan_ehh_noalloc
+bool params_ok(const selscan_params *p);
+// Checks the arguments of a single-locus report (n at most max_n) and fills
+// the walk arguments and the six walks' scratch layout; the scratch base is
+// left null for the caller: scratch_off is where it starts inside a workspace
+// of ws_need bytes.  SELSCAN_ERR_UNSUPPORTED when the walks' on-chip slices
+// (whose marker window grows with the row stride) exceed one CTA's shared
+// memory.
+int ehh_prepare(const uint64_t *hap, int64_t ld, int32_t n, int64_t m, const int64_t *pos_bp,
+                const double *gmap, int64_t locus, const selscan_params *p,
+                const selscan_ehh_out *out, int64_t capacity, int32_t max_n, ScanArgs *a,
+                Scratch *sc, size_t *scratch_off, size_t *ws_need);
+// Clears the error word, validates positions / map and launches the report.
+int ehh_run(const ScanArgs &a, int64_t locus, const selscan_params *p, const Scratch &sc,
+            const selscan_ehh_out *out, int64_t capacity, void *stream);
 
 // ---- sorted-sweep walks (sweep.cu)
 constexpr int kSplitWarps = 8;       // warps of one split-walk CTA

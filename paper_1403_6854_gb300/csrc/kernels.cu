@@ -101,14 +101,14 @@ __global__ void __launch_bounds__(256, MINB) walk_persistent_kernel(ScanArgs a, 
         idx = __shfl_sync(FULLMASK, idx, 0);
         if (idx >= total) break;
         if (pass == 2) {
-            run_item<NPOP>(a, sk, b, sk.sorted2[idx], 0, wpar);
+            if (!run_item<NPOP>(a, sk, b, sk.sorted2[idx], 0, wpar)) return;
             continue;
         }
         const unsigned long long end = idx + step < total ? idx + step : total;
         for (unsigned long long c = idx; c < end; ++c) {
             if (sk.core_status[c] == (int8_t)SELSCAN_LOCUS_MAF_FILTERED) continue;
             for (int q = 0; q < ipc; ++q)
-                run_item<NPOP>(a, sk, b, (uint32_t)(c * ipc + q), max_steps, wpar);
+                if (!run_item<NPOP>(a, sk, b, (uint32_t)(c * ipc + q), max_steps, wpar)) return;
         }
     }
 }
@@ -146,7 +146,8 @@ __global__ void __launch_bounds__(128) walk_plain_kernel(ScanArgs a, ItemSink sk
                            sc.base + (size_t)slot * sc.per_warp, sc);
     init_window(b);
     unsigned wpar[2] = {0u, 0u};
-    run_item<NPOP>(a, sk, b, (uint32_t)(core * (NPOP == 2 ? 2 : 4) + warp), 0, wpar);
+    // a warp whose copies may still be in flight keeps its slot (nothing else reuses it)
+    if (!run_item<NPOP>(a, sk, b, (uint32_t)(core * (NPOP == 2 ? 2 : 4) + warp), 0, wpar)) return;
     __syncwarp();
     if (lane == 0) {
         __threadfence();

@@ -83,6 +83,9 @@ struct WalkOut {
     unsigned long long dig[3];
     unsigned long long D;            // C(N,2) of the walk's sample (pooled for XPEHH)
     float key;                       // EHH at the step cap (unfinished walks)
+    bool abandon;                    // a bounded wait for the warp's window copies gave
+                                     // up: a copy may still land in its buffers, so the
+                                     // warp must not start another walk
 };
 
 __device__ __forceinline__ unsigned int lanemask_lt()
@@ -574,6 +577,7 @@ __device__ WalkOut walk(const ScanArgs &a, long long core, int dir, int sel, con
     o.dig[0] = o.dig[1] = o.dig[2] = 0ull;
     o.D = 0ull;
     o.key = 0.f;
+    o.abandon = false;
 
     // ---- the core row, staged in window buffer 0 (refilled after step 0)
     const unsigned int *row0 = (const unsigned int *)(a.hap + core * a.ld);
@@ -707,7 +711,8 @@ __device__ WalkOut walk(const ScanArgs &a, long long core, int dir, int sel, con
     // drain copies still in flight before the buffers serve the next walk
     const bool d0 = win_wait(b, wb[0], 0);
     const bool d1 = win_wait(b, wb[1], 1);
-    if (!d0 || !d1) o.status = WALK_UNDEFINED;
+    o.abandon = !d0 || !d1;
+    if (o.abandon) o.status = WALK_UNDEFINED;
     win_parity[0] = wb[0].parity;
     win_parity[1] = wb[1].parity;
     if (NPOP == 2) {

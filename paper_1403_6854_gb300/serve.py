@@ -346,6 +346,9 @@ class GpuExecutor:
         out = {f: host[f].numpy() for f in self.FIELDS}
         out["digest"] = out["digest"].view(np.uint64)
         if int(out["error"][0]) != 0:
+            # a device error ends the serving loop and fails every open request:
+            # a TIMEOUT voids the whole tick it happened in, including the other
+            # scans' walks of that tick, so no result of it may be returned
             raise self.sg.SelscanError(int(out["error"][0]), "served scan")
         return out
 

@@ -153,3 +153,25 @@ def test_sweep_plan_shape_on_host(sg):
     # direction) take about 69 stages, two launches each
     k = sg.selscan_launch_count(5000, 1_000_000, I, sg.make_launch(sg.SCHED_SWEEP, sweep_stage_cores=64))
     assert (k - 7) % 2 == 0 and 60 <= (k - 7) // 2 <= 80
+
+
+def test_single_locus_report_refuses_a_row_stride_beyond_shared_memory(sg):
+    """Both single-locus entry points stage rows of ld words in each walk's
+    marker window: a padded stride above about 1,040 words would exceed one
+    CTA's shared memory, and both refuse it as unsupported before any device
+    work (fake device pointers are never touched)."""
+    lib = sg.load_library()
+    p = sg.selscan_default_params()
+    fake = ctypes.c_void_p(0x1000)
+    oe = sg.selscan_ehh_out(*([fake] * 7))
+    for ld, want in ((1100, sg.ERR_UNSUPPORTED), (4096, sg.ERR_UNSUPPORTED)):
+        assert lib.selscan_ehh(fake, ld, 100, 10, fake, fake, 3, ctypes.byref(p), ctypes.byref(oe),
+                               4, fake, 1 << 30, None) == want
+        assert lib.selscan_ehh_noalloc(fake, ld, 100, 10, fake, fake, 3, ctypes.byref(p),
+                                       ctypes.byref(oe), 4, None) == want
+    # arguments are checked the same way by both
+    bad = sg.selscan_default_params(ehh_cut=(1, 0))
+    assert lib.selscan_ehh_noalloc(fake, 2, 100, 10, fake, fake, 3, ctypes.byref(bad),
+                                   ctypes.byref(oe), 4, None) == sg.ERR_INVALID_ARG
+    assert lib.selscan_ehh_noalloc(fake, 2, 100, 10, fake, fake, 10, ctypes.byref(p),
+                                   ctypes.byref(oe), 4, None) == sg.ERR_INVALID_ARG

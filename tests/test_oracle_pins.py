@@ -300,6 +300,57 @@ def test_maf_boundary(minor, reported):
         assert r["stop"][0].tolist() == [0, 0, 0, 0]
 
 
+def xpehh_rows(hapA, hapB):
+    return np.concatenate([pack(hapA), pack(hapB)], 1)
+
+
+@pytest.mark.parametrize("derived_a,derived_b,filtered", [
+    (5, 0, False),    # pooled minor 5 of 100: 5/100 >= 1/20, reported; B alone is monomorphic
+    (2, 3, False),    # pooled minor 5: reported, though A alone (2/50 < 1/20) would be filtered
+    (4, 0, True),     # pooled minor 4 of 100: filtered, though A alone (4/50) would pass
+    (50, 46, True),   # pooled derived 96: minor 4, filtered (the minor allele is the ancestral one)
+    (45, 50, False),  # pooled derived 95: minor 5, reported
+])
+def test_xpehh_maf_filter_tests_the_pooled_sample(derived_a, derived_b, filtered):
+    """Reading c9: the paper states the MAF filter for iHS only (Section 1.2).
+    With xpehh_maf_filter set, the oracle applies that rule to the pooled
+    sample A + B at the core (minor count vs n_A + n_B), not to either
+    population alone; without it every marker is reported.  n_A = n_B = 50,
+    cutoff 1/20: a pooled minor count of 5 is reported and 4 is filtered,
+    including cases where a per-population reading would decide the other
+    way."""
+    nA = nB = 50
+    m = 6
+    hA = np.zeros((m, nA), dtype=np.uint8)
+    hB = np.zeros((m, nB), dtype=np.uint8)
+    hA[3, :derived_a] = 1
+    hB[3, :derived_b] = 1
+    # the flanking markers split every pair, so walks end after one step
+    rng = np.random.default_rng(derived_a * 100 + derived_b)
+    for k in (0, 1, 2, 4, 5):
+        hA[k] = rng.integers(0, 2, nA)
+        hB[k] = rng.integers(0, 2, nB)
+    pos = np.arange(m, dtype=np.int64) * 1000 + 1
+    gmap = np.arange(m, dtype=np.float64) * DELTA
+    rows = xpehh_rows(hA, hB)
+    on = oracle.xpehh(rows, nA, nB, pos, gmap, cores=[3], p=oracle.params(xpehh_maf_filter=1))
+    off = oracle.xpehh(rows, nA, nB, pos, gmap, cores=[3], p=oracle.params(xpehh_maf_filter=0))
+    assert on["n1"][0] == off["n1"][0] == derived_a + derived_b
+    assert off["status"][0] != oracle.MAF_FILTERED
+    if filtered:
+        assert on["status"][0] == oracle.MAF_FILTERED and np.isnan(on["lnratio"][0])
+        assert on["stop"][0].tolist() == [0, 0] and on["digest"][0].tolist() == [0] * 6
+    else:
+        assert on["status"][0] == off["status"][0] != oracle.MAF_FILTERED
+        assert on["stop"][0].tolist() == off["stop"][0].tolist()
+        assert on["digest"][0].tolist() == off["digest"][0].tolist()
+    # the filter also follows the cutoff parameter: at 1/10 a pooled minor count
+    # of 5 is filtered
+    tight = oracle.xpehh(rows, nA, nB, pos, gmap, cores=[3],
+                         p=oracle.params(xpehh_maf_filter=1, maf=(1, 10)))
+    assert tight["status"][0] == oracle.MAF_FILTERED
+
+
 def test_ehh_exactly_at_cutoff_continues():
     # Reading c2 (strict "<"): 16 carriers walking down from core marker 4;
     # x_1 splits them 4 + 12, so S(1) = 6 + 66 = 72 and EHH_1(x_1) = 72/120,

@@ -4,9 +4,11 @@ Some callers cannot allocate device memory while they run (their memory
 belongs to another framework's pool, or everything is reserved at start-up),
 so this entry point takes no workspace and uses a fixed array inside the
 library instead.  Its results must equal those of selscan_ehh, which uses a
-caller workspace, on consecutive calls (the second call finds the first
-call's leftovers in the shared array).  This file is named to be collected
-last.
+caller workspace, on consecutive calls that find the previous call's
+leftovers in the shared array, including calls whose sample size (and with
+it the slices' size and offsets in the array) changes from one call to the
+next.  A 5,000-haplotype locus is also checked against the CPU oracle.  This
+file is named to be collected last.
 """
 import ctypes
 
@@ -14,6 +16,7 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 import synth
 from parity_util import IHH_RTOL, to_np
 
@@ -62,23 +65,42 @@ def assert_same(a, b):
     np.testing.assert_allclose(a["ihh"], b["ihh"], rtol=IHH_RTOL, atol=0)
 
 
-@pytest.mark.parametrize("name", ["chr22", "wide"])
-def test_noalloc_equals_workspace_entry_point_on_consecutive_calls(sg, name):
-    if name == "chr22":
-        d = synth.generate(synth.spec("chr22"))
-        loci = [11_000, 11_090]
-    else:   # 5,000 haplotypes: slices near the array's size
-        spec = synth.ScanSpec("wide", "ihs", 3000, 750_000, 7, [synth.PopSpec(5000, 200)])
-        d = synth.generate(spec)
-        loci = [1500, 1517]
-    n = d.spec.pops[0].n
-    hap, pos, gmap = sg.to_device(d.rows, d.pos, d.gmap)
+def wide_data():
+    """5,000 haplotypes on 3,000 markers: slices near the array's size."""
+    spec = synth.ScanSpec("wide", "ihs", 3000, 750_000, 7, [synth.PopSpec(5000, 200)])
+    return synth.generate(spec)
+
+
+def test_noalloc_equals_workspace_entry_point_on_consecutive_calls(sg):
+    """Calls in the order wide, small, wide, small, wide: each one equals a
+    fresh selscan_ehh on the same locus, whatever the previous call left in
+    the shared array."""
     cap = 2048
-    for locus in loci:                      # two calls in a row on the shared array
+    wide = wide_data()
+    small = synth.generate(synth.spec("chr22"))
+    sets = []
+    for d in (wide, small):
+        hap, pos, gmap = sg.to_device(d.rows, d.pos, d.gmap)
+        sets.append((hap, d.spec.pops[0].n, pos, gmap))
+    sequence = [(0, 1500), (1, 11_000), (0, 1517), (1, 11_090), (0, 1500)]
+    for which, locus in sequence:
+        hap, n, pos, gmap = sets[which]
         got = call_noalloc_abi(sg, hap, n, pos, gmap, locus, cap)
         ref = sg.selscan_ehh(hap, n, pos, gmap, locus, cap)
         sg.check(ref)
         assert_same(got, to_np(ref))
+
+
+def test_noalloc_wide_locus_matches_the_oracle(sg):
+    """The 5,000-haplotype case against the CPU oracle's literal string
+    enumeration: every S(i) recorded, lengths, stops, status and iHH."""
+    cap = 2048
+    d = wide_data()
+    hap, pos, gmap = sg.to_device(d.rows, d.pos, d.gmap)
+    for locus in (1500, 1517):
+        got = call_noalloc_abi(sg, hap, 5000, pos, gmap, locus, cap)
+        ref = oracle.ehh(d.rows, 5000, d.pos, d.gmap, locus, cap)
+        assert_same(got, ref)
 
 
 def test_noalloc_refuses_samples_above_its_limit(sg):
