@@ -189,7 +189,8 @@ void selscan_default_params(selscan_params *p);
 
 /* Workspace bytes needed by one call of the given mode on a problem of
  * n_total haplotypes (n, or n_A + n_B) and m markers, for the given launch
- * (NULL = defaults).  The workspace must be 256-byte aligned. */
+ * (NULL = defaults); for a core-range call, m = its number of cores k1 - k0.
+ * The workspace must be 256-byte aligned. */
 size_t selscan_workspace_bytes(int32_t n_total, int64_t m, int32_t mode,
                                const selscan_launch *launch);
 
@@ -205,6 +206,26 @@ int selscan_xpehh(const uint64_t *hap, int64_t ld, int32_t nA, int32_t nB, int64
                   const int64_t *pos_bp, const double *gmap, const selscan_params *p,
                   const selscan_xpehh_out *out, void *workspace, size_t ws_bytes,
                   const selscan_launch *launch, void *stream);
+
+/* The scans of one chromosome restricted to the cores [k0, k1) (0 <= k0 <
+ * k1 <= m), for splitting one scan over several GPUs or calls (Section 3:
+ * the sites are independent and every walk may read the whole data set).
+ * Each call needs the whole matrix, positions and map of all m markers --
+ * walks run to wherever their EHH or the rules stop them, outside the range
+ * too -- but walks only from its own cores: outputs are arrays of k1 - k0
+ * cores (entry j is core k0 + j; stop and digest as for the whole scan, 4 or
+ * 2 / 6 per core).  The results of core k equal those of the whole scan bit
+ * for bit, whatever the split.  Workspace: selscan_workspace_bytes(n_total,
+ * k1 - k0, mode, launch); the default schedule is chosen for k1 - k0 cores.
+ * SELSCAN_ERR_INVALID_ARG for an empty or out-of-bounds range. */
+int selscan_ihs_range(const uint64_t *hap, int64_t ld, int32_t n, int64_t m, int64_t k0,
+                      int64_t k1, const int64_t *pos_bp, const double *gmap,
+                      const selscan_params *p, const selscan_ihs_out *out, void *workspace,
+                      size_t ws_bytes, const selscan_launch *launch, void *stream);
+int selscan_xpehh_range(const uint64_t *hap, int64_t ld, int32_t nA, int32_t nB, int64_t m,
+                        int64_t k0, int64_t k1, const int64_t *pos_bp, const double *gmap,
+                        const selscan_params *p, const selscan_xpehh_out *out, void *workspace,
+                        size_t ws_bytes, const selscan_launch *launch, void *stream);
 
 /* EHH decay around one locus (Eq. 1 and Eq. 3 at every step, Section 1.1),
  * S(i) recorded for i < capacity.  SELSCAN_ERR_UNSUPPORTED when the six
@@ -308,6 +329,33 @@ size_t selscan_normalize_workspace_bytes(int32_t nbins);
 int selscan_normalize(const double *score, const int8_t *status, const int32_t *n1, int64_t m,
                       int32_t n, int32_t nbins, double *out, int64_t *bin_count, double *bin_mean,
                       double *bin_sd, void *workspace, size_t ws_bytes, void *stream);
+
+/* The steps of selscan_normalize, for scores spread over several calls or
+ * GPUs (the shards of one genome): per-bin sums over one shard, then totals
+ * summed across shards by the caller (e.g. an all-reduce), then the bin
+ * statistics, then the scores.  Bins, statuses and the NaN rules are those
+ * of selscan_normalize; the sums are deterministic within a shard, so a
+ * split into shards changes only the order of the additions (the results
+ * agree with one call to rounding).  Sequence, with totals summed across
+ * shards after each bin_sums call:
+ *   selscan_normalize_bin_sums(pass 0) -> bin_count [nbins], bin_sum = the
+ *     shard's sum of its OK scores per bin
+ *   selscan_normalize_finish(pass 0, totals) -> bin_mean
+ *   selscan_normalize_bin_sums(pass 1, bin_mean) -> bin_sum = the shard's sum
+ *     of squared deviations about the mean (bin_count is not written)
+ *   selscan_normalize_finish(pass 1, totals) -> bin_sd (sample SD)
+ *   selscan_normalize_apply(shard scores, bin statistics) -> out [m]
+ * All arrays are device memory; bin_sums takes a workspace of
+ * selscan_normalize_workspace_bytes(nbins) bytes (256-byte aligned). */
+int selscan_normalize_bin_sums(const double *score, const int8_t *status, const int32_t *n1,
+                               int64_t m, int32_t n, int32_t nbins, int32_t pass,
+                               const double *bin_mean, int64_t *bin_count, double *bin_sum,
+                               void *workspace, size_t ws_bytes, void *stream);
+int selscan_normalize_finish(int32_t nbins, int32_t pass, const int64_t *bin_count,
+                             const double *bin_sum, double *bin_mean, double *bin_sd, void *stream);
+int selscan_normalize_apply(const double *score, const int8_t *status, const int32_t *n1,
+                            int64_t m, int32_t n, int32_t nbins, const int64_t *bin_count,
+                            const double *bin_mean, const double *bin_sd, double *out, void *stream);
 
 /* Pack a 0/1 uint8 matrix into rows (Section 1.1 coding, 0 ancestral / 1
  * derived).  hap_major = 0: hap01 is [m][n] (marker-major); 1: [n][m].

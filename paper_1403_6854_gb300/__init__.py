@@ -77,6 +77,8 @@ class selscan_scan(ctypes.Structure):
 
 
 EXPORTS = ("selscan_default_params", "selscan_workspace_bytes", "selscan_ihs", "selscan_xpehh",
+           "selscan_ihs_range", "selscan_xpehh_range", "selscan_normalize_bin_sums",
+           "selscan_normalize_finish", "selscan_normalize_apply",
            "selscan_ehh", "selscan_ehh_noalloc", "selscan_pack", "selscan_strerror",
            "selscan_batch_item_bytes", "selscan_batch_workspace_bytes", "selscan_batch_prepare",
            "selscan_batch_run", "selscan_batch_finalize", "selscan_launch_count",
@@ -110,6 +112,27 @@ def load_library():
                                   ctypes.c_int64, _P, _P, ctypes.POINTER(selscan_params),
                                   ctypes.POINTER(selscan_xpehh_out), _P, ctypes.c_size_t,
                                   ctypes.POINTER(selscan_launch), _P]
+    lib.selscan_ihs_range.restype = ctypes.c_int
+    lib.selscan_ihs_range.argtypes = [_P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int64,
+                                      ctypes.c_int64, ctypes.c_int64, _P, _P,
+                                      ctypes.POINTER(selscan_params),
+                                      ctypes.POINTER(selscan_ihs_out), _P, ctypes.c_size_t,
+                                      ctypes.POINTER(selscan_launch), _P]
+    lib.selscan_xpehh_range.restype = ctypes.c_int
+    lib.selscan_xpehh_range.argtypes = [_P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                        ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, _P, _P,
+                                        ctypes.POINTER(selscan_params),
+                                        ctypes.POINTER(selscan_xpehh_out), _P, ctypes.c_size_t,
+                                        ctypes.POINTER(selscan_launch), _P]
+    lib.selscan_normalize_bin_sums.restype = ctypes.c_int
+    lib.selscan_normalize_bin_sums.argtypes = [_P, _P, _P, ctypes.c_int64, ctypes.c_int32,
+                                               ctypes.c_int32, ctypes.c_int32, _P, _P, _P, _P,
+                                               ctypes.c_size_t, _P]
+    lib.selscan_normalize_finish.restype = ctypes.c_int
+    lib.selscan_normalize_finish.argtypes = [ctypes.c_int32, ctypes.c_int32, _P, _P, _P, _P, _P]
+    lib.selscan_normalize_apply.restype = ctypes.c_int
+    lib.selscan_normalize_apply.argtypes = [_P, _P, _P, ctypes.c_int64, ctypes.c_int32,
+                                            ctypes.c_int32, _P, _P, _P, _P, _P]
     lib.selscan_ehh.restype = ctypes.c_int
     lib.selscan_ehh.argtypes = [_P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int64, _P, _P,
                                 ctypes.c_int64, ctypes.POINTER(selscan_params),
@@ -241,6 +264,49 @@ def selscan_normalize(score: torch.Tensor, status: torch.Tensor, n1: torch.Tenso
     return out
 
 
+def selscan_normalize_bin_sums(score: torch.Tensor, status: torch.Tensor, n1: torch.Tensor, n: int,
+                               nbins: int, pass_: int, bin_mean: Optional[torch.Tensor] = None,
+                               stream=None, workspace: Optional[torch.Tensor] = None):
+    """One shard's per-bin sums: pass 0 -> (count int64 [nbins], sum of scores);
+    pass 1 -> (None, sum of squared deviations about bin_mean)."""
+    lib = load_library()
+    dev = score.device
+    cnt = torch.empty(nbins, dtype=torch.int64, device=dev) if pass_ == 0 else None
+    sm = torch.empty(nbins, dtype=torch.float64, device=dev)
+    ws = _workspace(int(lib.selscan_normalize_workspace_bytes(nbins)), dev, workspace)
+    rc = lib.selscan_normalize_bin_sums(_ptr(score), _ptr(status), _ptr(n1), score.numel(), n, nbins,
+                                        pass_, _ptr(bin_mean), _ptr(cnt), _ptr(sm), _ptr(ws),
+                                        ws.numel(), _stream(stream))
+    if rc != OK:
+        raise SelscanError(rc, "selscan_normalize_bin_sums")
+    return cnt, sm
+
+
+def selscan_normalize_finish(nbins: int, pass_: int, bin_count: torch.Tensor, bin_sum: torch.Tensor,
+                             stream=None) -> torch.Tensor:
+    """Bin means (pass 0) or sample SDs (pass 1) from totals over all shards."""
+    out = torch.empty(nbins, dtype=torch.float64, device=bin_sum.device)
+    rc = load_library().selscan_normalize_finish(
+        nbins, pass_, _ptr(bin_count), _ptr(bin_sum), _ptr(out) if pass_ == 0 else None,
+        _ptr(out) if pass_ == 1 else None, _stream(stream))
+    if rc != OK:
+        raise SelscanError(rc, "selscan_normalize_finish")
+    return out
+
+
+def selscan_normalize_apply(score: torch.Tensor, status: torch.Tensor, n1: torch.Tensor, n: int,
+                            nbins: int, bin_count: torch.Tensor, bin_mean: torch.Tensor,
+                            bin_sd: torch.Tensor, stream=None) -> torch.Tensor:
+    """Standardised scores of one shard from the genome-wide bin statistics."""
+    out = torch.empty(score.numel(), dtype=torch.float64, device=score.device)
+    rc = load_library().selscan_normalize_apply(_ptr(score), _ptr(status), _ptr(n1), score.numel(),
+                                                n, nbins, _ptr(bin_count), _ptr(bin_mean),
+                                                _ptr(bin_sd), _ptr(out), _stream(stream))
+    if rc != OK:
+        raise SelscanError(rc, "selscan_normalize_apply")
+    return out
+
+
 def selscan_default_schedule(n_total: int, m: int, mode: int) -> int:
     """Schedule a default launch takes for this scan shape (-1: bad arguments)."""
     return int(load_library().selscan_default_schedule(n_total, m, mode))
@@ -285,33 +351,60 @@ def _as_rows(hap: torch.Tensor) -> torch.Tensor:
     return hap
 
 
+def _ihs_outputs(k: int, dev) -> Dict[str, torch.Tensor]:
+    return dict(status=torch.empty(k, dtype=torch.int8, device=dev),
+                n1=torch.empty(k, dtype=torch.int32, device=dev),
+                ihh1=torch.empty(k, dtype=torch.float64, device=dev),
+                ihh0=torch.empty(k, dtype=torch.float64, device=dev),
+                lnratio=torch.empty(k, dtype=torch.float64, device=dev),
+                stop=torch.empty((k, 4), dtype=torch.int32, device=dev),
+                digest=torch.empty((k, 4), dtype=torch.int64, device=dev),
+                error=torch.zeros(1, dtype=torch.int32, device=dev))
+
+
+def _xpehh_outputs(k: int, dev) -> Dict[str, torch.Tensor]:
+    return dict(status=torch.empty(k, dtype=torch.int8, device=dev),
+                n1=torch.empty(k, dtype=torch.int32, device=dev),
+                ihhA=torch.empty(k, dtype=torch.float64, device=dev),
+                ihhB=torch.empty(k, dtype=torch.float64, device=dev),
+                lnratio=torch.empty(k, dtype=torch.float64, device=dev),
+                stop=torch.empty((k, 2), dtype=torch.int32, device=dev),
+                digest=torch.empty((k, 6), dtype=torch.int64, device=dev),
+                error=torch.zeros(1, dtype=torch.int32, device=dev))
+
+
 def selscan_ihs(hap: torch.Tensor, n: int, pos: torch.Tensor, gmap: torch.Tensor,
                 params: Optional[selscan_params] = None, launch: Optional[selscan_launch] = None,
                 stream=None, workspace: Optional[torch.Tensor] = None,
                 out: Optional[Dict[str, torch.Tensor]] = None) -> Dict[str, torch.Tensor]:
     """iHS at every marker; returns device tensors (valid after stream sync)."""
+    return selscan_ihs_range(hap, n, pos, gmap, 0, hap.shape[0], params, launch, stream,
+                             workspace, out)
+
+
+def selscan_ihs_range(hap: torch.Tensor, n: int, pos: torch.Tensor, gmap: torch.Tensor, k0: int,
+                      k1: int, params: Optional[selscan_params] = None,
+                      launch: Optional[selscan_launch] = None, stream=None,
+                      workspace: Optional[torch.Tensor] = None,
+                      out: Optional[Dict[str, torch.Tensor]] = None) -> Dict[str, torch.Tensor]:
+    """iHS at the cores [k0, k1) (outputs of k1 - k0 entries); the whole
+    matrix is read by the walks."""
     lib = load_library()
     hap = _as_rows(hap)
     m, ld = hap.shape
     dev = hap.device
     if out is None:
-        out = dict(status=torch.empty(m, dtype=torch.int8, device=dev),
-                   n1=torch.empty(m, dtype=torch.int32, device=dev),
-                   ihh1=torch.empty(m, dtype=torch.float64, device=dev),
-                   ihh0=torch.empty(m, dtype=torch.float64, device=dev),
-                   lnratio=torch.empty(m, dtype=torch.float64, device=dev),
-                   stop=torch.empty((m, 4), dtype=torch.int32, device=dev),
-                   digest=torch.empty((m, 4), dtype=torch.int64, device=dev),
-                   error=torch.zeros(1, dtype=torch.int32, device=dev))
+        out = _ihs_outputs(max(k1 - k0, 0), dev)
     p = params if params is not None else selscan_default_params()
-    ws = _workspace(selscan_workspace_bytes(n, m, MODE_IHS, launch), dev, workspace)
+    ws = _workspace(selscan_workspace_bytes(n, max(k1 - k0, 1), MODE_IHS, launch), dev, workspace)
     o = selscan_ihs_out(*(_ptr(out[f]) for f in ("status", "n1", "ihh1", "ihh0", "lnratio",
                                                   "stop", "digest", "error")))
-    rc = lib.selscan_ihs(_ptr(hap), ld, n, m, _ptr(pos), _ptr(gmap), ctypes.byref(p),
-                         ctypes.byref(o), _ptr(ws), ws.numel(),
-                         ctypes.byref(launch) if launch is not None else None, _stream(stream))
+    rc = lib.selscan_ihs_range(_ptr(hap), ld, n, m, k0, k1, _ptr(pos), _ptr(gmap), ctypes.byref(p),
+                               ctypes.byref(o), _ptr(ws), ws.numel(),
+                               ctypes.byref(launch) if launch is not None else None,
+                               _stream(stream))
     if rc != OK:
-        raise SelscanError(rc, "selscan_ihs")
+        raise SelscanError(rc, "selscan_ihs_range" if (k0, k1) != (0, m) else "selscan_ihs")
     out["_workspace"] = ws
     return out
 
@@ -322,28 +415,34 @@ def selscan_xpehh(hap: torch.Tensor, nA: int, nB: int, pos: torch.Tensor, gmap: 
                   workspace: Optional[torch.Tensor] = None,
                   out: Optional[Dict[str, torch.Tensor]] = None) -> Dict[str, torch.Tensor]:
     """XPEHH at every marker; rows hold W_A words of A then W_B words of B."""
+    return selscan_xpehh_range(hap, nA, nB, pos, gmap, 0, hap.shape[0], params, launch, stream,
+                               workspace, out)
+
+
+def selscan_xpehh_range(hap: torch.Tensor, nA: int, nB: int, pos: torch.Tensor,
+                        gmap: torch.Tensor, k0: int, k1: int,
+                        params: Optional[selscan_params] = None,
+                        launch: Optional[selscan_launch] = None, stream=None,
+                        workspace: Optional[torch.Tensor] = None,
+                        out: Optional[Dict[str, torch.Tensor]] = None) -> Dict[str, torch.Tensor]:
+    """XPEHH at the cores [k0, k1) (outputs of k1 - k0 entries)."""
     lib = load_library()
     hap = _as_rows(hap)
     m, ld = hap.shape
     dev = hap.device
     if out is None:
-        out = dict(status=torch.empty(m, dtype=torch.int8, device=dev),
-                   n1=torch.empty(m, dtype=torch.int32, device=dev),
-                   ihhA=torch.empty(m, dtype=torch.float64, device=dev),
-                   ihhB=torch.empty(m, dtype=torch.float64, device=dev),
-                   lnratio=torch.empty(m, dtype=torch.float64, device=dev),
-                   stop=torch.empty((m, 2), dtype=torch.int32, device=dev),
-                   digest=torch.empty((m, 6), dtype=torch.int64, device=dev),
-                   error=torch.zeros(1, dtype=torch.int32, device=dev))
+        out = _xpehh_outputs(max(k1 - k0, 0), dev)
     p = params if params is not None else selscan_default_params()
-    ws = _workspace(selscan_workspace_bytes(nA + nB, m, MODE_XPEHH, launch), dev, workspace)
+    ws = _workspace(selscan_workspace_bytes(nA + nB, max(k1 - k0, 1), MODE_XPEHH, launch), dev,
+                    workspace)
     o = selscan_xpehh_out(*(_ptr(out[f]) for f in ("status", "n1", "ihhA", "ihhB", "lnratio",
                                                     "stop", "digest", "error")))
-    rc = lib.selscan_xpehh(_ptr(hap), ld, nA, nB, m, _ptr(pos), _ptr(gmap), ctypes.byref(p),
-                           ctypes.byref(o), _ptr(ws), ws.numel(),
-                           ctypes.byref(launch) if launch is not None else None, _stream(stream))
+    rc = lib.selscan_xpehh_range(_ptr(hap), ld, nA, nB, m, k0, k1, _ptr(pos), _ptr(gmap),
+                                 ctypes.byref(p), ctypes.byref(o), _ptr(ws), ws.numel(),
+                                 ctypes.byref(launch) if launch is not None else None,
+                                 _stream(stream))
     if rc != OK:
-        raise SelscanError(rc, "selscan_xpehh")
+        raise SelscanError(rc, "selscan_xpehh_range" if (k0, k1) != (0, m) else "selscan_xpehh")
     out["_workspace"] = ws
     return out
 

@@ -272,14 +272,27 @@ Scratch make_scratch(unsigned char *ws, const Layout &l, int n_total, const Plan
     return sc;
 }
 
+// Device pointer to element -k of p: the kernels index per-core outputs by
+// the global core k in [k0, k1), and an output array of k1 - k0 entries starts
+// at core k0.  Only addresses of the caller's array are ever formed from it.
+template <typename T>
+inline T *at_core(T *p, long long k, long long per_core = 1)
+{
+    return (T *)((uintptr_t)p - (uintptr_t)(k * per_core) * sizeof(T));
+}
+
+// One scan of the cores [k0, k1) of an m-marker chromosome (a whole scan: k0
+// = 0, k1 = m).  Outputs hold k1 - k0 cores; the plan and the workspace are
+// those of a scan of k1 - k0 cores; walks still reach every marker.
 int run_scan(int mode, const uint64_t *hap, int64_t ld, int32_t nA, int32_t nB, int64_t m,
-             const int64_t *pos, const double *gmap, const selscan_params *p, int8_t *status,
-             int32_t *n1, int32_t *stop, uint64_t *digest, int32_t *err, double *o1, double *o2,
-             double *lnratio, void *workspace, size_t ws_bytes, const selscan_launch *launch,
-             void *stream)
+             int64_t k0, int64_t k1, const int64_t *pos, const double *gmap,
+             const selscan_params *p, int8_t *status, int32_t *n1, int32_t *stop,
+             uint64_t *digest, int32_t *err, double *o1, double *o2, double *lnratio,
+             void *workspace, size_t ws_bytes, const selscan_launch *launch, void *stream)
 {
     const int n_total = nA + nB;
-    const Plan plan = make_plan(mode, ld, launch, n_total, m);
+    const long long ncores = k1 - k0;
+    const Plan plan = make_plan(mode, ld, launch, n_total, ncores);
     if (plan.schedule < 0 || (launch && launch->warps_per_cta < 0)) return SELSCAN_ERR_INVALID_ARG;
     if (smem_per_warp(plan.cap_s, plan.tcap_s, plan.rowcap, plan.poscap) * (size_t)plan.wpc > kMaxSmemPerCta)
         return SELSCAN_ERR_UNSUPPORTED;
@@ -288,17 +301,27 @@ int run_scan(int mode, const uint64_t *hap, int64_t ld, int32_t nA, int32_t nB, 
                   (size_t)plan.sw.split_bytes * (kSplitWarps * 32 / plan.sw.split_tile) > kMaxSmemPerCta))
         return SELSCAN_ERR_UNSUPPORTED;
     if (sweep && (plan.sw.slot_bytes & 15)) return SELSCAN_ERR_UNSUPPORTED;   // slots are read in 16-byte units
-    const Layout l = make_layout(n_total, m, mode, plan.nslots, sweep ? &plan.sw : nullptr);
+    const Layout l = make_layout(n_total, ncores, mode, plan.nslots, sweep ? &plan.sw : nullptr);
     if (!workspace || ws_bytes < l.total || ((uintptr_t)workspace & 255)) return SELSCAN_ERR_WORKSPACE;
     cudaStream_t s = (cudaStream_t)stream;
     unsigned char *ws = (unsigned char *)workspace;
 
-    const ScanArgs a = make_args(hap, ld, nA, nB, m, pos, gmap, p);
+    ScanArgs a = make_args(hap, ld, nA, nB, m, pos, gmap, p);
+    a.k0 = k0;
+    a.k1 = k1;
+    const int ipc = mode == SELSCAN_MODE_XPEHH ? 2 : 4;
+    status = at_core(status, k0);
+    n1 = at_core(n1, k0);
+    stop = at_core(stop, k0, ipc);
+    digest = at_core(digest, k0, mode == SELSCAN_MODE_XPEHH ? 6 : 4);
+    o1 = at_core(o1, k0);
+    o2 = at_core(o2, k0);
+    lnratio = at_core(lnratio, k0);
     ItemSink sk;
     sk.mode = mode == SELSCAN_MODE_XPEHH ? 1 : 0;
     sk.core_status = status;
-    sk.item_status = (int8_t *)(ws + l.item_status);
-    sk.item_ihh = (double *)(ws + l.item_ihh);
+    sk.item_status = at_core((int8_t *)(ws + l.item_status), k0, ipc);
+    sk.item_ihh = at_core((double *)(ws + l.item_ihh), k0, 4);   // four sums per core either mode
     sk.stop = stop;
     sk.digest = (unsigned long long *)digest;
     sk.list2 = (uint32_t *)(ws + l.list2);
@@ -348,16 +371,16 @@ int run_scan(int mode, const uint64_t *hap, int64_t ld, int32_t nA, int32_t nB, 
         if (launch_pass2(a, sk, sc, plan.wpc, plan.ctas, plan.minb, s) != cudaSuccess)
             return SELSCAN_ERR_CUDA;
     } else if (launch_walk(a, sk, sc, plan.schedule, plan.wpc, ctas_or_slots, plan.probe, plan.fetch,
-                           plan.minb, m, s) != cudaSuccess) {
+                           plan.minb, ncores, s) != cudaSuccess) {
         return SELSCAN_ERR_CUDA;
     }
     if (launch && launch->walk_end_event &&
         cudaEventRecord((cudaEvent_t)launch->walk_end_event, s) != cudaSuccess)
         return SELSCAN_ERR_CUDA;
     if (sk.mode == 1)
-        e = launch_finalize_xpehh(sk, m, o1, o2, lnratio, status, s);
+        e = launch_finalize_xpehh(sk, k0, k1, o1, o2, lnratio, status, s);
     else
-        e = launch_finalize_ihs(sk, m, o1, o2, lnratio, status, s);
+        e = launch_finalize_ihs(sk, k0, k1, o1, o2, lnratio, status, s);
     return e == cudaSuccess ? SELSCAN_OK : SELSCAN_ERR_CUDA;
 }
 
@@ -456,19 +479,47 @@ int32_t selscan_launch_count(int32_t n_total, int64_t m, int32_t mode, const sel
     }
 }
 
-int selscan_ihs(const uint64_t *hap, int64_t ld, int32_t n, int64_t m, const int64_t *pos_bp,
-                const double *gmap, const selscan_params *p, const selscan_ihs_out *out,
-                void *workspace, size_t ws_bytes, const selscan_launch *launch, void *stream)
+int selscan_ihs_range(const uint64_t *hap, int64_t ld, int32_t n, int64_t m, int64_t k0,
+                      int64_t k1, const int64_t *pos_bp, const double *gmap,
+                      const selscan_params *p, const selscan_ihs_out *out, void *workspace,
+                      size_t ws_bytes, const selscan_launch *launch, void *stream)
 {
     if (!hap || !pos_bp || !gmap || !out || !params_ok(p)) return SELSCAN_ERR_INVALID_ARG;
     if (n < 2 || n > kMaxHaplotypes || m < 1 || m >= (1ll << 30) || ld < (n + 63) / 64)
         return SELSCAN_ERR_INVALID_ARG;
+    if (k0 < 0 || k1 <= k0 || k1 > m) return SELSCAN_ERR_INVALID_ARG;
     if (!out->status || !out->n1 || !out->ihh1 || !out->ihh0 || !out->lnratio || !out->stop ||
         !out->digest || !out->error)
         return SELSCAN_ERR_INVALID_ARG;
-    return run_scan(SELSCAN_MODE_IHS, hap, ld, n, 0, m, pos_bp, gmap, p, out->status, out->n1,
-                    out->stop, out->digest, out->error, out->ihh1, out->ihh0, out->lnratio,
+    return run_scan(SELSCAN_MODE_IHS, hap, ld, n, 0, m, k0, k1, pos_bp, gmap, p, out->status,
+                    out->n1, out->stop, out->digest, out->error, out->ihh1, out->ihh0, out->lnratio,
                     workspace, ws_bytes, launch, stream);
+}
+
+int selscan_ihs(const uint64_t *hap, int64_t ld, int32_t n, int64_t m, const int64_t *pos_bp,
+                const double *gmap, const selscan_params *p, const selscan_ihs_out *out,
+                void *workspace, size_t ws_bytes, const selscan_launch *launch, void *stream)
+{
+    return selscan_ihs_range(hap, ld, n, m, 0, m, pos_bp, gmap, p, out, workspace, ws_bytes, launch,
+                             stream);
+}
+
+int selscan_xpehh_range(const uint64_t *hap, int64_t ld, int32_t nA, int32_t nB, int64_t m,
+                        int64_t k0, int64_t k1, const int64_t *pos_bp, const double *gmap,
+                        const selscan_params *p, const selscan_xpehh_out *out, void *workspace,
+                        size_t ws_bytes, const selscan_launch *launch, void *stream)
+{
+    if (!hap || !pos_bp || !gmap || !out || !params_ok(p)) return SELSCAN_ERR_INVALID_ARG;
+    if (nA < 2 || nB < 2 || (long long)nA + nB > kMaxHaplotypes || m < 1 || m >= (1ll << 30) ||
+        ld < (nA + 63) / 64 + (nB + 63) / 64)
+        return SELSCAN_ERR_INVALID_ARG;
+    if (k0 < 0 || k1 <= k0 || k1 > m) return SELSCAN_ERR_INVALID_ARG;
+    if (!out->status || !out->n1 || !out->ihhA || !out->ihhB || !out->lnratio || !out->stop ||
+        !out->digest || !out->error)
+        return SELSCAN_ERR_INVALID_ARG;
+    return run_scan(SELSCAN_MODE_XPEHH, hap, ld, nA, nB, m, k0, k1, pos_bp, gmap, p, out->status,
+                    out->n1, out->stop, out->digest, out->error, out->ihhA, out->ihhB,
+                    out->lnratio, workspace, ws_bytes, launch, stream);
 }
 
 int selscan_xpehh(const uint64_t *hap, int64_t ld, int32_t nA, int32_t nB, int64_t m,
@@ -476,16 +527,8 @@ int selscan_xpehh(const uint64_t *hap, int64_t ld, int32_t nA, int32_t nB, int64
                   const selscan_xpehh_out *out, void *workspace, size_t ws_bytes,
                   const selscan_launch *launch, void *stream)
 {
-    if (!hap || !pos_bp || !gmap || !out || !params_ok(p)) return SELSCAN_ERR_INVALID_ARG;
-    if (nA < 2 || nB < 2 || (long long)nA + nB > kMaxHaplotypes || m < 1 || m >= (1ll << 30) ||
-        ld < (nA + 63) / 64 + (nB + 63) / 64)
-        return SELSCAN_ERR_INVALID_ARG;
-    if (!out->status || !out->n1 || !out->ihhA || !out->ihhB || !out->lnratio || !out->stop ||
-        !out->digest || !out->error)
-        return SELSCAN_ERR_INVALID_ARG;
-    return run_scan(SELSCAN_MODE_XPEHH, hap, ld, nA, nB, m, pos_bp, gmap, p, out->status, out->n1,
-                    out->stop, out->digest, out->error, out->ihhA, out->ihhB, out->lnratio,
-                    workspace, ws_bytes, launch, stream);
+    return selscan_xpehh_range(hap, ld, nA, nB, m, 0, m, pos_bp, gmap, p, out, workspace, ws_bytes,
+                               launch, stream);
 }
 
 int selscan_ehh(const uint64_t *hap, int64_t ld, int32_t n, int64_t m, const int64_t *pos_bp,

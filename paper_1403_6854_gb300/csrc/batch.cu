@@ -130,6 +130,8 @@ BatchDesc make_desc(const selscan_scan *s)
     a.hap = (const unsigned long long *)s->hap;
     a.ld = s->ld;
     a.m = s->m;
+    a.k0 = 0;                 // ticks name their own core ranges; outputs span the scan
+    a.k1 = s->m;
     a.pos = (const long long *)s->pos_bp;
     a.gmap = s->gmap;
     a.WA = (s->nA + 63) / 64;
@@ -293,10 +295,10 @@ int selscan_batch_finalize(const selscan_scan *s, void *stream)
     const BatchDesc d = make_desc(s);
     cudaError_t e;
     if (s->mode == SELSCAN_MODE_XPEHH)
-        e = launch_finalize_xpehh(d.sk, s->m, s->ihh_a, s->ihh_b, s->lnratio, s->status,
+        e = launch_finalize_xpehh(d.sk, 0, s->m, s->ihh_a, s->ihh_b, s->lnratio, s->status,
                                   (cudaStream_t)stream);
     else
-        e = launch_finalize_ihs(d.sk, s->m, s->ihh_a, s->ihh_b, s->lnratio, s->status,
+        e = launch_finalize_ihs(d.sk, 0, s->m, s->ihh_a, s->ihh_b, s->lnratio, s->status,
                                 (cudaStream_t)stream);
     return e == cudaSuccess ? SELSCAN_OK : SELSCAN_ERR_CUDA;
 }

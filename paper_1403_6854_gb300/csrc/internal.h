@@ -86,9 +86,10 @@ cudaError_t launch_core_select(const ScanArgs &a, int mode, unsigned maf_num, un
 cudaError_t launch_walk(const ScanArgs &a, const ItemSink &sink, const Scratch &sc,
                         int schedule, int warps_per_cta, int ctas, int probe_steps, int fetch,
                         int minb, long long n_items, cudaStream_t s);
-cudaError_t launch_finalize_ihs(const ItemSink &sink, long long m, double *ihh1, double *ihh0,
-                                double *lnratio, int8_t *status, cudaStream_t s);
-cudaError_t launch_finalize_xpehh(const ItemSink &sink, long long m, double *ihhA,
+// per-core results of cores [k0, k1) (iHH_c = down + up, status, ln ratio)
+cudaError_t launch_finalize_ihs(const ItemSink &sink, long long k0, long long k1, double *ihh1,
+                                double *ihh0, double *lnratio, int8_t *status, cudaStream_t s);
+cudaError_t launch_finalize_xpehh(const ItemSink &sink, long long k0, long long k1, double *ihhA,
                                   double *ihhB, double *lnratio, int8_t *status, cudaStream_t s);
 cudaError_t launch_ehh(const ScanArgs &a, long long locus, const Scratch &sc,
                        unsigned long long *S, long long cap, long long *len, int32_t *stop,

@@ -47,7 +47,7 @@ __global__ void core_select_kernel(ScanArgs a, int mode, unsigned maf_num, unsig
     const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
     const unsigned n_total = (unsigned)(a.nA + a.nB);
-    for (long long k = warp; k < a.m; k += nw) {
+    for (long long k = a.k0 + warp; k < a.k1; k += nw) {
         const unsigned int *row = (const unsigned int *)(a.hap + k * a.ld);
         unsigned c = 0;
         for (int w = lane; w < 2 * a.W; w += 32) c += (unsigned)__popc(__ldg(row + w) & valid32(a, w));
@@ -65,8 +65,9 @@ __global__ void core_select_kernel(ScanArgs a, int mode, unsigned maf_num, unsig
 cudaError_t launch_core_select(const ScanArgs &a, int mode, unsigned maf_num, unsigned maf_den,
                                int maf_filter, int32_t *n1, int8_t *core_status, cudaStream_t s)
 {
-    long long blocks = (a.m * 32 + 255) / 256;
+    long long blocks = ((a.k1 - a.k0) * 32 + 255) / 256;
     if (blocks > 8192) blocks = 8192;
+    if (blocks < 1) blocks = 1;
     core_select_kernel<<<(unsigned)blocks, 256, 0, s>>>(a, mode, maf_num, maf_den, maf_filter,
                                                          n1, core_status);
     return cudaGetLastError();
@@ -105,7 +106,8 @@ __global__ void __launch_bounds__(256, MINB) walk_persistent_kernel(ScanArgs a, 
             continue;
         }
         const unsigned long long end = idx + step < total ? idx + step : total;
-        for (unsigned long long c = idx; c < end; ++c) {
+        for (unsigned long long c = (unsigned long long)a.k0 + idx; c < (unsigned long long)a.k0 + end;
+             ++c) {
             if (sk.core_status[c] == (int8_t)SELSCAN_LOCUS_MAF_FILTERED) continue;
             for (int q = 0; q < ipc; ++q)
                 if (!run_item<NPOP>(a, sk, b, (uint32_t)(c * ipc + q), max_steps, wpar)) return;
@@ -122,7 +124,7 @@ __global__ void __launch_bounds__(128) walk_plain_kernel(ScanArgs a, ItemSink sk
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    const long long core = blockIdx.x;
+    const long long core = a.k0 + blockIdx.x;
     if (sk.core_status[core] == (int8_t)SELSCAN_LOCUS_MAF_FILTERED) return;
     int slot = -1;
     if (lane == 0) {
@@ -336,10 +338,10 @@ cudaError_t launch_walk(const ScanArgs &a, const ItemSink &sink, const Scratch &
 }
 
 // ------------------------------------------------------------ finalize
-__global__ void finalize_ihs_kernel(ItemSink sk, long long m, double *ihh1, double *ihh0,
+__global__ void finalize_ihs_kernel(ItemSink sk, long long k0, long long k1, double *ihh1, double *ihh0,
                                     double *lnratio, int8_t *status)
 {
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < m;
+    for (long long c = k0 + blockIdx.x * (long long)blockDim.x + threadIdx.x; c < k1;
          c += (long long)gridDim.x * blockDim.x) {
         if (sk.core_status[c] == (int8_t)SELSCAN_LOCUS_MAF_FILTERED) {
             ihh1[c] = 0.0;
@@ -363,10 +365,10 @@ __global__ void finalize_ihs_kernel(ItemSink sk, long long m, double *ihh1, doub
     }
 }
 
-__global__ void finalize_xpehh_kernel(ItemSink sk, long long m, double *ihhA, double *ihhB,
+__global__ void finalize_xpehh_kernel(ItemSink sk, long long k0, long long k1, double *ihhA, double *ihhB,
                                       double *lnratio, int8_t *status)
 {
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < m;
+    for (long long c = k0 + blockIdx.x * (long long)blockDim.x + threadIdx.x; c < k1;
          c += (long long)gridDim.x * blockDim.x) {
         if (sk.core_status[c] == (int8_t)SELSCAN_LOCUS_MAF_FILTERED) {
             ihhA[c] = 0.0;
@@ -391,21 +393,23 @@ __global__ void finalize_xpehh_kernel(ItemSink sk, long long m, double *ihhA, do
     }
 }
 
-cudaError_t launch_finalize_ihs(const ItemSink &sink, long long m, double *ihh1, double *ihh0,
-                                double *lnratio, int8_t *status, cudaStream_t s)
+cudaError_t launch_finalize_ihs(const ItemSink &sink, long long k0, long long k1, double *ihh1,
+                                double *ihh0, double *lnratio, int8_t *status, cudaStream_t s)
 {
-    long long blocks = (m + 255) / 256;
+    long long blocks = (k1 - k0 + 255) / 256;
     if (blocks > 4096) blocks = 4096;
-    finalize_ihs_kernel<<<(unsigned)blocks, 256, 0, s>>>(sink, m, ihh1, ihh0, lnratio, status);
+    if (blocks < 1) blocks = 1;
+    finalize_ihs_kernel<<<(unsigned)blocks, 256, 0, s>>>(sink, k0, k1, ihh1, ihh0, lnratio, status);
     return cudaGetLastError();
 }
 
-cudaError_t launch_finalize_xpehh(const ItemSink &sink, long long m, double *ihhA,
+cudaError_t launch_finalize_xpehh(const ItemSink &sink, long long k0, long long k1, double *ihhA,
                                   double *ihhB, double *lnratio, int8_t *status, cudaStream_t s)
 {
-    long long blocks = (m + 255) / 256;
+    long long blocks = (k1 - k0 + 255) / 256;
     if (blocks > 4096) blocks = 4096;
-    finalize_xpehh_kernel<<<(unsigned)blocks, 256, 0, s>>>(sink, m, ihhA, ihhB, lnratio, status);
+    if (blocks < 1) blocks = 1;
+    finalize_xpehh_kernel<<<(unsigned)blocks, 256, 0, s>>>(sink, k0, k1, ihhA, ihhB, lnratio, status);
     return cudaGetLastError();
 }
 

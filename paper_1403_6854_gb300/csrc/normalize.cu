@@ -69,9 +69,10 @@ __global__ void __launch_bounds__(kNormThreads) norm_partial_kernel(
     }
 }
 
-__global__ void norm_combine_kernel(int nbins, int pass, const double *part_sum,
-                                    const long long *part_cnt, long long *bin_count,
-                                    double *bin_mean, double *bin_sd)
+// Per-bin totals of the segment partials, segments in order: pass 0 the
+// count and the sum, pass 1 the sum of squared deviations.
+__global__ void norm_sums_kernel(int nbins, int pass, const double *part_sum,
+                                 const long long *part_cnt, long long *bin_count, double *bin_sum)
 {
     for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nbins; b += gridDim.x * blockDim.x) {
         double s = 0.0;
@@ -80,12 +81,22 @@ __global__ void norm_combine_kernel(int nbins, int pass, const double *part_sum,
             s += part_sum[b * kNormSegments + seg];
             c += part_cnt[b * kNormSegments + seg];
         }
-        if (pass == 0) {
-            bin_count[b] = c;
+        bin_sum[b] = s;
+        if (pass == 0) bin_count[b] = c;
+    }
+}
+
+// Mean (pass 0) or sample SD (pass 1) of each bin from its totals.
+__global__ void norm_finish_kernel(int nbins, int pass, const long long *bin_count,
+                                   const double *bin_sum, double *bin_mean, double *bin_sd)
+{
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nbins; b += gridDim.x * blockDim.x) {
+        const long long c = bin_count[b];
+        const double s = bin_sum[b];
+        if (pass == 0)
             bin_mean[b] = c > 0 ? s / (double)c : __longlong_as_double(0x7ff8000000000000ll);
-        } else {
+        else
             bin_sd[b] = c > 1 ? sqrt(s / (double)(c - 1)) : __longlong_as_double(0x7ff8000000000000ll);
-        }
     }
 }
 
@@ -111,41 +122,112 @@ __global__ void norm_apply_kernel(const double *score, const int8_t *status, con
 
 using namespace selscan;
 
+namespace {
+
+size_t parts_bytes(int nbins)
+{
+    return ((size_t)nbins * kNormSegments * 8 + 255) & ~(size_t)255;
+}
+
+bool norm_args_ok(const double *score, const int8_t *status, const int32_t *n1, int64_t m,
+                  int32_t n, int32_t nbins)
+{
+    return score && status && n1 && m >= 1 && n >= 1 && nbins >= 1 && nbins <= SELSCAN_NORM_MAX_BINS;
+}
+
+// pass 0: bin_count and bin_sum (sum of the scores); pass 1: bin_sum = sum of
+// squared deviations about bin_mean.  part_sum / part_cnt: workspace.
+void launch_bin_sums(const double *score, const int8_t *status, const int32_t *n1, int64_t m,
+                     int32_t n, int32_t nbins, int pass, const double *bin_mean,
+                     long long *bin_count, double *bin_sum, double *part_sum, long long *part_cnt,
+                     cudaStream_t s)
+{
+    const unsigned grid = (unsigned)(nbins * kNormSegments);
+    norm_partial_kernel<<<grid, kNormThreads, 0, s>>>(score, status, n1, m, n, nbins, pass, bin_mean,
+                                                      part_sum, part_cnt);
+    norm_sums_kernel<<<(nbins + 127) / 128, 128, 0, s>>>(nbins, pass, part_sum, part_cnt, bin_count,
+                                                         bin_sum);
+}
+
+void launch_apply(const double *score, const int8_t *status, const int32_t *n1, int64_t m,
+                  int32_t n, int32_t nbins, const double *bin_mean, const double *bin_sd,
+                  const long long *bin_count, double *out, cudaStream_t s)
+{
+    long long blocks = (m + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    norm_apply_kernel<<<(unsigned)blocks, 256, 0, s>>>(score, status, n1, m, n, nbins, bin_mean,
+                                                       bin_sd, bin_count, out);
+}
+
+}  // namespace
+
 extern "C" {
 
 size_t selscan_normalize_workspace_bytes(int32_t nbins)
 {
     if (nbins < 1 || nbins > SELSCAN_NORM_MAX_BINS) return 0;
-    const size_t parts = (size_t)nbins * kNormSegments;
-    return ((parts * 8 + 255) & ~(size_t)255) * 2;
+    return parts_bytes(nbins) * 2 + (((size_t)nbins * 8 + 255) & ~(size_t)255);
 }
 
 int selscan_normalize(const double *score, const int8_t *status, const int32_t *n1, int64_t m,
                       int32_t n, int32_t nbins, double *out, int64_t *bin_count, double *bin_mean,
                       double *bin_sd, void *workspace, size_t ws_bytes, void *stream)
 {
-    if (!score || !status || !n1 || !out || !bin_count || !bin_mean || !bin_sd || m < 1 ||
-        n < 1 || nbins < 1 || nbins > SELSCAN_NORM_MAX_BINS)
+    if (!norm_args_ok(score, status, n1, m, n, nbins) || !out || !bin_count || !bin_mean || !bin_sd)
         return SELSCAN_ERR_INVALID_ARG;
     const size_t need = selscan_normalize_workspace_bytes(nbins);
     if (!workspace || ws_bytes < need || ((uintptr_t)workspace & 255)) return SELSCAN_ERR_WORKSPACE;
     cudaStream_t s = (cudaStream_t)stream;
-    const size_t half = need / 2;
     double *part_sum = (double *)workspace;
-    long long *part_cnt = (long long *)((unsigned char *)workspace + half);
-    const unsigned grid = (unsigned)(nbins * kNormSegments);
-    norm_partial_kernel<<<grid, kNormThreads, 0, s>>>(score, status, n1, m, n, nbins, 0, nullptr,
-                                                      part_sum, part_cnt);
-    norm_combine_kernel<<<(nbins + 127) / 128, 128, 0, s>>>(nbins, 0, part_sum, part_cnt,
-                                                           (long long *)bin_count, bin_mean, bin_sd);
-    norm_partial_kernel<<<grid, kNormThreads, 0, s>>>(score, status, n1, m, n, nbins, 1, bin_mean,
-                                                      part_sum, part_cnt);
-    norm_combine_kernel<<<(nbins + 127) / 128, 128, 0, s>>>(nbins, 1, part_sum, part_cnt,
-                                                           (long long *)bin_count, bin_mean, bin_sd);
-    long long blocks = (m + 255) / 256;
-    if (blocks > 4096) blocks = 4096;
-    norm_apply_kernel<<<(unsigned)blocks, 256, 0, s>>>(score, status, n1, m, n, nbins, bin_mean,
-                                                       bin_sd, (const long long *)bin_count, out);
+    long long *part_cnt = (long long *)((unsigned char *)workspace + parts_bytes(nbins));
+    double *bin_sum = (double *)((unsigned char *)workspace + 2 * parts_bytes(nbins));
+    long long *cnt = (long long *)bin_count;
+    for (int pass = 0; pass < 2; ++pass) {
+        launch_bin_sums(score, status, n1, m, n, nbins, pass, bin_mean, cnt, bin_sum, part_sum,
+                        part_cnt, s);
+        norm_finish_kernel<<<(nbins + 127) / 128, 128, 0, s>>>(nbins, pass, cnt, bin_sum, bin_mean,
+                                                               bin_sd);
+    }
+    launch_apply(score, status, n1, m, n, nbins, bin_mean, bin_sd, cnt, out, s);
+    return cudaGetLastError() == cudaSuccess ? SELSCAN_OK : SELSCAN_ERR_CUDA;
+}
+
+int selscan_normalize_bin_sums(const double *score, const int8_t *status, const int32_t *n1,
+                               int64_t m, int32_t n, int32_t nbins, int32_t pass,
+                               const double *bin_mean, int64_t *bin_count, double *bin_sum,
+                               void *workspace, size_t ws_bytes, void *stream)
+{
+    if (!norm_args_ok(score, status, n1, m, n, nbins) || !bin_sum || (pass != 0 && pass != 1) ||
+        (pass == 0 && !bin_count) || (pass == 1 && !bin_mean))
+        return SELSCAN_ERR_INVALID_ARG;
+    const size_t need = selscan_normalize_workspace_bytes(nbins);
+    if (!workspace || ws_bytes < need || ((uintptr_t)workspace & 255)) return SELSCAN_ERR_WORKSPACE;
+    double *part_sum = (double *)workspace;
+    long long *part_cnt = (long long *)((unsigned char *)workspace + parts_bytes(nbins));
+    launch_bin_sums(score, status, n1, m, n, nbins, pass, bin_mean, (long long *)bin_count, bin_sum,
+                    part_sum, part_cnt, (cudaStream_t)stream);
+    return cudaGetLastError() == cudaSuccess ? SELSCAN_OK : SELSCAN_ERR_CUDA;
+}
+
+int selscan_normalize_finish(int32_t nbins, int32_t pass, const int64_t *bin_count,
+                             const double *bin_sum, double *bin_mean, double *bin_sd, void *stream)
+{
+    if (nbins < 1 || nbins > SELSCAN_NORM_MAX_BINS || (pass != 0 && pass != 1) || !bin_count ||
+        !bin_sum || (pass == 0 && !bin_mean) || (pass == 1 && !bin_sd))
+        return SELSCAN_ERR_INVALID_ARG;
+    norm_finish_kernel<<<(nbins + 127) / 128, 128, 0, (cudaStream_t)stream>>>(
+        nbins, pass, (const long long *)bin_count, bin_sum, bin_mean, bin_sd);
+    return cudaGetLastError() == cudaSuccess ? SELSCAN_OK : SELSCAN_ERR_CUDA;
+}
+
+int selscan_normalize_apply(const double *score, const int8_t *status, const int32_t *n1,
+                            int64_t m, int32_t n, int32_t nbins, const int64_t *bin_count,
+                            const double *bin_mean, const double *bin_sd, double *out, void *stream)
+{
+    if (!norm_args_ok(score, status, n1, m, n, nbins) || !bin_count || !bin_mean || !bin_sd || !out)
+        return SELSCAN_ERR_INVALID_ARG;
+    launch_apply(score, status, n1, m, n, nbins, bin_mean, bin_sd, (const long long *)bin_count, out,
+                 (cudaStream_t)stream);
     return cudaGetLastError() == cudaSuccess ? SELSCAN_OK : SELSCAN_ERR_CUDA;
 }
 

@@ -158,9 +158,9 @@ __global__ void __launch_bounds__(T, T == 512 ? 2 : (T == 256 ? 3 : 512 / T)) sw
     const int dir = blockIdx.x / w.nch;          // 0: walks toward lower indices
     const int c = blockIdx.x % w.nch;
     const long long m = w.a.m;
-    const long long c0 = (long long)c * w.B;
-    if (c0 >= m) return;
-    const long long c1 = c0 + w.B < m ? c0 + w.B : m;
+    const long long c0 = w.a.k0 + (long long)c * w.B;   // chunk c covers cores [c0, c1) of [k0, k1)
+    if (c0 >= w.a.k1) return;
+    const long long c1 = c0 + w.B < w.a.k1 ? c0 + w.B : w.a.k1;
     long long klo, khi;                          // this stage's cores [klo, khi)
     if (dir == 0) {
         klo = c0 + (long long)w.stage * w.R;
@@ -743,9 +743,9 @@ __global__ void __launch_bounds__(kSplitWarps * 32, SPLIT_MIN_CTAS) split_walk_k
         const int r = (int)(gsl - cr * (unsigned)w.R);
         const int dir = cr >= (unsigned)w.nch ? 1 : 0;
         const int c = (int)(cr - (unsigned)dir * (unsigned)w.nch);
-        const long long c0 = (long long)c * w.B;
-        if (c0 >= m) continue;
-        const long long c1 = c0 + w.B < m ? c0 + w.B : m;
+        const long long c0 = w.a.k0 + (long long)c * w.B;
+        if (c0 >= w.a.k1) continue;
+        const long long c1 = c0 + w.B < w.a.k1 ? c0 + w.B : w.a.k1;
         long long k;
         if (dir == 0) {
             const long long klo = c0 + (long long)w.stage * w.R;

@@ -43,7 +43,10 @@ enum : int {
 struct ScanArgs {
     const unsigned long long *hap;  // rows, row k at hap + k * ld (64-bit words)
     long long ld;
-    long long m;
+    long long m;                     // markers (walks may reach any of them)
+    long long k0, k1;                // the cores of this call: [k0, k1) (a whole scan: [0, m));
+                                     // per-core outputs are indexed by the global core k,
+                                     // through pointers the host has offset by k0
     const long long *pos;
     const double *gmap;
     int W;                           // 64-bit words in use (iHS: W; XPEHH: W_A + W_B)

@@ -180,6 +180,21 @@ def generate(spec: ScanSpec, ld: Optional[int] = None) -> ScanData:
     return ScanData(spec, rows, pos, gmap)
 
 
+def sweep_cores(data: "ScanData", pop: int = 0) -> np.ndarray:
+    """Core marker of each planted sweep of population `pop`: the marker
+    nearest to the sweep's centre (the first of two equally near), the rule
+    synth.c plants the sweep's derived allele at."""
+    pos = data.pos
+    out = []
+    for c, _, _ in data.spec.pops[pop].sweeps:
+        k = int(np.searchsorted(pos, c, side="left"))
+        k = min(k, pos.size - 1)
+        if k > 0 and (c - pos[k - 1]) <= (pos[k] - c):
+            k -= 1
+        out.append(k)
+    return np.array(out, dtype=np.int64)
+
+
 # ---------------------------------------------------------------- workloads
 CHR22_GAP_FRACTIONS = (0.05, 0.15, 0.30, 0.45, 0.60, 0.70, 0.80, 0.90)
 CHR22_GAP_BP = (20_000, 20_001, 45_000, 120_000, 200_000, 200_001, 350_000, 3_000_000)
@@ -202,6 +217,17 @@ def spec(name: str, seed: int = 0) -> ScanSpec:
         return ScanSpec("xpehh", "xpehh", m, 35_000_000, seed,
                         [PopSpec(204, 30, [(17_500_000.0, 400_000.0, 0.6)]), PopSpec(210, 60)],
                         map_rate=1.2, map_spread=0.5, gaps=_chr22_gaps(m))
+    if name == "ihs200k":
+        # a smaller analogue of ihs1m whose sweep centres the oracle checks in
+        # full: 1,000 haplotypes x 200,000 SNPs on 50 Mb, 4 planted sweeps
+        m, L, ns = 200_000, 50_000_000, 4
+        sweeps = []
+        for k in range(ns):
+            width = 50_000.0 + 450_000.0 * uniform(seed, 1, k)
+            freq = 0.3 + 0.6 * uniform(seed, 2, k)
+            sweeps.append(((k + 0.5) / ns * L, width, freq))
+        return ScanSpec(name, "ihs", m, L, seed, [PopSpec(1000, 200, sweeps)],
+                        map_rate=1.2, map_spread=0.5)
     if name in ("ihs1m", "ihs250k"):
         # ihs250k: the same recipe on a quarter of the chromosome (5 sweeps), a
         # profiling-sized case whose matrix (158 MB) still exceeds L2

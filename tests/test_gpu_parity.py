@@ -297,13 +297,38 @@ def test_unsorted_input_sets_device_error(sg, plain):
     assert e.value.code == sg.ERR_UNSORTED
 
 
+def longest_walk_cores(got, k):
+    """The k walked cores with the largest sum of stop indices on the GPU (the
+    selection uses the GPU's output; the comparison is element by element)."""
+    walked = np.flatnonzero(got["status"] != 1)
+    tot = got["stop"][walked].astype(np.int64).sum(1)
+    return walked[np.argsort(-tot, kind="stable")[:k]]
+
+
+def sweep_region_cores(d, m, half=8):
+    """Every planted sweep's core marker and its neighbours within +-half markers."""
+    c = synth.sweep_cores(d)
+    near = (c[:, None] + np.arange(-half, half + 1)[None, :]).ravel()
+    return near[(near >= 0) & (near < m)]
+
+
 def test_1m_sampled_cores_and_invariants(sg):
+    """The bench's workload at full size (5,000 x 1,000,000, 20 planted
+    sweeps) in the default launch (the sorted sweep): 48 random cores, every
+    sweep centre with its +-8 neighbours (the long EHH tails the statistic is
+    about) and the 128 cores with the longest walks on the GPU match the
+    oracle element by element; properties hold at every core."""
     d = synth.generate(synth.spec("ihs1m"))
     got = run_ihs(sg, d.rows, 5000, d.pos, d.gmap)
     rng = np.random.default_rng(0)
-    cores = np.sort(rng.choice(d.spec.m, 48, replace=False))
+    cores = np.unique(np.concatenate([rng.choice(d.spec.m, 48, replace=False),
+                                      sweep_region_cores(d, d.spec.m),
+                                      longest_walk_cores(got, 128)]))
     ref = oracle.ihs(d.rows, 5000, d.pos, d.gmap, cores=cores)
     assert_ihs_equal(got, ref, idx=cores)
+    # the sweep centres walk hundreds of steps each way
+    centres = np.searchsorted(cores, synth.sweep_cores(d))
+    assert np.all(ref["stop"][centres, :2].min(1) > 100)
     # properties at every core
     st = got["status"]
     assert set(np.unique(st)) <= {0, 1, 2, 3, 4}
@@ -315,3 +340,23 @@ def test_1m_sampled_cores_and_invariants(sg):
     assert np.all(got["stop"][walked, 1] <= d.spec.m - idx[walked])
     n1 = synth.unpack(d.rows[:2000], 5000).sum(1)
     assert np.array_equal(got["n1"][:2000], n1)
+
+
+@pytest.mark.parametrize("schedule", ["default", "in_order"])
+def test_200k_every_sweep_centre(sg, schedule):
+    """1,000 haplotypes x 200,000 SNPs on 50 Mb with four planted sweeps (an
+    iHS analogue of the 200k XPEHH case): every sweep centre with its +-16
+    neighbours, 64 random cores and the 64 longest GPU walks match the oracle
+    in the default launch (the sorted sweep) and in the per-step schedule."""
+    d = synth.generate(synth.spec("ihs200k"))
+    L = None if schedule == "default" else sg.make_launch(sg.SCHED_IN_ORDER)
+    got = run_ihs(sg, d.rows, 1000, d.pos, d.gmap, launch=L)
+    rng = np.random.default_rng(3)
+    cores = np.unique(np.concatenate([rng.choice(d.spec.m, 64, replace=False),
+                                      sweep_region_cores(d, d.spec.m, half=16),
+                                      longest_walk_cores(got, 64)]))
+    ref = oracle.ihs(d.rows, 1000, d.pos, d.gmap, cores=cores)
+    assert_ihs_equal(got, ref, idx=cores)
+    centres = np.searchsorted(cores, synth.sweep_cores(d))
+    assert np.all(ref["status"][centres] == 0)
+    assert np.all(ref["stop"][centres, :2].min(1) > 100)

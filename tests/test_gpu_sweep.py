@@ -204,15 +204,29 @@ def test_haplotype_limit(sg, n):
     assert_ihs_equal(got, ref, idx=cores)
 
 
+def longest_walk_cores(got, k):
+    """The k cores with the largest sum of stop indices on the GPU."""
+    tot = got["stop"].astype(np.int64).sum(1)
+    return np.argsort(-tot, kind="stable")[:k]
+
+
+def sweep_region_cores(d, m, half):
+    c = synth.sweep_cores(d)
+    near = (c[:, None] + np.arange(-half, half + 1)[None, :]).ravel()
+    return near[(near >= 0) & (near < m)]
+
+
 def test_xpehh_at_scale_sampled_cores(sg):
     """1,000 + 1,000 haplotypes x 200,000 SNPs with four planted sweeps in A:
-    the default launch takes the sorted sweep; sampled cores (including the
-    sweep centres) match the oracle."""
+    the default launch takes the sorted sweep; random cores, every sweep
+    centre with its +-16 neighbours and the 64 longest GPU walks match the
+    oracle."""
     d = synth.generate(synth.spec("xpehh200k"))
     got = run_xpehh(sg, d.rows, 1000, 1000, d.pos, d.gmap)
     rng = np.random.default_rng(1)
-    centres = np.searchsorted(d.pos, [(k + 0.5) / 4 * 50_000_000 for k in range(4)])
-    cores = np.unique(np.concatenate([rng.choice(d.spec.m, 24, replace=False), centres]))
+    cores = np.unique(np.concatenate([rng.choice(d.spec.m, 24, replace=False),
+                                      sweep_region_cores(d, d.spec.m, 16),
+                                      longest_walk_cores(got, 64)]))
     ref = oracle.xpehh(d.rows, 1000, 1000, d.pos, d.gmap, cores=cores)
     assert_xpehh_equal(got, ref, idx=cores)
     assert np.array_equal(np.isfinite(got["lnratio"]), got["status"] == 0)
@@ -221,12 +235,15 @@ def test_xpehh_at_scale_sampled_cores(sg):
 def test_xpehh_1m_sampled_cores(sg):
     """The bench's XPEHH workload at full size (2,500 + 2,500 haplotypes x
     1,000,000 SNPs, 20 planted sweeps in A) in the launch the bench times (the
-    default: the sorted sweep): random cores match the oracle, and every locus
-    has a finite ratio exactly when it is OK."""
+    default: the sorted sweep): random cores, every sweep centre with its +-8
+    neighbours and the 128 longest GPU walks match the oracle, and every
+    locus has a finite ratio exactly when it is OK."""
     d = synth.generate(synth.spec("xpehh1m"))
     got = run_xpehh(sg, d.rows, 2500, 2500, d.pos, d.gmap)
     rng = np.random.default_rng(2)
-    cores = np.sort(rng.choice(d.spec.m, 24, replace=False))
+    cores = np.unique(np.concatenate([rng.choice(d.spec.m, 24, replace=False),
+                                      sweep_region_cores(d, d.spec.m, 8),
+                                      longest_walk_cores(got, 128)]))
     ref = oracle.xpehh(d.rows, 2500, 2500, d.pos, d.gmap, cores=cores)
     assert_xpehh_equal(got, ref, idx=cores)
     assert np.array_equal(np.isfinite(got["lnratio"]), got["status"] == 0)
