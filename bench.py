@@ -314,7 +314,7 @@ def main():
     value = cores_all * K / (ms_max / 1e3)
 
     # end to end: host buffers, H2D of the inputs and D2H of the scores every step
-    e2e = None
+    e2e, e2e_bufs = None, None
     if rank == 0 and not args.no_extras:
         h_rows = torch.from_numpy(d.rows.view(np.int64)).pin_memory()
         h_pos = torch.from_numpy(d.pos).pin_memory()
@@ -339,6 +339,7 @@ def main():
                "h2d_bytes_per_step": int(d.rows.nbytes + d.pos.nbytes + d.gmap.nbytes),
                "d2h_bytes_per_step": int(sum(r.numel() * r.element_size() for r in res.values())),
                "ms_per_step": e2e_s * 1e3}
+        e2e_bufs = (h_rows, h_pos, h_gmap, res, dh, dp, dg, o2)
 
     extras = {}
     if rank == 0 and world == 1 and not args.no_extras:
@@ -357,6 +358,10 @@ def main():
                                        "deterministic two-pass reduction",
                                "ms": nms, "value": spec.m / (nms / 1e3), "unit": "markers/s",
                                "bins_with_scores": int((nz["count"] > 0).sum())}
+
+    if rank == 0 and world == 1 and not args.no_extras:
+        del e2e_bufs
+        extras["ingest"] = run_ingest(sg, torch, d, n, params, launch_fields)
 
     if rank == 0 and world == 1 and args.served > 0 and not args.no_extras:
         extras["served"] = run_served(args, torch, synth)
@@ -602,6 +607,62 @@ def run_extras(sg, torch, synth, d, hap, pos, gmap, n, ws):
     return ex
 
 
+def hap_major_bytes(rows, n):
+    """uint8 [n, m] 0/1 matrix (one row per haplotype) from packed marker-major
+    rows: the input layout of a phased haplotype file read haplotype by
+    haplotype.  Built 64 haplotypes (one row word) at a time."""
+    m = rows.shape[0]
+    out = np.empty((n, m), dtype=np.uint8)
+    for w in range((n + 63) // 64):
+        bits = np.unpackbits(np.ascontiguousarray(rows[:, w]).view(np.uint8).reshape(m, 8), axis=1,
+                             bitorder="little")                      # [m, 64]
+        h = min(64, n - 64 * w)
+        out[64 * w:64 * w + h] = bits[:, :h].T
+    return out
+
+
+def run_ingest(sg, torch, d, n, params, launch_fields, reps=3):
+    """Timed ingest of the bench's matrix: haplotype-major 0/1 bytes in pinned
+    host memory -> H2D -> selscan_pack (device) -> the scan, per call; events
+    split the three parts.  The packed rows equal the generator's."""
+    host = torch.from_numpy(hap_major_bytes(d.rows, n)).pin_memory()       # [n, m] uint8
+    h_pos = torch.from_numpy(d.pos).pin_memory()
+    h_gmap = torch.from_numpy(d.gmap).pin_memory()
+    dev = torch.device("cuda")
+    dbytes = torch.empty(host.shape, dtype=torch.uint8, device=dev)
+    dp, dg = torch.empty_like(h_pos, device=dev), torch.empty_like(h_gmap, device=dev)
+    out, ws = None, None
+    times = []
+    for r in range(reps + 1):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        torch.cuda.synchronize()
+        ev[0].record()
+        dbytes.copy_(host, non_blocking=True)
+        dp.copy_(h_pos, non_blocking=True)
+        dg.copy_(h_gmap, non_blocking=True)
+        ev[1].record()
+        rows = sg.selscan_pack(dbytes, n, hap_major=True)
+        ev[2].record()
+        out = sg.selscan_ihs(rows, n, dp, dg, params=params, workspace=ws, out=out,
+                             launch=sg.make_launch(**launch_fields))
+        ws = out["_workspace"]
+        ev[3].record()
+        torch.cuda.synchronize()
+        if r > 0:
+            times.append([ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]),
+                          ev[2].elapsed_time(ev[3])])
+    sg.check(out)
+    same = bool(torch.equal(rows, torch.from_numpy(d.rows.view(np.int64)).to(dev)))
+    t = np.mean(np.array(times), axis=0)
+    cores = int((out["status"] != sg.LOCUS_MAF_FILTERED).sum())
+    return {"what": "haplotype-major 0/1 bytes in pinned host memory -> H2D -> selscan_pack -> "
+                    "selscan_ihs, per call (CUDA events)",
+            "h2d_bytes": int(host.numel() + h_pos.numel() * 8 + h_gmap.numel() * 8),
+            "h2d_ms": float(t[0]), "pack_ms": float(t[1]), "scan_ms": float(t[2]),
+            "total_ms": float(t.sum()), "value": cores / (float(t.sum()) / 1e3),
+            "unit": "core loci/s", "pack_equals_generator": same}
+
+
 def run_served(args, torch, synth):
     """Served mix: Poisson arrivals at `load` x the server's measured capacity;
     continuous batching vs one plain launch per scan, same arrivals."""
@@ -632,9 +693,11 @@ def run_served(args, torch, synth):
             r.arrival = float(a)
         _, lat_s, mk_s = serve(reqs, ex, budget, tick_cores=args.tick_cores, policy=args.policy)
         _, lat_p, mk_p = run_plain(reqs)
+        _, lat_d, mk_d = run_plain(reqs, schedule=-1)
         return {"arrival_rate_per_s": rps,
                 "continuous_batching": summarize(lat_s, total_cores, mk_s),
-                "plain_launches": summarize(lat_p, total_cores, mk_p)}
+                "plain_launches": summarize(lat_p, total_cores, mk_p),
+                "sequential_default_launches": summarize(lat_d, total_cores, mk_d)}
 
     out = {"requests": len(reqs), "mix": "70% iHS / 30% XPEHH, haplotypes log-U(100, 5000), "
                                          "SNPs log-U(10k, 500k), seed 1000 + i",
@@ -646,7 +709,11 @@ def run_served(args, torch, synth):
         out["overload"] = dict(load=args.overload, **at_rate(args.overload * rate / args.load))
     out["note"] = ("latency = results on host - arrival; core_loci_per_s counts every marker "
                    "(MAF-filtered cores included) over the makespan; capacity = the whole mix "
-                   "present at t = 0 through the server; both arms see the same arrivals")
+                   "present at t = 0 through the server; every arm sees the same arrivals; "
+                   "plain_launches: one request at a time, one CTA per core; "
+                   "sequential_default_launches: one request at a time with the library's "
+                   "default launch (the same walk algorithms the server uses), so the gap to "
+                   "continuous_batching is what batching and overlap add")
     return out
 
 

@@ -11,6 +11,9 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libselscan_gb300.so")
 SOURCES = ["api.cu", "kernels.cu", "batch.cu", "noalloc.cu", "sweep.cu", "normalize.cu", "tped.cpp"]
+# the integer-pipe peak measurement, a library of its own (include/selscan_peak.h)
+PEAK_SOURCES = ["intpeak.cu"]
+PEAK_LIB = os.path.join(PKG, "libselscan_peak.so")
 HEADERS = ["walk.cuh", "internal.h", "device_common.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
@@ -24,23 +27,21 @@ def _flags(ptxas_verbose: bool):
     return f
 
 
-def _stale() -> bool:
-    if not os.path.exists(LIB):
+def _stale(lib, sources, headers) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
-    deps = [os.path.join(CSRC, s) for s in SOURCES + HEADERS]
-    deps.append(os.path.join(ROOT, "include", "selscan.h"))
+    t = os.path.getmtime(lib)
+    deps = [os.path.join(CSRC, s) for s in sources + HEADERS] + headers
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, ptxas_verbose: bool = False, quiet: bool = True) -> str:
-    """Compile every translation unit in parallel and link libselscan_gb300.so."""
-    if not force and not _stale():
-        return LIB
+def _build_lib(lib, sources, headers, force, ptxas_verbose, quiet):
+    if not force and not _stale(lib, sources, headers):
+        return lib
     os.makedirs(BUILD, exist_ok=True)
     procs = []
     objs = []
-    for s in SOURCES:
+    for s in sources:
         obj = os.path.join(BUILD, os.path.splitext(s)[0] + ".o")
         objs.append(obj)
         cmd = [NVCC, "-c", os.path.join(CSRC, s), "-o", obj] + _flags(ptxas_verbose)
@@ -56,15 +57,24 @@ def build(force: bool = False, ptxas_verbose: bool = False, quiet: bool = True) 
     if failed:
         msg = "\n".join(" ".join(c) + "\n" + t for c, t in failed)
         raise RuntimeError("nvcc failed:\n" + msg)
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     cuda_lib = os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "lib64")
     cmd = [NVCC, "-shared", "-o", tmp] + objs + ARCH + ["-cudart", "shared",
                                                          "-Xlinker", "-rpath," + cuda_lib]
     r = subprocess.run(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n" + r.stdout.decode(errors="replace"))
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
+
+
+def build(force: bool = False, ptxas_verbose: bool = False, quiet: bool = True) -> str:
+    """Compile every translation unit in parallel and link libselscan_gb300.so
+    (the scan library) and libselscan_peak.so (the integer-peak measurement)."""
+    _build_lib(PEAK_LIB, PEAK_SOURCES, [os.path.join(ROOT, "include", "selscan_peak.h")], force,
+               ptxas_verbose, quiet)
+    return _build_lib(LIB, SOURCES, [os.path.join(ROOT, "include", "selscan.h")], force,
+                      ptxas_verbose, quiet)
 
 
 if __name__ == "__main__":

@@ -553,12 +553,17 @@ class Server:
 
 
 def run_plain(requests: List[Request], device="cuda", clock: Callable[[], float] = time.perf_counter,
-              realtime: bool = True) -> Tuple[Dict[int, Dict], Dict[int, float], float]:
-    """Comparison: each request alone, in arrival order, one plain launch (one CTA per core)."""
+              realtime: bool = True, schedule: Optional[int] = None
+              ) -> Tuple[Dict[int, Dict], Dict[int, float], float]:
+    """Comparison: each request alone, in arrival order, one call per request.
+    schedule None: plain launches (one CTA per core, no persistence); a
+    schedule number (SCHED_DEFAULT: the library's own choice, the sorted sweep
+    for long chromosomes and the persistent per-step walk otherwise) isolates
+    what serving adds over running the same algorithm one request at a time."""
     import torch
     import paper_1403_6854_gb300 as sg
     results, latency = {}, {}
-    L = sg.make_launch(sg.SCHED_PLAIN)
+    L = sg.make_launch(sg.SCHED_PLAIN if schedule is None else schedule)
     t0 = clock()
     for req in sorted(requests, key=lambda r: r.arrival):
         if realtime:

@@ -175,3 +175,19 @@ def test_single_locus_report_refuses_a_row_stride_beyond_shared_memory(sg):
                                    ctypes.byref(oe), 4, None) == sg.ERR_INVALID_ARG
     assert lib.selscan_ehh_noalloc(fake, 2, 100, 10, fake, fake, 10, ctypes.byref(p),
                                    ctypes.byref(oe), 4, None) == sg.ERR_INVALID_ARG
+
+
+def test_peak_library_exports_its_header(sg):
+    """The integer-peak measurement library exports exactly what
+    include/selscan_peak.h declares and refuses bad arguments on the host."""
+    from paper_1403_6854_gb300 import peak
+    src = open(os.path.join(ROOT, "include", "selscan_peak.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = set(re.findall(r"\b(selscan_peak_[a-z_]+)\s*\(", src))
+    out = subprocess.run(["nm", "-D", "--defined-only", peak.PEAK_LIB_PATH], capture_output=True,
+                         text=True, check=True).stdout
+    assert set(re.findall(r"\bT (selscan_\w+)", out)) == names == set(peak.EXPORTS)
+    lib = peak.load_library()
+    r = peak.selscan_peak_result()
+    assert lib.selscan_peak_int(7, 10, ctypes.c_void_p(0x1000), 1 << 30, ctypes.byref(r)) == -1
+    assert lib.selscan_peak_int(0, 0, ctypes.c_void_p(0x1000), 1 << 30, ctypes.byref(r)) == -1

@@ -287,6 +287,22 @@ def test_pack_matches_reference_packing(sg):
         assert np.array_equal(got2, want)
 
 
+def test_pack_matches_reference_packing_at_full_size(sg):
+    """Device packing of the bench's 5,000 x 1,000,000 matrix from 0/1 bytes
+    (5 GB), marker-major and haplotype-major, equals the generator's packing
+    bit for bit (pad bits 0)."""
+    d = synth.generate(synth.spec("ihs1m"))
+    want = torch.from_numpy(d.rows.view(np.int64)).cuda()
+    hap01 = torch.from_numpy(synth.unpack(d.rows, 5000)).cuda()       # [m, n]
+    got = sg.selscan_pack(hap01, 5000)
+    assert torch.equal(got, want)
+    del got
+    hm = hap01.t().contiguous()                                        # [n, m]
+    del hap01
+    got2 = sg.selscan_pack(hm, 5000, hap_major=True)
+    assert torch.equal(got2, want)
+
+
 def test_unsorted_input_sets_device_error(sg, plain):
     pos = plain.pos.copy()
     pos[100], pos[101] = pos[101], pos[100]

@@ -101,10 +101,13 @@ def test_server_futures_equal_alone(sg):
     assert srv._loop.sch.used == 0
 
 
-def test_plain_runner_equals_alone(sg):
+@pytest.mark.parametrize("schedule", [None, -1])
+def test_plain_runner_equals_alone(sg, schedule):
+    """Both comparison arms of the served bench (plain launches, and the
+    library's default launch one request at a time) give the scan alone."""
     from paper_1403_6854_gb300.serve import run_plain
     reqs = make_requests()[:3]
-    res, lat, mk = run_plain(reqs, realtime=False)
+    res, lat, mk = run_plain(reqs, realtime=False, schedule=schedule)
     for r in reqs:
         ref = alone(sg, r)
         assert np.array_equal(res[r.rid]["stop"], ref["stop"])
