@@ -22,6 +22,8 @@ NVCC = os.environ.get("NVCC", "nvcc")
 def _flags(ptxas_verbose: bool):
     f = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
                 "-I", os.path.join(ROOT, "include")]
+    # extra nvcc flags for a debugging build (e.g. -DSELSCAN_SWEEP_CHECKS=1)
+    f += [x for x in os.environ.get("SELSCAN_NVCC_FLAGS", "").split() if x]
     if ptxas_verbose:
         f += ["-Xptxas", "-v"]
     return f
