@@ -630,10 +630,17 @@ __device__ const unsigned short *build_window(const Tile &tile, const SplitSmem 
 
 // Pair counts fit 32 bits (C(16383, 2) < 2^32); the digest and the cutoff
 // product are 64-bit.
+// The trapezoid sum (Eq. 4 / Eq. 5) is kept per lane: the lane that owns
+// step i of the current G-step block (the lane whose map step it computed)
+// records that step's integer term S(i-1) + S(i) in `rec`, and once per
+// block every lane adds rec * g to its FP64 partial sum; the partial sums are
+// added over the tile when the walk ends.  One FP64 multiply-add per lane and
+// block instead of one per step: FP64 is a narrow pipe on this GPU.
 struct ClassWalk {
     unsigned D, S, prev;
+    unsigned rec;                   // this lane's step term of the current block (0: none)
     unsigned long long dig, numD;   // numD = cut_num * D
-    double acc;
+    double acc;                     // this lane's partial trapezoid sum
     int status, stop;
     bool active;
 };
@@ -800,7 +807,8 @@ __global__ void __launch_bounds__(kSplitWarps * 32, SPLIT_MIN_CTAS) split_walk_k
         ClassWalk cw[NWK];
         unsigned SA = 0, SB = 0, pA = 0, pB = 0, DA = 0, DB = 0;
         unsigned long long dA = 0, dB = 0;
-        double accB = 0.0;
+        double accB = 0.0;                  // XPEHH: population B's partial sum (A's in cw[0])
+        unsigned recB = 0;
         if (NPOP == 2) {
             const unsigned nA = (unsigned)w.a.nA, nB = (unsigned)w.a.nB;
             const unsigned a0 = count_a(s, n0), a1 = nA - a0;
@@ -826,6 +834,7 @@ __global__ void __launch_bounds__(kSplitWarps * 32, SPLIT_MIN_CTAS) split_walk_k
             cw[q].prev = cw[q].S;
             cw[q].dig = cw[q].S;
             cw[q].acc = 0.0;
+            cw[q].rec = 0u;
             cw[q].stop = 0;
             cw[q].status = cw[q].D == 0u ? WALK_UNDEFINED : WALK_OK;
             cw[q].active = cw[q].D != 0u;
@@ -833,8 +842,8 @@ __global__ void __launch_bounds__(kSplitWarps * 32, SPLIT_MIN_CTAS) split_walk_k
         }
 
         const long long step = dir ? 1 : -1;
-        double gq = 0.0;        // this lane's step of the current G-step block:
-                                // map step g >= 0, -1 past the array end, -2 a gap abort
+        double gq = 0.0;        // this lane's step of the current G-step block: the map step g
+        int gk = 0;             // its kind: 0 a step, WALK_EDGE past the array end, WALK_GAP a gap abort
         // steps [lo, lo + wlen) are grouped in cl: first the slot's window
         // (steps 1..w1), then windows of 64 steps found in M
         int lo = 1, wlen = w1 > 0 ? w1 : 64;
@@ -855,13 +864,21 @@ __global__ void __launch_bounds__(kSplitWarps * 32, SPLIT_MIN_CTAS) split_walk_k
         int fin = WALK_OK;                           // how the still-active walks end
         int i = 1;                              // walks stay below 2^31 steps (a chunk history)
         for (; any; ++i) {
-            if (((i - 1) & (G - 1)) == 0) {       // gaps and map steps of the next G steps
+            const int own_step = (int)((i - 1) & (G - 1));   // the lane that owns step i
+            if (own_step == 0) {                  // gaps and map steps of the next G steps
+                if (i > 1) {                      // the previous block's terms
+#pragma unroll
+                    for (int q = 0; q < NWK; ++q) { cw[q].acc += (double)cw[q].rec * gq; cw[q].rec = 0u; }
+                    if (NPOP == 2) { accB += (double)recB * gq; recB = 0u; }
+                }
                 const long long xl = k + step * (i + lane), xp = xl - step;
-                if (xl < 0 || xl >= m) gq = -1.0;
+                gq = 0.0;
+                gk = 0;
+                if (xl < 0 || xl >= m) gk = WALK_EDGE;
                 else {
                     const long long p1 = __ldg(w.a.pos + xl), p0 = __ldg(w.a.pos + xp);
                     const long long bp = dir ? p1 - p0 : p0 - p1;
-                    if (bp > w.a.max_gap) gq = -2.0;
+                    if (bp > w.a.max_gap) gk = WALK_GAP;
                     else {
                         double gg;
                         if (w.a.physical) gg = (double)bp;
@@ -874,8 +891,9 @@ __global__ void __launch_bounds__(kSplitWarps * 32, SPLIT_MIN_CTAS) split_walk_k
                     }
                 }
             }
-            const double g = tile.shfl(gq, (int)((i - 1) & (G - 1)));
-            if (g < 0.0) { fin = g == -1.0 ? WALK_EDGE : WALK_GAP; break; }
+            const int kind = tile.shfl(gk, own_step);
+            if (kind != 0) { fin = kind; break; }
+            const bool own = lane == own_step;
             if (i > hz) { fin = WALK_UNFINISHED; break; }
             if (i >= lo + wlen) {
                 lo += wlen;
@@ -927,9 +945,9 @@ __global__ void __launch_bounds__(kSplitWarps * 32, SPLIT_MIN_CTAS) split_walk_k
                 const bool stop = (unsigned long long)w.a.cut_den * q.S < q.numD;
                 if (stop && !w.a.crossing) { q.stop = (int)i; q.active = false; }
                 else {
-                    if (lane == 0) {
-                        q.acc += (double)(pA + SA) * g;
-                        accB += (double)(pB + SB) * g;
+                    if (own) {
+                        q.rec = pA + SA;
+                        recB = pB + SB;
                     }
                     if (stop) { q.stop = (int)i; q.active = false; }
                     pA = SA;
@@ -944,7 +962,7 @@ __global__ void __launch_bounds__(kSplitWarps * 32, SPLIT_MIN_CTAS) split_walk_k
                     q.dig += (unsigned long long)ii * q.S;
                     const bool stop = (unsigned long long)w.a.cut_den * q.S < q.numD;
                     if (stop && !w.a.crossing) { q.stop = (int)i; q.active = false; continue; }
-                    if (lane == 0) q.acc += (double)(q.prev + q.S) * g;
+                    if (own) q.rec = q.prev + q.S;
                     if (stop) { q.stop = (int)i; q.active = false; continue; }
                     q.prev = q.S;
                 }
@@ -952,6 +970,16 @@ __global__ void __launch_bounds__(kSplitWarps * 32, SPLIT_MIN_CTAS) split_walk_k
             any = false;
 #pragma unroll
             for (int q = 0; q < NWK; ++q) any |= cw[q].active;
+        }
+        // ---- the last block's terms, then the tile's sum of the partial sums
+#pragma unroll
+        for (int q = 0; q < NWK; ++q) {
+            cw[q].acc += (double)cw[q].rec * gq;
+            cw[q].acc = cg::reduce(tile, cw[q].acc, cg::plus<double>());
+        }
+        if (NPOP == 2) {
+            accB += (double)recB * gq;
+            accB = cg::reduce(tile, accB, cg::plus<double>());
         }
         // ---- results (lane 0)
         if (lane == 0) {
