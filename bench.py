@@ -193,6 +193,14 @@ def run_reference(args, rank, world):
 
 
 SWEEP_DRAM_BYTES_PER_CORE = 4.6139e9 / 125020
+# ncu capture of the 250k case (5,000 x 250,000, default sweep shape; the
+# launch list and capture summarised in profiles/sweep_split_walk_ihs250k_full.md):
+# sweep_kernel alone read + wrote 3.493 GB (125,020 core loci), and its ALU-pipe
+# instructions (sm__inst_executed_pipe_alu, 51.8 % of the elapsed peak over
+# 14.56 ms at 2,070 MHz on 152 SMs, 2 warp instructions per SM cycle) come to
+# 29.8 thread operations per sorted element and marker pass
+SORT_DRAM_BYTES_PER_CORE = 3.4930e9 / 125020
+SORT_ALU_OPS_PER_ELEMENT_PASS = 29.8
 
 
 def main():
@@ -267,10 +275,12 @@ def main():
         shape = dict(shape, source=("autotuner, sorted-sweep candidates timed on the whole scan"
                                     if shape.get("schedule") == 3 else
                                     "autotuner on the first 65,536 markers"))
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(K)]
-    for a, b in ev:                      # create the events before handing them out
-        a.record(); b.record()
+    # per step: before the first walk kernel, after it the sort of the first
+    # stage (sweep schedule), after the last walk kernel
+    ev = [tuple(torch.cuda.Event(enable_timing=True) for _ in range(3)) for _ in range(K)]
+    for trio in ev:                      # create the events before handing them out
+        for e_ in trio:
+            e_.record()
     torch.cuda.synchronize()
     ws = None
     out = None
@@ -301,7 +311,8 @@ def main():
             dist.barrier()
     sg.check(out)
     ms = t0.elapsed_time(t1)
-    walk_ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+    walk_ms = float(np.mean([a.elapsed_time(b) for a, b, _ in ev]))
+    sort_ms = float(np.mean([a.elapsed_time(c) for a, _, c in ev]))
     status = out["status"].cpu().numpy()
     stop = out["stop"].cpu().numpy()
     cores = int((status != sg.LOCUS_MAF_FILTERED).sum())
@@ -373,15 +384,39 @@ def main():
     if rank == 0:
         hbm, src = peaks()
         achieved = walk_bytes / (walk_ms / 1e3) / 1e9
-        # DRAM bytes of the sorted-sweep kernels from one ncu capture of the
-        # 250k-marker case (dram__bytes_read.sum + dram__bytes_write.sum of
-        # sweep_kernel and split_walk_kernel: 4.61 GB over 125,020 core loci),
-        # scaled by core loci
-        traffic, traffic_note = None, "no capture for this schedule"
-        if launch_fields.get("schedule") == 3:
-            traffic = cores * SWEEP_DRAM_BYTES_PER_CORE
-            traffic_note = ("ncu capture of the 250k case, 36,910 DRAM bytes per core locus, "
-                            "scaled by core loci")
+        path = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "walk_ms": walk_ms, "walk_bytes": walk_bytes,
+                "what": "algorithmic row bytes of every walk step (sum of L x 8W + 16 (L - 1)) "
+                        "over the time of all walk kernels",
+                "peak_source": f"{src} hbm_gbs (MEASURED_PEAKS.json)"}
+        work = sg.selscan_sweep_work(n, spec.m, sg.MODE_IHS, sg.make_launch(**launch_fields))
+        if work is not None:
+            # the dominant kernel, the sort, against the integer-pipe peak measured here
+            from paper_1403_6854_gb300 import peak as int_peak
+            pk = int_peak.measure()
+            alu_peak = float(np.median([pk[o]["ops_per_s"] for o in ("LOP3", "PRMT", "SHF")]))
+            element_passes = work[0] * work[1]
+            ops = element_passes * SORT_ALU_OPS_PER_ELEMENT_PASS
+            alu = ops / (sort_ms / 1e3)
+            roofline = {"bound": "alu", "kernel": "sweep_kernel (the sort; first stage)",
+                        "achieved": alu / 1e9, "peak": alu_peak / 1e9, "unit": "Gop/s",
+                        "frac": alu / alu_peak,
+                        "traffic": cores * SORT_DRAM_BYTES_PER_CORE,
+                        "traffic_note": "ncu capture of the 250k case (3.49 GB of sweep_kernel "
+                                        "DRAM traffic over 125,020 core loci), scaled by core loci",
+                        "kernel_ms": sort_ms, "split_walk_ms": walk_ms - sort_ms,
+                        "element_passes": element_passes, "marker_passes": work[0],
+                        "ops_per_element_pass": SORT_ALU_OPS_PER_ELEMENT_PASS,
+                        "ops_note": "ALU-pipe thread operations per sorted element and marker "
+                                    "pass from the ncu capture of the 250k case, times the passes "
+                                    "of this launch",
+                        "peak_source": "ALU pipe (LOP3 / PRMT / funnel shift: 64 lanes per SM "
+                                       "cycle) measured in this run by libselscan_peak",
+                        "int_peaks_ops_per_sm_per_cycle": {k: round(v["ops_per_sm_per_cycle"], 2)
+                                                           for k, v in pk.items()},
+                        "path": path}
+        else:
+            roofline = dict(path, kernel="walk_persistent_kernel (both passes)", traffic=None)
         line = {
             "metric": METRIC, "value": value, "unit": "core loci/s", "n_gpus": world,
             "steps": K, "warmup": Wm, "ms_per_step": ms_max / K, "higher_is_better": True,
@@ -396,13 +431,7 @@ def main():
                        "launch_shape": shape,
                        "l2": "inputs larger than L2 (packed matrix 632 MB), no flush",
                        "parallelism": f"weak: one chromosome (seed = rank) per GPU x{world}"},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": achieved / hbm, "traffic": traffic, "traffic_note": traffic_note,
-                         "kernel": ("sweep_kernel + split_walk_kernel, all stages, and the "
-                                    "second per-step pass" if launch_fields.get("schedule") == 3
-                                    else "walk_persistent_kernel (both passes)"),
-                         "walk_ms": walk_ms, "walk_bytes": walk_bytes,
-                         "peak_source": f"{src} hbm_gbs (MEASURED_PEAKS.json)"},
+            "roofline": roofline,
             "gpu_launches": launches_per_step * K,
             "clocks": clk.summary(),
         }

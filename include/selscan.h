@@ -141,6 +141,10 @@ typedef struct {
                                   it holds at most 32 haplotypes per thread */
     int32_t sweep_split_tile;  /* sweep schedule: lanes per split walk, 32 or 16 (two walks
                                   per warp) (0 = default) */
+    int32_t reserved0;
+    void *sweep_done_event;    /* optional cudaEvent_t, recorded after the sorting kernel of the
+                                  first stage (sweep schedule): with walk_begin_event it times
+                                  the sort of a one-stage scan on its own */
 } selscan_launch;
 
 /* iHS outputs: device arrays of length m (one record per marker). */
@@ -370,6 +374,15 @@ int selscan_pack(const uint8_t *hap01, int32_t n, int64_t m, int32_t hap_major,
  * haplotypes, else SELSCAN_SCHED_IN_ORDER; -1 for bad arguments (mode
  * SELSCAN_MODE_IHS or SELSCAN_MODE_XPEHH).  Host only: no device work. */
 int32_t selscan_default_schedule(int32_t n_total, int64_t m, int32_t mode);
+
+/* Work of the sorting kernels of a sweep-schedule call: *marker_passes = the
+ * markers all sorting CTAs step through over every stage (each chunk's cores
+ * plus its warm-up, both directions), *elements = the sorted elements per
+ * marker pass (n_total rounded up to the CTA's element grid).  Host only: no
+ * device work.  Returns SELSCAN_OK, or SELSCAN_ERR_INVALID_ARG for bad
+ * arguments or a launch that does not take the sweep schedule. */
+int selscan_sweep_work(int32_t n_total, int64_t m, int32_t mode, const selscan_launch *launch,
+                       int64_t *marker_passes, int64_t *elements);
 
 /* Kernel launches one selscan_ihs / selscan_xpehh call makes with this
  * launch shape (mode SELSCAN_MODE_IHS or SELSCAN_MODE_XPEHH), or -1 for bad

@@ -51,7 +51,8 @@ class selscan_launch(ctypes.Structure):
                 ("walk_begin_event", ctypes.c_void_p), ("walk_end_event", ctypes.c_void_p),
                 ("big_group_entries", ctypes.c_int32), ("sweep_warmup", ctypes.c_int32),
                 ("sweep_stage_cores", ctypes.c_int32), ("sweep_threads", ctypes.c_int32),
-                ("sweep_split_tile", ctypes.c_int32)]
+                ("sweep_split_tile", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("sweep_done_event", ctypes.c_void_p)]
 
 
 class selscan_ihs_out(ctypes.Structure):
@@ -82,7 +83,7 @@ EXPORTS = ("selscan_default_params", "selscan_workspace_bytes", "selscan_ihs", "
            "selscan_ehh", "selscan_ehh_noalloc", "selscan_pack", "selscan_strerror",
            "selscan_batch_item_bytes", "selscan_batch_workspace_bytes", "selscan_batch_prepare",
            "selscan_batch_run", "selscan_batch_finalize", "selscan_launch_count",
-           "selscan_default_schedule",
+           "selscan_default_schedule", "selscan_sweep_work",
            "selscan_normalize", "selscan_normalize_workspace_bytes", "selscan_read_tped")
 EHH_NOALLOC_MAX_N = 8192
 
@@ -167,6 +168,9 @@ def load_library():
                                       _P, _P, _P, _P, _P, ctypes.c_size_t, _P]
     lib.selscan_launch_count.restype = ctypes.c_int32
     lib.selscan_launch_count.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, _P]
+    lib.selscan_sweep_work.restype = ctypes.c_int
+    lib.selscan_sweep_work.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, _P,
+                                       ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
     lib.selscan_default_schedule.restype = ctypes.c_int32
     lib.selscan_default_schedule.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_int32]
     lib.selscan_batch_finalize.restype = ctypes.c_int
@@ -205,7 +209,8 @@ def make_launch(schedule: int = SCHED_DEFAULT, warps_per_cta: int = 0, ctas_per_
                 cores_per_fetch: int = 0, min_ctas_per_sm: int = 0, big_group_entries: int = 0,
                 sweep_warmup: int = 0, sweep_stage_cores: int = 0, sweep_threads: int = 0,
                 sweep_split_tile: int = 0, events=None) -> selscan_launch:
-    """events: optional (begin, end) torch.cuda.Event pair bracketing the walk kernels."""
+    """events: optional (begin, end) torch.cuda.Event pair bracketing the walk kernels,
+    or (begin, end, sort_done) with an event recorded after the first stage's sort."""
     L = selscan_launch(schedule, warps_per_cta, ctas_per_sm, smem_entries, probe_steps,
                        window_rows, cores_per_fetch, min_ctas_per_sm)
     L.big_group_entries = big_group_entries
@@ -216,6 +221,8 @@ def make_launch(schedule: int = SCHED_DEFAULT, warps_per_cta: int = 0, ctas_per_
     if events is not None:
         L.walk_begin_event = ctypes.c_void_p(events[0].cuda_event)
         L.walk_end_event = ctypes.c_void_p(events[1].cuda_event)
+        if len(events) > 2:
+            L.sweep_done_event = ctypes.c_void_p(events[2].cuda_event)
     return L
 
 
@@ -310,6 +317,17 @@ def selscan_normalize_apply(score: torch.Tensor, status: torch.Tensor, n1: torch
 def selscan_default_schedule(n_total: int, m: int, mode: int) -> int:
     """Schedule a default launch takes for this scan shape (-1: bad arguments)."""
     return int(load_library().selscan_default_schedule(n_total, m, mode))
+
+
+def selscan_sweep_work(n_total: int, m: int, mode: int,
+                       launch: Optional[selscan_launch] = None):
+    """(marker passes, elements per pass) of the sorting kernels of a sweep
+    call, or None if the launch does not take the sweep schedule."""
+    mp, el = ctypes.c_int64(0), ctypes.c_int64(0)
+    rc = load_library().selscan_sweep_work(n_total, m, mode,
+                                           ctypes.byref(launch) if launch is not None else None,
+                                           ctypes.byref(mp), ctypes.byref(el))
+    return None if rc != OK else (int(mp.value), int(el.value))
 
 
 def selscan_launch_count(n_total: int, m: int, mode: int,

@@ -368,6 +368,7 @@ int run_scan(int mode, const uint64_t *hap, int64_t ld, int32_t nA, int32_t nB, 
         w.walk_ctas = plan.sw.walk_ctas;
         w.walk_head = (unsigned long long *)(ws + l.sweep_head);
         w.err = err;
+        w.sweep_done_event = launch ? launch->sweep_done_event : nullptr;
         if (launch_sweep_path(w, s) != cudaSuccess) return SELSCAN_ERR_CUDA;
         if (launch_pass2(a, sk, sc, plan.wpc, plan.ctas, plan.minb, s) != cudaSuccess)
             return SELSCAN_ERR_CUDA;
@@ -465,6 +466,28 @@ int32_t selscan_default_schedule(int32_t n_total, int64_t m, int32_t mode)
 {
     if (n_total < 2 || m < 1 || (mode != SELSCAN_MODE_IHS && mode != SELSCAN_MODE_XPEHH)) return -1;
     return default_schedule(mode, n_total, m);
+}
+
+int selscan_sweep_work(int32_t n_total, int64_t m, int32_t mode, const selscan_launch *launch,
+                       int64_t *marker_passes, int64_t *elements)
+{
+    if (n_total < 2 || m < 1 || (mode != SELSCAN_MODE_IHS && mode != SELSCAN_MODE_XPEHH) ||
+        !marker_passes || !elements)
+        return SELSCAN_ERR_INVALID_ARG;
+    const Plan p = make_plan(mode, (n_total + 63) / 64, launch, n_total, m);
+    if (p.schedule != SELSCAN_SCHED_SWEEP) return SELSCAN_ERR_INVALID_ARG;
+    long long passes = 0;
+    for (int c = 0; c < p.sw.nch; ++c) {
+        const long long c0 = (long long)c * p.sw.B;
+        if (c0 >= m) break;
+        const long long c1 = c0 + p.sw.B < m ? c0 + p.sw.B : m;
+        const long long s0 = c0 - p.sw.L > 0 ? c0 - p.sw.L : 0;
+        const long long e0 = c1 - 1 + p.sw.L < m - 1 ? c1 - 1 + p.sw.L : m - 1;
+        passes += (c1 - s0) + (e0 - c0 + 1);       // toward lower / higher indices
+    }
+    *marker_passes = passes;
+    *elements = (int64_t)sweep_elements(n_total, p.sw.threads);
+    return SELSCAN_OK;
 }
 
 int32_t selscan_launch_count(int32_t n_total, int64_t m, int32_t mode, const selscan_launch *launch)

@@ -143,11 +143,13 @@ struct SweepArgs {
     int walk_ctas;           // persistent split-walk grid
     unsigned long long *walk_head;   // slot counter of the current walk launch
     int32_t *err;                    // device error word of the call
+    void *sweep_done_event;          // optional event after the first stage's sort
 };
 
 size_t sweep_smem_bytes(int n, int W, int T, int R);
 size_t sweep_slot_bytes(int n, int xpehh);
 size_t sweep_state_bytes(int n, int T);
+size_t sweep_elements(int n, int T);     // sorted elements of one CTA (n and its padding)
 size_t split_smem_per_warp(int n, int xpehh);
 size_t split_scratch_per_warp(int n);
 int split_walk_ctas(int n, int xpehh, int tile);

@@ -123,6 +123,7 @@ size_t sweep_slot_bytes(int n, int xpehh)
 }
 
 size_t sweep_state_bytes(int n, int T) { return (size_t)sweep_npad(n, T) * 4; }
+size_t sweep_elements(int n, int T) { return (size_t)sweep_npad(n, T); }
 
 
 // ---- the sweep ---------------------------------------------------------------
@@ -634,8 +635,10 @@ __device__ const unsigned short *build_window(const Tile &tile, const SplitSmem 
 // step i of the current G-step block (the lane whose map step it computed)
 // records that step's integer term S(i-1) + S(i) in `rec`, and once per
 // block every lane adds rec * g to its FP64 partial sum; the partial sums are
-// added over the tile when the walk ends.  One FP64 multiply-add per lane and
-// block instead of one per step: FP64 is a narrow pipe on this GPU.
+// added over the tile by a fixed butterfly when the walk ends.  One FP64
+// multiply-add per lane and block instead of one per step (FP64 is a narrow
+// pipe on this GPU); with 32-lane tiles the additions are exactly those of the
+// per-step walk, so a walk handed over to it gives the same bits.
 struct ClassWalk {
     unsigned D, S, prev;
     unsigned rec;                   // this lane's step term of the current block (0: none)
@@ -975,11 +978,11 @@ __global__ void __launch_bounds__(kSplitWarps * 32, SPLIT_MIN_CTAS) split_walk_k
 #pragma unroll
         for (int q = 0; q < NWK; ++q) {
             cw[q].acc += (double)cw[q].rec * gq;
-            cw[q].acc = cg::reduce(tile, cw[q].acc, cg::plus<double>());
+            cw[q].acc = lane_sum_f64<G>(cw[q].acc);
         }
         if (NPOP == 2) {
             accB += (double)recB * gq;
-            accB = cg::reduce(tile, accB, cg::plus<double>());
+            accB = lane_sum_f64<G>(accB);
         }
         // ---- results (lane 0)
         if (lane == 0) {
@@ -1072,6 +1075,9 @@ cudaError_t launch_sweep_path(const SweepArgs &w0, cudaStream_t s)
     for (int st = 0; st < w.nstages; ++st) {
         w.stage = st;
         sweep<<<2 * w.nch, w.threads, ssm, s>>>(w);
+        if (st == 0 && w.sweep_done_event &&
+            (e = cudaEventRecord((cudaEvent_t)w.sweep_done_event, s)) != cudaSuccess)
+            return e;
         walk<<<w.walk_ctas, kSplitWarps * 32, wsm, s>>>(w);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }

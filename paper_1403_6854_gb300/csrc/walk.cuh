@@ -91,6 +91,17 @@ struct WalkOut {
                                      // warp must not start another walk
 };
 
+// Sum of the partial sums of G consecutive lanes (a warp, or half of one),
+// by a butterfly in a fixed order; every lane gets the sum, lane 0's is used.
+template <int G>
+__device__ __forceinline__ double lane_sum_f64(double v)
+{
+    const unsigned mask = G == 32 ? 0xFFFFFFFFu : (0xFFFFu << (threadIdx.x & 16));
+#pragma unroll
+    for (int d = G / 2; d > 0; d >>= 1) v += __shfl_xor_sync(mask, v, d);
+    return v;
+}
+
 __device__ __forceinline__ unsigned int lanemask_lt()
 {
     unsigned int r;
@@ -702,8 +713,11 @@ __device__ WalkOut walk(const ScanArgs &a, long long core, int dir, int sel, con
         const bool stop = below_cut(a, NPOP == 2 ? SP : S0, Dstop);
         if (stop && !a.crossing) { o.stop = (int)i; break; }
         // trapezoid (Eq. 4 / Eq. 5): (EHH(i-1) + EHH(i)) / 2 * g, with the
-        // common 1 / (2 C(N,2)) applied once at the end
-        if (lane == 0) {                      // one lane keeps the FP64 sums
+        // common 1 / (2 C(N,2)) applied once at the end.  Lane (i - 1) % 32
+        // keeps the term of step i in its partial sum; the partial sums are
+        // added by a fixed butterfly when the walk ends.  The sorted-sweep
+        // walk sums in the same order, so both give the same bits.
+        if (lane == (int)((i - 1) & 31)) {
             acc0 += (double)(p0 + S0) * g;
             if (NPOP == 2) acc1 += (double)(p1 + S1) * g;
         }
@@ -718,6 +732,8 @@ __device__ WalkOut walk(const ScanArgs &a, long long core, int dir, int sel, con
     if (o.abandon) o.status = WALK_UNDEFINED;
     win_parity[0] = wb[0].parity;
     win_parity[1] = wb[1].parity;
+    acc0 = lane_sum_f64<32>(acc0);
+    if (NPOP == 2) acc1 = lane_sum_f64<32>(acc1);
     if (NPOP == 2) {
         o.ihh[0] = D0 ? acc0 / (2.0 * (double)D0) : 0.0;
         o.ihh[1] = D1 ? acc1 / (2.0 * (double)D1) : 0.0;

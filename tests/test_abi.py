@@ -191,3 +191,19 @@ def test_peak_library_exports_its_header(sg):
     r = peak.selscan_peak_result()
     assert lib.selscan_peak_int(7, 10, ctypes.c_void_p(0x1000), 1 << 30, ctypes.byref(r)) == -1
     assert lib.selscan_peak_int(0, 0, ctypes.c_void_p(0x1000), 1 << 30, ctypes.byref(r)) == -1
+
+
+def test_sweep_work_on_host(sg):
+    """Host-only count of the sorting kernels' work: a chunk's passes are its
+    cores plus its warm-up (clipped at the chromosome ends), both directions;
+    None for a launch that does not sort."""
+    I = sg.MODE_IHS
+    passes, elements = sg.selscan_sweep_work(5000, 1_000_000, I)
+    assert elements >= 5000 and elements % 64 == 0
+    # 2 x (m markers) plus at most two warm-ups per chunk and direction
+    assert 2_000_000 < passes < 2_000_000 + 2 * 228 * 1536 + 1
+    L = sg.make_launch(sg.SCHED_SWEEP, sweep_warmup=1024)
+    p2, _ = sg.selscan_sweep_work(5000, 1_000_000, I, L)
+    assert p2 < passes
+    assert sg.selscan_sweep_work(204, 22147, I) is None          # per-step default
+    assert sg.selscan_sweep_work(204, 22147, I, sg.make_launch(sg.SCHED_SWEEP)) is not None
