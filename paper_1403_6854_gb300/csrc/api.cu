@@ -85,23 +85,15 @@ SweepPlan make_sweep_plan(int n_total, long long m, int mode, const selscan_laun
     // once).  Larger samples: 256 threads up to 6,144 haplotypes, else 512
     const int want = L ? L->sweep_threads : 0;
     const long long g = nch > (3ll * sms) / 2 ? 16 : 8;
-    if (want == 32 || want == 64 || want == 128 || want == 256 || want == 512 || want == 1024)
-        w.threads = want;
+    if (want == 32 || want == 64 || want == 128 || want == 256 || want == 512) w.threads = want;
     else if (n_total <= 128 * g)
         w.threads = n_total <= 32 * g ? 32 : n_total <= 64 * g ? 64 : 128;
     else w.threads = n_total <= 256 * 24 ? 256 : 512;
-    // every thread keeps its elements in registers: at most 24 per thread
-    while (w.threads < 1024 && n_total > w.threads * 24) w.threads *= 2;
-    // the resident sweep CTAs split over both directions: as many as fit an
-    // SM for the wide CTAs (three of 256 threads at 5,000 haplotypes), at
-    // most sixteen warps of the narrow widths (shorter chunks would only add
-    // warm-up); without a device to ask, three of 256, one of 512 or 1024.
-    // (Row words: at most one more for XPEHH, whose populations start on word
-    // boundaries.)
-    const int fit = sweep_ctas_per_sm(n_total, (n_total + 63) / 64 + (mode == SELSCAN_MODE_XPEHH),
-                                      w.threads);
-    int per_sm = w.threads >= 512 ? 1 : (w.threads == 256 ? 3 : 512 / w.threads);
-    if (fit > 0) per_sm = w.threads >= 256 ? fit : (fit < per_sm ? fit : per_sm);
+    // a thread's allele bits live in one 32-bit word: at most 32 elements per thread
+    while (w.threads < 512 && n_total > w.threads * 32) w.threads *= 2;
+    // the resident sweep CTAs split over both directions: three 256-thread
+    // CTAs per SM, two of 512, sixteen warps of the narrow widths
+    const int per_sm = w.threads == 512 ? 2 : (w.threads == 256 ? 3 : 512 / w.threads);
     const int nmax = (per_sm * sms) / 2;
     if (nch > nmax) nch = nmax;
     if (nch < 1) nch = 1;

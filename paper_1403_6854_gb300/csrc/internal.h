@@ -150,9 +150,6 @@ size_t sweep_smem_bytes(int n, int W, int T, int R);
 size_t sweep_slot_bytes(int n, int xpehh);
 size_t sweep_state_bytes(int n, int T);
 size_t sweep_elements(int n, int T);     // sorted elements of one CTA (n and its padding)
-// resident sorting CTAs of T threads per SM for n haplotypes on rows of W
-// 64-bit words (0 if the device cannot be asked)
-int sweep_ctas_per_sm(int n, int W, int T);
 size_t split_smem_per_warp(int n, int xpehh);
 size_t split_scratch_per_warp(int n);
 int split_walk_ctas(int n, int xpehh, int tile);

@@ -41,21 +41,16 @@ namespace selscan {
 
 namespace {
 
-constexpr int kBlock = 16;                  // markers whose alleles one transposed row block holds
+constexpr unsigned kInf16 = 0xFFFFu;
+constexpr int kRowRing = 4;                 // rows in flight ahead of the sort (cp.async)
 constexpr int kSlotListCap = 1024;          // first-window boundaries kept per slot
 constexpr int kSplitListSmem = 1024;        // window list entries a walking warp keeps on chip
 
 __host__ __device__ inline int sweep_e(int n, int T)
 {
     int e = (n + T - 1) / T;
-    return (e + 1) & ~1;                    // even: elements are read two (16 bytes) at a time
+    return (e + 3) & ~3;                    // a multiple of 4: elements are read 4 at a time
 }
-// words per staged row: the row's 32-bit words, plus two when that count is a
-// multiple of four (16 rows at that stride then fall in 16 distinct banks)
-__host__ __device__ inline int sweep_w32r(int W32) { return W32 + ((W32 & 3) == 0 ? 2 : 0); }
-// bytes of the allele table: one 16-bit entry per bit index of a row, plus
-// the padding elements' entry, rounded to 16 bytes
-__host__ __device__ inline size_t sweep_at_bytes(int W32) { return (((size_t)32 * W32 + 1) * 2 + 15) & ~(size_t)15; }
 __host__ __device__ inline int sweep_npad(int n, int T) { return sweep_e(n, T) * T; }
 __host__ __device__ inline int split_nw(int n) { return (n + 32) >> 5; }   // bits 0..n
 
@@ -116,9 +111,9 @@ __host__ __device__ inline size_t slot_list_at(int n, int xpehh) { return slot_o
 
 size_t sweep_smem_bytes(int n, int W, int T, int R)
 {
-    const int W32 = 2 * W;
-    return (size_t)sweep_npad(n, T) * 8 + (size_t)kBlock * sweep_w32r(W32) * 4 + sweep_at_bytes(W32) +
-           T / 32 * 8 + 2 * 65 * 4 + (size_t)((R + 31) / 32) * 4;
+    const int W32 = ((2 * W) + 4) & ~3;
+    return (size_t)sweep_npad(n, T) * 4 * 2 + (size_t)W32 * 4 * kRowRing + T / 32 * 8 + 2 * 65 * 4 +
+           (size_t)((R + 31) / 32) * 4;
 }
 
 size_t sweep_slot_bytes(int n, int xpehh)
@@ -127,75 +122,36 @@ size_t sweep_slot_bytes(int n, int xpehh)
     return slot_list_at(n, xpehh) + (((size_t)slot_list_cap(n) * 2 + 15) & ~(size_t)15);
 }
 
-size_t sweep_state_bytes(int n, int T) { return (size_t)sweep_npad(n, T) * 8; }
+size_t sweep_state_bytes(int n, int T) { return (size_t)sweep_npad(n, T) * 4; }
 size_t sweep_elements(int n, int T) { return (size_t)sweep_npad(n, T); }
 
 
 // ---- the sweep ---------------------------------------------------------------
-// One element of the sorted order is 8 bytes: x = M | M << 16, the run length
-// with its predecessor in both halves (one 16x2 SIMD minimum then updates the
-// tails of both alleles); y = bit index of the haplotype in the row | its
-// alleles at the kBlock markers of the current block << 16 (bit 16 + j: the
-// j-th marker of the block in sweep order).  At the start of each block the
-// CTA transposes the block's kBlock rows (staged by cp.async) into a table of
-// 16-bit allele words indexed by bit index, and every element picks up its
-// word; a marker then reads its allele from the element itself.
-//
-// Shared memory: the np elements (one buffer: every thread holds its E
-// elements in registers between the two passes, so the placement can
-// overwrite them in place), the row block, the allele table (its entry past
-// the rows, at the padding elements' bit index, is all ones: padding elements
-// sort after every real haplotype and never touch a real element's run
-// length), the warp totals, a core's first-window counts and offsets, and the
-// stage's core bitmap.  T threads (32 to 1024), at most EMAX <= 24 elements
-// each.
-__host__ __device__ constexpr int sweep_min_ctas(int T)
-{
-    return T == 1024 ? 1 : (T == 512 ? 1 : (T == 256 ? 3 : 512 / T));
-}
-
-// 32 x 32 bit transpose across a warp: lane l holds row l on entry and, on
-// exit, bit j of lane l is bit l of row j.
-__device__ __forceinline__ unsigned warp_transpose32(unsigned x)
-{
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int k = 16; k > 0; k >>= 1) {
-        const unsigned mask = k == 16 ? 0x0000FFFFu : k == 8 ? 0x00FF00FFu : k == 4 ? 0x0F0F0F0Fu
-                            : k == 2 ? 0x33333333u : 0x55555555u;
-        const unsigned y = __shfl_xor_sync(FULLMASK, x, k);
-        x = (lane & k) ? ((x & ~mask) | ((y >> k) & mask)) : ((x & mask) | ((y & mask) << k));
-    }
-    return x;
-}
-
-// Optional self-checks of the sorting CTA's indices (a debugging build with
-// -DSELSCAN_SWEEP_CHECKS=1): an index out of range writes -(1000 + the line
-// of the check) to the error word and the access is skipped.
-#ifndef SELSCAN_SWEEP_CHECKS
-#define SELSCAN_SWEEP_CHECKS 0
-#endif
-#define SWEEP_CHECK(cond) \
-    (SELSCAN_SWEEP_CHECKS && !(cond) ? (atomicExch(w.err, -(1000 + __LINE__)), false) : true)
-
+// Shared memory: two buffers of np packed elements (bit index of the haplotype
+// in the row | run length with its predecessor << 16), a ring of kRowRing row
+// buffers (filled by cp.async, each with one extra all-ones word), the warp
+// totals, a core's first-window counts and offsets, and the stage's core
+// bitmap.  Positions n..np-1 hold padding elements whose allele is that
+// all-ones word: they sort after every real haplotype and never touch a real
+// element's run length.  T threads (32 to 512); EMAX bounds the elements per
+// thread (at most 32, one allele bit each in a 32-bit mask), up to 24 stay in
+// registers between the two passes.
 template <int T, int EMAX>
-__global__ void __launch_bounds__(T, sweep_min_ctas(T)) sweep_kernel(SweepArgs w)
+__global__ void __launch_bounds__(T, T == 512 ? 2 : (T == 256 ? 3 : 512 / T)) sweep_kernel(SweepArgs w)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    static_assert(EMAX <= 24 && EMAX % 2 == 0, "elements per thread");
+    constexpr bool CACHE = EMAX <= 24;
     const int n = w.n;
     const int E = sweep_e(n, T);
     const int np = E * T;
-    const int W = w.a.W;
-    const int W32 = 2 * W;
-    const int W32r = sweep_w32r(W32);
+    const int W32 = 2 * w.a.W;
+    const int W32r = (W32 + 4) & ~3;             // >= W32 + 1
     const unsigned pad_bi = 32u * (unsigned)W32; // bit index of the padding elements
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr int NW = T / 32;
-    uint2 *P = (uint2 *)smem;                    // the elements
-    unsigned *Rb = (unsigned *)(P + np);         // row r of the block at Rb + r * W32r
-    unsigned short *AT = (unsigned short *)(Rb + kBlock * W32r);   // allele table
-    unsigned *wsum = (unsigned *)((unsigned char *)AT + sweep_at_bytes(W32));
+    unsigned *P0 = (unsigned *)smem;             // buffer b at P0 + b * np
+    unsigned *R0 = P0 + 2 * np;                  // row ring: slot r at R0 + r * W32r
+    unsigned *wsum = R0 + kRowRing * W32r;
     unsigned *hcnt = wsum + 2 * NW;              // a core's first window: per-step counts,
     unsigned *hoff = hcnt + 65;                  // then cursors and (at [64]) W1
     unsigned *cbits = hoff + 65;                 // the stage's cores that pass the filter
@@ -228,31 +184,32 @@ __global__ void __launch_bounds__(T, sweep_min_ctas(T)) sweep_kernel(SweepArgs w
         xlast = klo;
     }
     const long long step = dir == 0 ? 1 : -1;
-    uint2 *st = (uint2 *)w.st + (size_t)blockIdx.x * np;
+    unsigned *st = (unsigned *)w.st + (size_t)blockIdx.x * np;
 
     if (blockIdx.x == 0 && tid == 0) *w.walk_head = 0ull;   // the next walk launch's slot counter
     // ---- state in
     if (w.stage == 0) {
-        for (int t = tid; t < np; t += T) P[t] = make_uint2(0u, t < n ? bit_index(w, t) : pad_bi);
+        for (int t = tid; t < np; t += T) P0[t] = t < n ? bit_index(w, t) : pad_bi;
     } else {
-        for (int t = tid; t < np; t += T) P[t] = st[t];
+        for (int t = tid; t < np; t += T) P0[t] = st[t];
     }
-    if (tid == 0) AT[pad_bi] = 0xFFFFu;
     const unsigned long long *hap64 = (const unsigned long long *)w.a.hap;
     const long long ld = w.a.ld;
+    const int W = w.a.W;
     const long long nq = (xlast - xfirst) * step + 1;   // markers of this launch
-    // rows of block b (markers kBlock b .. in sweep order) into the row block
-    auto fetch_block = [&](long long b) {
-        const long long q0 = b * kBlock;
-        for (int i = tid; i < kBlock * W; i += T) {
-            const int r = i / W, t = i - r * W;
-            if (q0 + r < nq && SWEEP_CHECK(xfirst + (q0 + r) * step >= 0 && xfirst + (q0 + r) * step < m))
-                cp_async8(Rb + r * W32r + 2 * t, hap64 + (xfirst + (q0 + r) * step) * ld + t);
+    // row q (in sweep order) goes to ring slot q % kRowRing, kRowRing - 1 rows ahead
+    auto fetch_row = [&](long long q) {
+        if (q < nq) {
+            unsigned *dst = R0 + (q & (kRowRing - 1)) * W32r;
+            const unsigned long long *src = hap64 + (xfirst + q * step) * ld;
+            for (int t = tid; t < W; t += T) cp_async8(dst + 2 * t, src + t);
         }
         cp_async_commit();
     };
-    fetch_block(0);
+    for (int q = 0; q < kRowRing; ++q) fetch_row(q);
     for (int t = tid; t < 64; t += T) hcnt[t] = 0u;
+    for (int r = 0; r < kRowRing; ++r)          // the padding elements' all-ones word
+        if (tid < W32r - W32) R0[r * W32r + W32 + tid] = 0xFFFFFFFFu;
     {
         const int nrc = (int)(khi - klo);
         for (int r0 = 0; r0 < nrc; r0 += T) {
@@ -262,60 +219,44 @@ __global__ void __launch_bounds__(T, sweep_min_ctas(T)) sweep_kernel(SweepArgs w
             if (lane == 0 && r0 + warp * 32 < nrc) cbits[(r0 >> 5) + warp] = bits;
         }
     }
-    // the core bitmap (and the padding entry of the allele table) must be
-    // visible to every thread before the first marker reads it: the first
-    // marker of a later stage is always a core
+    cp_async_wait<kRowRing - 1>();               // row 0
     __syncthreads();
 
+    int cur = 0;
     const int base = tid * E;
+    unsigned val[CACHE ? EMAX : 1];
     long long q = 0;
     for (long long x = xfirst;; x += step, ++q) {
         const bool more = x != xlast;
         const bool is_core = x >= klo && x < khi;
         const bool wr = is_core && ((cbits[(x - klo) >> 5] >> ((x - klo) & 31)) & 1u);
-        const int jb = (int)(q & (kBlock - 1));
-        if (jb == 0) {
-            // a new block: transpose its rows into the allele table (one warp
-            // per 32-bit column), then fetch the next block into the row block
-            cp_async_wait<0>();
-            __syncthreads();
-            for (int col = warp; col < W32; col += NW) {
-                const unsigned v = warp_transpose32(lane < kBlock ? Rb[lane * W32r + col] : 0u);
-                AT[32 * col + lane] = (unsigned short)v;
-            }
-            __syncthreads();
-            fetch_block(q / kBlock + 1);
-        }
 
+        const unsigned *Pc = P0 + cur * np;
+        const unsigned *row = R0 + (q & (kRowRing - 1)) * W32r;
         // pass 1: alleles, the new run lengths as far as this segment decides
         // them, and the segment summary.  Both tails live in one word (allele
         // 0 low, 1 high).  Run lengths stay at most 65,000 (a chunk plus its
         // warm-up spans at most 65,000 markers), so adding one to each half
-        // after the minimum with a run length never carries.  The first element
-        // of each allele in the segment gets its prefix tail after placement.
-        const int sh = 15 - jb;                   // allele bit 16 + jb to bit 31
+        // never carries.  The first element of each allele in the segment gets
+        // its prefix tail after placement.
         unsigned vmask = 0u, allw = 0xFFFFFFFFu, mn01 = 0xFFFFFFFFu;
-        uint2 cv[EMAX];
 #pragma unroll
-        for (int e = 0; e < EMAX; e += 2) {
+        for (int e = 0; e < EMAX; e += 4) {
             if (e < E) {
-                const uint4 q2 = *(const uint4 *)(P + base + e);
-                const unsigned ex[2] = {q2.x, q2.z}, ey[2] = {q2.y, q2.w};
+                // 16-byte loads: a thread's segment starts at 16 E bytes, and
+                // eight lanes at that stride cover distinct banks
+                const uint4 q = *(const uint4 *)(Pc + base + e);
+                const unsigned q4[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const unsigned xx = ex[h];
-                    unsigned yy = ey[h];
-                    if (jb == 0) {
-                        unsigned ai = yy & 0xFFFFu;
-                        if (!SWEEP_CHECK(ai <= pad_bi)) ai = pad_bi;
-                        yy = (yy & 0xFFFFu) | ((unsigned)AT[ai] << 16);
-                    }
-                    const unsigned vm = (unsigned)((int)(yy << sh) >> 31);   // 0 or all ones
-                    vmask |= vm & (1u << (e + h));
-                    allw = min(allw, xx);
-                    const unsigned tt = __vminu2(mn01, xx);
-                    cv[e + h] = make_uint2(__byte_perm(tt + 0x00010001u, 0u, 0x1010u ^ (vm & 0x2222u)), yy);
-                    mn01 = tt | (vm & 0xFFFF0000u) | (~vm & 0x0000FFFFu);
+                for (int h = 0; h < 4; ++h) {
+                    const unsigned pv = q4[h];
+                    const unsigned wd = row[(pv & 0xFFFFu) >> 5];
+                    const unsigned v = __funnelshift_r(wd, wd, pv) & 1u;   // bit pv % 32
+                    vmask |= v << (e + h);
+                    allw = min(allw, pv);                 // high half: the segment minimum
+                    mn01 = __vminu2(mn01, __byte_perm(pv, 0u, 0x3232u));
+                    if (CACHE) val[e + h] = __byte_perm(pv, mn01 + 0x00010001u, v ? 0x7610u : 0x5410u);
+                    mn01 |= v ? 0xFFFF0000u : 0x0000FFFFu;
                 }
             }
         }
@@ -323,7 +264,7 @@ __global__ void __launch_bounds__(T, sweep_min_ctas(T)) sweep_kernel(SweepArgs w
         const unsigned zeros = (unsigned)E - ones;
         const unsigned hp0 = zeros != 0u, hp1 = ones != 0u;
         unsigned p0 = mn01;
-        unsigned p1 = (allw & 0xFFFFu) | (zeros << 16) | (hp0 << 30) | (hp1 << 31);
+        unsigned p1 = (allw >> 16) | (zeros << 16) | (hp0 << 30) | (hp1 << 31);
         // warp inclusive scan
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
@@ -334,7 +275,8 @@ __global__ void __launch_bounds__(T, sweep_min_ctas(T)) sweep_kernel(SweepArgs w
         unsigned x0 = __shfl_up_sync(FULLMASK, p0, 1), x1 = __shfl_up_sync(FULLMASK, p1, 1);
         if (lane == 0) { x0 = kId0; x1 = kId1; }
         if (lane == 31) { wsum[2 * warp] = p0; wsum[2 * warp + 1] = p1; }
-        __syncthreads();                          // also: every element is in registers
+        __syncthreads();
+        fetch_row(q + kRowRing);                  // every thread is done with this row's slot
         // every warp scans the warp totals: its own prefix and the block total
         unsigned q0 = lane < NW ? wsum[2 * lane] : kId0;
         unsigned q1 = lane < NW ? wsum[2 * lane + 1] : kId1;
@@ -350,39 +292,69 @@ __global__ void __launch_bounds__(T, sweep_min_ctas(T)) sweep_kernel(SweepArgs w
         const unsigned tot1 = __shfl_sync(FULLMASK, q1, NW - 1);
         const unsigned n0 = (tot1 >> 16) & 0x3FFFu;
         compose(w0, w1, x0, x1);                  // this thread's exclusive prefix
-        // pass 2: place the elements (in place); the first allele-0 /
-        // allele-1 element of the segment takes its run length from the prefix
-        // (0 if it is the first of its allele overall)
+        // pass 2: place the elements; the first allele-0 / allele-1 element of
+        // the segment takes its run length from the prefix (0 if it is the
+        // first of its allele overall)
         const unsigned zs = (x1 >> 16) & 0x3FFFu;
         const unsigned os = n0 + (unsigned)base - zs;
-        {
+        unsigned z = zs, o = os;
+        unsigned *Pn = P0 + (cur ^ 1) * np;
+        if (CACHE) {
             // allele-0 elements go to zs + (elements so far) - (ones so far)
             const unsigned zk = zs + os;
-            unsigned o = os;
 #pragma unroll
             for (int e = 0; e < EMAX; ++e) {
                 if (e < E) {
                     const unsigned one = (vmask >> e) & 1u;
-                    const unsigned pos = one ? o : zk + (unsigned)e - o;
-                    if (SWEEP_CHECK(pos < (unsigned)np)) P[pos] = cv[e];
+                    Pn[one ? o : zk + (unsigned)e - o] = val[CACHE ? e : 0];
                     o += one;
                 }
             }
         }
-        if (hp0 && SWEEP_CHECK(zs < (unsigned)np)) {
-            const unsigned u = P[zs].x & 0xFFFFu;
-            const unsigned out = ((x1 >> 30) & 1u) ? min((x0 & 0xFFFFu) + 1u, u) : 0u;
-            P[zs].x = out | (out << 16);
+        if (!CACHE) {
+            // second sweep over the segment for the run lengths (large samples)
+            unsigned a0 = x0 & 0xFFFFu, a1 = x0 >> 16;
+            unsigned h0 = (x1 >> 30) & 1u, h1 = x1 >> 31;
+            z = zs;
+            o = os;
+            for (int e = 0; e < E; ++e) {
+                const unsigned q = Pc[base + e];
+                const unsigned mv = q >> 16;
+                a0 = min(a0, mv);
+                a1 = min(a1, mv);
+                const unsigned one = (vmask >> e) & 1u;
+                const unsigned mnv = one ? a1 : a0;
+                const unsigned hpv = one ? h1 : h0;
+                const unsigned out = hpv ? min(mnv + 1u, kInf16) : 0u;
+                const unsigned p = one ? o : z;
+                o += one;
+                z += one ^ 1u;
+                a1 = one ? kInf16 : a1;
+                a0 = one ? a0 : kInf16;
+                h1 |= one;
+                h0 |= one ^ 1u;
+                Pn[p] = (q & 0xFFFFu) | (out << 16);
+            }
+        } else {
+            // the first allele-0 / allele-1 element of the segment (placed at zs
+            // / os): 1 + the minimum over the prefix tail and its own span
+            if (hp0) {
+                const unsigned u = Pn[zs];
+                const unsigned out = ((x1 >> 30) & 1u) ? min((x0 & 0xFFFFu) + 1u, u >> 16) : 0u;
+                Pn[zs] = (u & 0xFFFFu) | (out << 16);
+            }
+            if (hp1) {
+                const unsigned u = Pn[os];
+                const unsigned out = (x1 >> 31) ? min((x0 >> 16) + 1u, u >> 16) : 0u;
+                Pn[os] = (u & 0xFFFFu) | (out << 16);
+            }
         }
-        if (hp1 && SWEEP_CHECK(os < (unsigned)np)) {
-            const unsigned u = P[os].x & 0xFFFFu;
-            const unsigned out = (x1 >> 31) ? min((x0 >> 16) + 1u, u) : 0u;
-            P[os].x = out | (out << 16);
-        }
+        cp_async_wait<kRowRing - 1>();           // row q + 1 has landed
         __syncthreads();
+        cur ^= 1;
 
         // ---- a core of this stage: hand its sorted state to the walk
-        if (wr && SWEEP_CHECK((dir == 0 ? (int)(x - klo) : (int)(khi - 1 - x)) < w.R)) {
+        if (wr) {
             const int r = dir == 0 ? (int)(x - klo) : (int)(khi - 1 - x);
             unsigned char *slot = w.slots + ((size_t)(dir * w.nch + c) * w.R + r) * w.slot_bytes;
             const int xp = w.a.nB > 0;
@@ -394,33 +366,32 @@ __global__ void __launch_bounds__(T, sweep_min_ctas(T)) sweep_kernel(SweepArgs w
                 else hz = e0 == m - 1 ? INT_MAX : e0 - x;
                 hdr[1] = (int)hz;
             }
-            // run lengths, 8 per 16-byte store (np is a multiple of 64, the
+            const unsigned *Ps = P0 + cur * np;
+            // run lengths, 8 per 16-byte store (np is a multiple of 512, the
             // slot's M region a multiple of 16 bytes; values past n are never
             // read), counting the boundaries of each of steps 1..64 (M in [1, 64])
-            const uint4 *P4 = (const uint4 *)P;
+            const uint4 *P4 = (const uint4 *)Ps;
             uint4 *M4 = (uint4 *)(slot + 16);
             for (int t = tid; t < (n + 7) / 8; t += T) {
-                const uint4 a = P4[4 * t], b = P4[4 * t + 1], cc = P4[4 * t + 2], dd = P4[4 * t + 3];
-                M4[t] = make_uint4(__byte_perm(a.x, a.z, 0x5410u), __byte_perm(b.x, b.z, 0x5410u),
-                                   __byte_perm(cc.x, cc.z, 0x5410u), __byte_perm(dd.x, dd.z, 0x5410u));
-                const unsigned e8[8] = {a.x, a.z, b.x, b.z, cc.x, cc.z, dd.x, dd.z};
+                const uint4 a = P4[2 * t], b = P4[2 * t + 1];
+                M4[t] = make_uint4((a.x >> 16) | (a.y & 0xFFFF0000u), (a.z >> 16) | (a.w & 0xFFFF0000u),
+                                   (b.x >> 16) | (b.y & 0xFFFF0000u), (b.z >> 16) | (b.w & 0xFFFF0000u));
+                const unsigned e8[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
 #pragma unroll
-                for (int jj = 0; jj < 8; ++jj) {
-                    const unsigned mv = e8[jj] & 0xFFFFu;
-                    if (mv - 1u < 64u && 8 * t + jj < n) atomicAdd(hcnt + mv - 1, 1u);
-                }
+                for (int j = 0; j < 8; ++j)
+                    if (e8[j] - 0x10000u < 0x400000u && 8 * t + j < n) atomicAdd(hcnt + (e8[j] >> 16) - 1, 1u);
             }
             if (xp) {                            // population of each sorted position
                 const unsigned limA = 64u * (unsigned)w.a.WA;
                 unsigned *isA = (unsigned *)(slot + slot_isa_at(n));
                 const int nw = split_nw(n);
-                for (int qq = tid; qq < nw; qq += T) {
+                for (int q = tid; q < nw; q += T) {
                     unsigned word = 0u;
                     for (int b = 0; b < 32; ++b) {
-                        const int t = qq * 32 + b;
-                        if (t < n && (P[t].y & 0xFFFFu) < limA) word |= 1u << b;
+                        const int t = q * 32 + b;
+                        if (t < n && (Ps[t] & 0xFFFFu) < limA) word |= 1u << b;
                     }
-                    isA[qq] = word;
+                    isA[q] = word;
                 }
             }
             __syncthreads();
@@ -428,56 +399,50 @@ __global__ void __launch_bounds__(T, sweep_min_ctas(T)) sweep_kernel(SweepArgs w
             // boundaries fit the slot's list
             unsigned short *soff = (unsigned short *)(slot + slot_off_at(n, xp));
             if (warp == 0) {
-                const unsigned h0 = hcnt[2 * lane], h1 = hcnt[2 * lane + 1];
-                unsigned incl = h0 + h1;
+                const unsigned c0 = hcnt[2 * lane], c1 = hcnt[2 * lane + 1];
+                unsigned incl = c0 + c1;
 #pragma unroll
                 for (int d = 1; d < 32; d <<= 1) {
                     const unsigned v = __shfl_up_sync(FULLMASK, incl, d);
                     if (lane >= d) incl += v;
                 }
-                const unsigned ex = incl - h0 - h1;
+                const unsigned ex = incl - c0 - c1;
                 const unsigned cap = (unsigned)slot_list_cap(n);
-                // steps 2 lane + 1 and 2 lane + 2 end at offsets ex + h0 and incl
-                const unsigned w1c = __popc(__ballot_sync(FULLMASK, ex + h0 <= cap)) +
-                                     __popc(__ballot_sync(FULLMASK, incl <= cap));
+                // steps 2 lane + 1 and 2 lane + 2 end at offsets ex + c0 and incl
+                const unsigned w1 = __popc(__ballot_sync(FULLMASK, ex + c0 <= cap)) +
+                                    __popc(__ballot_sync(FULLMASK, incl <= cap));
                 soff[2 * lane] = (unsigned short)min(ex, 0xFFFFu);
-                soff[2 * lane + 1] = (unsigned short)min(ex + h0, 0xFFFFu);
+                soff[2 * lane + 1] = (unsigned short)min(ex + c0, 0xFFFFu);
                 if (lane == 31) soff[64] = (unsigned short)min(incl, 0xFFFFu);
                 hoff[2 * lane] = ex;
-                hoff[2 * lane + 1] = ex + h0;
+                hoff[2 * lane + 1] = ex + c0;
                 hcnt[2 * lane] = 0u;
                 hcnt[2 * lane + 1] = 0u;
                 if (lane == 0) {
-                    hoff[64] = w1c;
-                    ((int *)slot)[2] = (int)w1c;
+                    hoff[64] = w1;
+                    ((int *)slot)[2] = (int)w1;
                     ((int *)slot)[3] = 0;
                 }
             }
             __syncthreads();
             // place the window's boundaries by step
-            const unsigned lim = hoff[64];
+            const unsigned lim = hoff[64] << 16;
             unsigned short *slist = (unsigned short *)(slot + slot_list_at(n, xp));
             for (int t = tid; t < (n + 7) / 8; t += T) {
-                const uint4 a = P4[4 * t], b = P4[4 * t + 1], cc = P4[4 * t + 2], dd = P4[4 * t + 3];
-                const unsigned e8[8] = {a.x, a.z, b.x, b.z, cc.x, cc.z, dd.x, dd.z};
+                const uint4 a = P4[2 * t], b = P4[2 * t + 1];
+                const unsigned e8[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
 #pragma unroll
-                for (int jj = 0; jj < 8; ++jj) {
-                    const unsigned mv = e8[jj] & 0xFFFFu;
-                    if (mv - 1u < lim && 8 * t + jj < n) {
-                        const unsigned at = atomicAdd(hoff + mv - 1, 1u);
-                        if (SWEEP_CHECK(at < (unsigned)slot_list_cap(n))) slist[at] = (unsigned short)(8 * t + jj);
-                    }
-                }
+                for (int j = 0; j < 8; ++j)
+                    if (e8[j] - 0x10000u < lim && 8 * t + j < n)
+                        slist[atomicAdd(hoff + (e8[j] >> 16) - 1, 1u)] = (unsigned short)(8 * t + j);
             }
-            // the elements are next overwritten after the next marker's first
-            // barrier, which every thread reaches only after this loop
         }
         if (!more) break;
     }
-    cp_async_wait<0>();                           // no copy outlives the CTA
     // ---- state out for the next stage
     if (w.stage + 1 < w.nstages) {
-        for (int t = tid; t < np; t += T) st[t] = P[t];
+        const unsigned *Ps = P0 + cur * np;
+        for (int t = tid; t < np; t += T) st[t] = Ps[t];
     }
 }
 
@@ -1081,40 +1046,25 @@ int split_walk_ctas(int n, int xpehh, int tile)
     return per_sm * (sms > 0 ? sms : 1);
 }
 
-// The instantiation for n haplotypes on T threads (at most 24 elements each).
-static void (*sweep_kernel_for(int n, int T))(SweepArgs)
-{
-    const int E = sweep_e(n, T);
-    if (E > 24) return nullptr;
-    switch (T) {
-    case 32: return E <= 8 ? sweep_kernel<32, 8> : E <= 16 ? sweep_kernel<32, 16> : sweep_kernel<32, 24>;
-    case 64: return E <= 8 ? sweep_kernel<64, 8> : E <= 16 ? sweep_kernel<64, 16> : sweep_kernel<64, 24>;
-    case 128: return E <= 8 ? sweep_kernel<128, 8> : E <= 16 ? sweep_kernel<128, 16> : sweep_kernel<128, 24>;
-    case 256: return E <= 8 ? sweep_kernel<256, 8> : E <= 16 ? sweep_kernel<256, 16> : sweep_kernel<256, 24>;
-    case 512: return E <= 8 ? sweep_kernel<512, 8> : E <= 16 ? sweep_kernel<512, 16> : sweep_kernel<512, 24>;
-    case 1024: return E <= 8 ? sweep_kernel<1024, 8> : sweep_kernel<1024, 16>;
-    default: return nullptr;
-    }
-}
-
-int sweep_ctas_per_sm(int n, int W, int T)
-{
-    void (*k)(SweepArgs) = sweep_kernel_for(n, T);
-    if (!k) return 0;
-    const size_t ssm = sweep_smem_bytes(n, W, T, 8192);
-    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm) != cudaSuccess)
-        return 0;
-    int per = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, T, ssm) != cudaSuccess) return 0;
-    return per;
-}
-
 cudaError_t launch_sweep_path(const SweepArgs &w0, cudaStream_t s)
 {
     SweepArgs w = w0;
     const size_t ssm = sweep_smem_bytes(w.n, w.a.W, w.threads, w.R);
-    void (*sweep)(SweepArgs) = sweep_kernel_for(w.n, w.threads);
-    if (!sweep) return cudaErrorInvalidValue;
+    const int E = sweep_e(w.n, w.threads);
+    void (*sweep)(SweepArgs);
+    if (w.threads == 256)
+        sweep = E <= 8 ? sweep_kernel<256, 8> : E <= 16 ? sweep_kernel<256, 16>
+              : E <= 24 ? sweep_kernel<256, 24> : sweep_kernel<256, 32>;
+    else if (w.threads == 512)
+        sweep = E <= 4 ? sweep_kernel<512, 4> : E <= 8 ? sweep_kernel<512, 8>
+              : E <= 16 ? sweep_kernel<512, 16> : E <= 24 ? sweep_kernel<512, 24>
+              : sweep_kernel<512, 32>;
+    else if (w.threads == 128)
+        sweep = E <= 8 ? sweep_kernel<128, 8> : E <= 16 ? sweep_kernel<128, 16> : sweep_kernel<128, 32>;
+    else if (w.threads == 64)
+        sweep = E <= 8 ? sweep_kernel<64, 8> : E <= 16 ? sweep_kernel<64, 16> : sweep_kernel<64, 32>;
+    else
+        sweep = E <= 8 ? sweep_kernel<32, 8> : E <= 16 ? sweep_kernel<32, 16> : sweep_kernel<32, 32>;
     cudaError_t e = cudaFuncSetAttribute(sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm);
     if (e != cudaSuccess) return e;
     const size_t wsm = (size_t)w.split_bytes * (kSplitWarps * 32 / w.split_tile);
