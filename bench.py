@@ -45,11 +45,12 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def walk_lengths(stop, pos, max_gap_bp, ipc=4):
-    """Steps computed by each walk (S values, i = 0 .. last), from its stop index."""
-    m = stop.shape[0]
-    j = np.arange(m)[:, None].repeat(ipc, 1)
-    d = (np.arange(ipc) & 1)[None, :].repeat(m, 0)
+def walk_lengths(stop, pos, max_gap_bp, ipc=4, k0=0):
+    """Steps computed by each walk (S values, i = 0 .. last), from its stop index
+    (stop holds the cores k0, k0 + 1, ... of a chromosome whose positions are pos)."""
+    m = pos.shape[0]
+    j = (k0 + np.arange(stop.shape[0]))[:, None].repeat(ipc, 1)
+    d = (np.arange(ipc) & 1)[None, :].repeat(stop.shape[0], 0)
     s = stop.astype(np.int64)
     edge = np.where(d == 0, s == j + 1, s == m - j)
     x = np.where(d == 0, j - s, j + s)
@@ -163,10 +164,12 @@ def cpu_baseline(data, budget_s=20.0, seed=1234):
                       f"; {threads} host threads)"}
 
 
-def rank_spec(workload: str, rank: int):
-    """Weak scaling: rank r scans its own chromosome (seed r) of the same shape."""
+def rank_spec(workload: str, rank: int, scaling: str = "weak"):
+    """Weak scaling: rank r scans its own chromosome (seed r) of the same shape;
+    strong scaling: every rank holds the same chromosome (seed 0) and scans its
+    share of the cores."""
     import synth
-    return synth.spec(workload, seed=rank)
+    return synth.spec(workload, seed=rank if scaling == "weak" else 0)
 
 
 def aggregate(ms: float, cores: int, world: int, device):
@@ -235,6 +238,10 @@ def main():
     ap.add_argument("--policy", default="fifo", choices=["fifo", "srpt", "ps"],
                     help="served tick composition")
     ap.add_argument("--tick-cores", type=int, default=32768, help="served cores per tick")
+    ap.add_argument("--scaling", default="strong", choices=["strong", "weak"],
+                    help="N > 1: strong = one chromosome, its cores split into contiguous ranges "
+                         "(one per rank, whole matrix on every GPU), results gathered and the "
+                         "standardisation's bin sums all-reduced; weak = one chromosome per rank")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--ref-budget", type=float, default=15.0)
@@ -271,8 +278,14 @@ def main():
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
 
-    spec = rank_spec(args.workload, rank)
+    spec = rank_spec(args.workload, rank, args.scaling)
     d = synth.generate(spec)
+    from paper_1403_6854_gb300 import shard
+    if args.scaling == "strong":
+        ranges = shard.partition(spec.m, world)
+        k0, k1 = ranges[rank]
+    else:
+        ranges, (k0, k1) = None, (0, spec.m)
     n = spec.pops[0].n
     W = spec.W
     hap, pos, gmap = sg.to_device(d.rows, d.pos, d.gmap, dev)
@@ -300,15 +313,15 @@ def main():
     ws = None
     out = None
     for _ in range(Wm):
-        out = sg.selscan_ihs(hap, n, pos, gmap, params=params,
-                             launch=sg.make_launch(**launch_fields), workspace=ws, out=out)
+        out = sg.selscan_ihs_range(hap, n, pos, gmap, k0, k1, params=params,
+                                   launch=sg.make_launch(**launch_fields), workspace=ws, out=out)
         ws = out["_workspace"]
     torch.cuda.synchronize()
     sg.check(out)
 
     gpu_id = str(torch.cuda.get_device_properties(dev).uuid)
     gpu_id = gpu_id if gpu_id.startswith("GPU-") else "GPU-" + gpu_id
-    launches_per_step = sg.selscan_launch_count(n, spec.m, sg.MODE_IHS, sg.make_launch(**launch_fields))
+    launches_per_step = sg.selscan_launch_count(n, k1 - k0, sg.MODE_IHS, sg.make_launch(**launch_fields))
     with ClockSampler(gpu_id) as clk:
         if world > 1:
             dist.barrier()
@@ -317,9 +330,9 @@ def main():
         t1 = torch.cuda.Event(enable_timing=True)
         t0.record()
         for k in range(K):
-            out = sg.selscan_ihs(hap, n, pos, gmap, params=params,
-                                 launch=sg.make_launch(events=ev[k], **launch_fields),
-                                 workspace=ws, out=out)
+            out = sg.selscan_ihs_range(hap, n, pos, gmap, k0, k1, params=params,
+                                       launch=sg.make_launch(events=ev[k], **launch_fields),
+                                       workspace=ws, out=out)
         t1.record()
         torch.cuda.synchronize()
         if world > 1:
@@ -331,7 +344,7 @@ def main():
     status = out["status"].cpu().numpy()
     stop = out["stop"].cpu().numpy()
     cores = int((status != sg.LOCUS_MAF_FILTERED).sum())
-    lens = walk_lengths(stop, d.pos, params.max_gap_bp)
+    lens = walk_lengths(stop, d.pos, params.max_gap_bp, k0=k0)
     lens[status == sg.LOCUS_MAF_FILTERED] = 0
     steps_total = int(lens.sum())
     walk_bytes = steps_total * 8 * W + int(np.maximum(lens - 1, 0).sum()) * 16
@@ -339,9 +352,27 @@ def main():
     ms_max, cores_all = aggregate(ms, cores, world, dev)
     value = cores_all * K / (ms_max / 1e3)
 
+    # the exchange of a split scan, once after the timed steps: gather of the
+    # per-core results and the two all-reduces of the standardisation's bin sums
+    exchange = None
+    if world > 1 and args.scaling == "strong":
+        mine = {f: out[f] for f in ("status", "n1", "ihh1", "ihh0", "lnratio", "stop", "digest")}
+        torch.cuda.synchronize()
+        dist.barrier()
+        a0 = time.perf_counter()
+        full = shard.gather(mine, ranges)
+        z, cnt, mean, sd = shard.normalize(shard.DeviceOps(sg), out["lnratio"], out["status"],
+                                           out["n1"], n, 100)
+        torch.cuda.synchronize()
+        exchange = {"what": "all-gather of the per-core results and the Eq. 7 bin-sum all-reduces "
+                            "(100 frequency bins), once after the timed steps",
+                    "ms": (time.perf_counter() - a0) * 1e3,
+                    "gathered_cores": int(full["status"].numel()),
+                    "bins_with_scores": int((cnt > 0).sum())}
+
     # end to end: host buffers, H2D of the inputs and D2H of the scores every step
     e2e, e2e_bufs = None, None
-    if rank == 0 and not args.no_extras:
+    if rank == 0 and world == 1 and not args.no_extras:
         h_rows = torch.from_numpy(d.rows.view(np.int64)).pin_memory()
         h_pos = torch.from_numpy(d.pos).pin_memory()
         h_gmap = torch.from_numpy(d.gmap).pin_memory()
@@ -404,7 +435,7 @@ def main():
                 "what": "algorithmic row bytes of every walk step (sum of L x 8W + 16 (L - 1)) "
                         "over the time of all walk kernels",
                 "peak_source": f"{src} hbm_gbs (MEASURED_PEAKS.json)"}
-        work = sg.selscan_sweep_work(n, spec.m, sg.MODE_IHS, sg.make_launch(**launch_fields))
+        work = sg.selscan_sweep_work(n, k1 - k0, sg.MODE_IHS, sg.make_launch(**launch_fields))
         if work is not None:
             # the dominant kernel, the sort, against the integer-pipe peak measured here
             from paper_1403_6854_gb300 import peak as int_peak
@@ -435,7 +466,8 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": "core loci/s", "n_gpus": world,
             "steps": K, "warmup": Wm, "ms_per_step": ms_max / K, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "u64+f64",
+            "scaling": args.scaling if world > 1 else "strong", "vs_baseline": None,
+            "dtype": "u64+f64",
             "data": "synthetic (seeded Li-Stephens mosaic; stands in for the paper's ms and "
                     "1000 Genomes inputs)",
             "config": {"workload": WORKLOADS[args.workload], "n_haplotypes": n, "n_snps": spec.m,
@@ -445,13 +477,18 @@ def main():
                                         launch_fields.get("schedule", 1)],
                        "launch_shape": shape,
                        "l2": "inputs larger than L2 (packed matrix 632 MB), no flush",
-                       "parallelism": f"weak: one chromosome (seed = rank) per GPU x{world}"},
+                       "parallelism": (f"strong: one chromosome, cores split into {world} "
+                                       f"contiguous ranges (rank 0: [{k0}, {k1}))"
+                                       if args.scaling == "strong" else
+                                       f"weak: one chromosome (seed = rank) per GPU x{world}")},
             "roofline": roofline,
             "gpu_launches": launches_per_step * K,
             "clocks": clk.summary(),
         }
         if e2e:
             line["e2e"] = e2e
+        if exchange:
+            line["exchange"] = exchange
         if cpu:
             line["cpu_baseline"] = cpu
         line.update(extras)
