@@ -141,7 +141,11 @@ typedef struct {
                                   it holds at most 32 haplotypes per thread */
     int32_t sweep_split_tile;  /* sweep schedule: lanes per split walk, 32 or 16 (two walks
                                   per warp) (0 = default) */
-    int32_t reserved0;
+    int32_t sweep_ctas_per_sm; /* sweep schedule, 256- and 512-thread sorts: sorting CTAs per SM
+                                  over both directions, which sets the chunk count (0 = 3 of
+                                  256 threads, 2 of 512; at most 2,048 threads per SM; a count
+                                  the SM cannot hold at once runs in waves).  More CTAs hide
+                                  more latency, but every chunk sorts its warm-up again */
     void *sweep_done_event;    /* optional cudaEvent_t, recorded after the sorting kernel of the
                                   first stage (sweep schedule): with walk_begin_event it times
                                   the sort of a one-stage scan on its own */

@@ -51,7 +51,7 @@ class selscan_launch(ctypes.Structure):
                 ("walk_begin_event", ctypes.c_void_p), ("walk_end_event", ctypes.c_void_p),
                 ("big_group_entries", ctypes.c_int32), ("sweep_warmup", ctypes.c_int32),
                 ("sweep_stage_cores", ctypes.c_int32), ("sweep_threads", ctypes.c_int32),
-                ("sweep_split_tile", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("sweep_split_tile", ctypes.c_int32), ("sweep_ctas_per_sm", ctypes.c_int32),
                 ("sweep_done_event", ctypes.c_void_p)]
 
 
@@ -208,7 +208,8 @@ def make_launch(schedule: int = SCHED_DEFAULT, warps_per_cta: int = 0, ctas_per_
                 smem_entries: int = 0, probe_steps: int = 0, window_rows: int = 0,
                 cores_per_fetch: int = 0, min_ctas_per_sm: int = 0, big_group_entries: int = 0,
                 sweep_warmup: int = 0, sweep_stage_cores: int = 0, sweep_threads: int = 0,
-                sweep_split_tile: int = 0, events=None) -> selscan_launch:
+                sweep_split_tile: int = 0, sweep_ctas_per_sm: int = 0,
+                events=None) -> selscan_launch:
     """events: optional (begin, end) torch.cuda.Event pair bracketing the walk kernels,
     or (begin, end, sort_done) with an event recorded after the first stage's sort."""
     L = selscan_launch(schedule, warps_per_cta, ctas_per_sm, smem_entries, probe_steps,
@@ -218,6 +219,7 @@ def make_launch(schedule: int = SCHED_DEFAULT, warps_per_cta: int = 0, ctas_per_
     L.sweep_stage_cores = sweep_stage_cores
     L.sweep_threads = sweep_threads
     L.sweep_split_tile = sweep_split_tile
+    L.sweep_ctas_per_sm = sweep_ctas_per_sm
     if events is not None:
         L.walk_begin_event = ctypes.c_void_p(events[0].cuda_event)
         L.walk_end_event = ctypes.c_void_p(events[1].cuda_event)

@@ -93,7 +93,9 @@ SweepPlan make_sweep_plan(int n_total, long long m, int mode, const selscan_laun
     while (w.threads < 512 && n_total > w.threads * 32) w.threads *= 2;
     // the resident sweep CTAs split over both directions: three 256-thread
     // CTAs per SM, two of 512, sixteen warps of the narrow widths
-    const int per_sm = w.threads == 512 ? 2 : (w.threads == 256 ? 3 : 512 / w.threads);
+    int per_sm = w.threads == 512 ? 2 : (w.threads == 256 ? 3 : 512 / w.threads);
+    const int want_sm = L ? L->sweep_ctas_per_sm : 0;
+    if (want_sm > 0 && w.threads >= 256) per_sm = want_sm < 2048 / w.threads ? want_sm : 2048 / w.threads;
     const int nmax = (per_sm * sms) / 2;
     if (nch > nmax) nch = nmax;
     if (nch < 1) nch = 1;
