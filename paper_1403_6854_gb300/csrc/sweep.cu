@@ -649,37 +649,30 @@ struct ClassWalk {
 };
 
 // Reductions of S caused by the boundaries b that part at this step
-// (iHS: d0 class 0, d1 class 1; XPEHH: d0 A, d1 B, d2 pooled).
+// (iHS: d0 class 0, d1 class 1; XPEHH: d0 A, d1 B, d2 pooled).  The pairs
+// whose common run ends exactly at step i are counted once, at the leftmost
+// boundary b of their span with M[b] = i: the first member lies in [p, b),
+// p the last run start before b with M <= i (the bitmap A, this step's
+// starts included), the second in [b, e), e the first old start after b
+// (M < i, the bitmap O).  So boundary b removes (b - p)(e - b) pairs, and
+// per population the products of its members on either side.
 template <int NPOP>
 __device__ __forceinline__ void split_terms(const SplitSmem &s, int b, int n, int n0, int &d0,
                                             int &d1, int &d2)
 {
     const int p = prev_set<true>(s, b);
-    const int rr = next_set<true>(s, b, n);
-    const bool old = (s.O[p >> 5] >> (p & 31)) & 1u;
-    // the old run [p, e) that b splits ends at the first old start after b: rr
-    // itself unless rr is another boundary of this step
-    int e = 0;
-    if (old) e = ((s.O[rr >> 5] >> (rr & 31)) & 1u) ? rr : next_set<false>(s, rr, n);
+    const int e = next_set<false>(s, b, n);
     if (NPOP == 2) {
-        const unsigned ab = count_a(s, b), ar = count_a(s, rr);
-        const unsigned la = ar - ab, lb = (unsigned)(rr - b) - la;
-        d0 += c2i(la);
-        d1 += c2i(lb);
-        d2 += c2i((unsigned)(rr - b));
-        if (old) {
-            const unsigned ap = count_a(s, p), ae = count_a(s, e);
-            const unsigned l1a = ab - ap, l1b = (unsigned)(b - p) - l1a;
-            const unsigned l2a = ae - ap, l2b = (unsigned)(e - p) - l2a;
-            d0 += c2i(l1a) - c2i(l2a);
-            d1 += c2i(l1b) - c2i(l2b);
-            d2 += c2i((unsigned)(b - p)) - c2i((unsigned)(e - p));
-        }
+        const unsigned ap = count_a(s, p), ab = count_a(s, b), ae = count_a(s, e);
+        const unsigned l1a = ab - ap, l2a = ae - ab;
+        const unsigned l1b = (unsigned)(b - p) - l1a, l2b = (unsigned)(e - b) - l2a;
+        d0 -= (int)(l1a * l2a);
+        d1 -= (int)(l1b * l2b);
+        d2 -= (b - p) * (e - b);
     } else {
-        int dd = c2i((unsigned)(rr - b));
-        if (old) dd += c2i((unsigned)(b - p)) - c2i((unsigned)(e - p));
-        if (b < n0) d0 += dd;
-        else d1 += dd;
+        const int dd = (b - p) * (e - b);
+        if (b < n0) d0 -= dd;
+        else d1 -= dd;
     }
 }
 
