@@ -640,11 +640,12 @@ __device__ const unsigned short *build_window(const Tile &tile, const SplitSmem 
 // pipe on this GPU); with 32-lane tiles the additions are exactly those of the
 // per-step walk, so a walk handed over to it gives the same bits.
 struct ClassWalk {
-    unsigned D, S, prev;
+    unsigned D, S;
     unsigned rec;                   // this lane's step term of the current block (0: none)
-    unsigned long long dig, numD;   // numD = cut_num * D
+    unsigned long long dig;
+    unsigned thr;                   // stop at the first S < thr, i.e. cut_den * S < cut_num * D
     double acc;                     // this lane's partial trapezoid sum
-    int status, stop;
+    int stop;                       // the step the walk stopped at (status: at the end)
     bool active;
 };
 
@@ -826,13 +827,15 @@ __global__ void __launch_bounds__(kSplitWarps * 32, SPLIT_MIN_CTAS) split_walk_k
         bool any = false;
 #pragma unroll
         for (int q = 0; q < NWK; ++q) {
-            cw[q].numD = (unsigned long long)w.a.cut_num * cw[q].D;
-            cw[q].prev = cw[q].S;
+            {
+                const unsigned long long t =
+                    ((unsigned long long)w.a.cut_num * cw[q].D + w.a.cut_den - 1u) / w.a.cut_den;
+                cw[q].thr = t < 0xFFFFFFFFull ? (unsigned)t : 0xFFFFFFFFu;
+            }
             cw[q].dig = cw[q].S;
             cw[q].acc = 0.0;
             cw[q].rec = 0u;
             cw[q].stop = 0;
-            cw[q].status = cw[q].D == 0u ? WALK_UNDEFINED : WALK_OK;
             cw[q].active = cw[q].D != 0u;
             any |= cw[q].active;
         }
@@ -938,7 +941,7 @@ __global__ void __launch_bounds__(kSplitWarps * 32, SPLIT_MIN_CTAS) split_walk_k
                 dA += (unsigned long long)ii * SA;
                 dB += (unsigned long long)ii * SB;
                 q.dig += (unsigned long long)ii * q.S;
-                const bool stop = (unsigned long long)w.a.cut_den * q.S < q.numD;
+                const bool stop = q.S < q.thr;
                 if (stop && !w.a.crossing) { q.stop = (int)i; q.active = false; }
                 else {
                     if (own) {
@@ -956,11 +959,10 @@ __global__ void __launch_bounds__(kSplitWarps * 32, SPLIT_MIN_CTAS) split_walk_k
                     if (!q.active) continue;
                     q.S += (unsigned)(c_ ? d1 : d0);
                     q.dig += (unsigned long long)ii * q.S;
-                    const bool stop = (unsigned long long)w.a.cut_den * q.S < q.numD;
+                    const bool stop = q.S < q.thr;
                     if (stop && !w.a.crossing) { q.stop = (int)i; q.active = false; continue; }
-                    if (own) q.rec = q.prev + q.S;
+                    if (own) q.rec = 2u * q.S - (unsigned)(c_ ? d1 : d0);   // S(i - 1) + S(i)
                     if (stop) { q.stop = (int)i; q.active = false; continue; }
-                    q.prev = q.S;
                 }
             }
             any = false;
@@ -986,6 +988,7 @@ __global__ void __launch_bounds__(kSplitWarps * 32, SPLIT_MIN_CTAS) split_walk_k
                 // iHS items: (allele 1, down), (allele 1, up), (allele 0, down), (allele 0, up)
                 const uint32_t item = NPOP == 2 ? (uint32_t)(k * 2 + dir)
                                                 : (uint32_t)(k * 4 + (q_ == 1 ? 0 : 2) + dir);
+                int status = q.D == 0u ? WALK_UNDEFINED : WALK_OK;
                 if (q.active) {
                     if (fin == WALK_UNFINISHED) {
                         const unsigned long long slot2 = atomicAdd(&sk.q->n2, 1ull);
@@ -993,10 +996,10 @@ __global__ void __launch_bounds__(kSplitWarps * 32, SPLIT_MIN_CTAS) split_walk_k
                         sk.key2[slot2] = bucket_of((float)((double)q.S / (double)q.D));
                         continue;
                     }
-                    q.status = fin;
+                    status = fin;
                     q.stop = (int)i;
                 }
-                sk.item_status[item] = (int8_t)q.status;
+                sk.item_status[item] = (int8_t)status;
                 sk.stop[item] = q.stop;
                 if (NPOP == 2) {
                     sk.item_ihh[2 * (size_t)item] = DA ? q.acc / (2.0 * (double)DA) : 0.0;
