@@ -136,13 +136,14 @@ size_t sweep_elements(int n, int T) { return (size_t)sweep_npad(n, T); }
 // element's run length.  T threads (32 to 512); EMAX bounds the elements per
 // thread (at most 32, one allele bit each in a 32-bit mask), up to 24 stay in
 // registers between the two passes.
-template <int T, int EMAX>
+template <int T, int EMAX, bool EXACT = false>
 __global__ void __launch_bounds__(T, T == 512 ? 2 : (T == 256 ? 3 : 512 / T)) sweep_kernel(SweepArgs w)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr bool CACHE = EMAX <= 24;
     const int n = w.n;
-    const int E = sweep_e(n, T);
+    // EXACT: every thread holds exactly EMAX elements (no per-element guards)
+    const int E = EXACT ? EMAX : sweep_e(n, T);
     const int np = E * T;
     const int W32 = 2 * w.a.W;
     const int W32r = (W32 + 4) & ~3;             // >= W32 + 1
@@ -1049,8 +1050,10 @@ cudaError_t launch_sweep_path(const SweepArgs &w0, cudaStream_t s)
     const int E = sweep_e(w.n, w.threads);
     void (*sweep)(SweepArgs);
     if (w.threads == 256)
-        sweep = E <= 8 ? sweep_kernel<256, 8> : E <= 16 ? sweep_kernel<256, 16>
-              : E <= 24 ? sweep_kernel<256, 24> : sweep_kernel<256, 32>;
+        sweep = E == 4 ? sweep_kernel<256, 4, true> : E == 8 ? sweep_kernel<256, 8, true>
+              : E == 12 ? sweep_kernel<256, 12, true> : E == 16 ? sweep_kernel<256, 16, true>
+              : E == 20 ? sweep_kernel<256, 20, true> : E == 24 ? sweep_kernel<256, 24, true>
+              : sweep_kernel<256, 32>;
     else if (w.threads == 512)
         sweep = E <= 4 ? sweep_kernel<512, 4> : E <= 8 ? sweep_kernel<512, 8>
               : E <= 16 ? sweep_kernel<512, 16> : E <= 24 ? sweep_kernel<512, 24>
