@@ -253,15 +253,18 @@ __global__ void __launch_bounds__(T, T == 512 ? 2 : (T == 256 ? 3 : 512 / T)) sw
                     const unsigned pv = q4[h];
                     const unsigned wd = row[(pv & 0xFFFFu) >> 5];
                     const unsigned v = __funnelshift_r(wd, wd, pv) & 1u;   // bit pv % 32
-                    vmask |= v << (e + h);
+                    vmask = vmask + vmask + v;            // element e at bit E - 1 - e
                     allw = min(allw, pv);                 // high half: the segment minimum
                     mn01 = __vminu2(mn01, __byte_perm(pv, 0u, 0x3232u));
-                    if (CACHE) val[e + h] = __byte_perm(pv, mn01 + 0x00010001u, v ? 0x7610u : 0x5410u);
-                    mn01 |= v ? 0xFFFF0000u : 0x0000FFFFu;
+                    // selectors by multiply-add: v ? 0x7610 : 0x5410, and the tail of
+                    // allele v restarted (v ? 0x7610 : 0x3254 with 0xFFFF in the other half)
+                    if (CACHE) val[e + h] = __byte_perm(pv, mn01 + 0x00010001u, 0x5410u + v * 0x2200u);
+                    mn01 = __byte_perm(mn01, 0xFFFFFFFFu, 0x3254u + v * 0x43BCu);
                 }
             }
         }
         const unsigned ones = (unsigned)__popc(vmask);
+        vmask <<= 32 - E;                         // element e at bit 31 - e
         const unsigned zeros = (unsigned)E - ones;
         const unsigned hp0 = zeros != 0u, hp1 = ones != 0u;
         unsigned p0 = mn01;
@@ -306,7 +309,7 @@ __global__ void __launch_bounds__(T, T == 512 ? 2 : (T == 256 ? 3 : 512 / T)) sw
 #pragma unroll
             for (int e = 0; e < EMAX; ++e) {
                 if (e < E) {
-                    const unsigned one = (vmask >> e) & 1u;
+                    const unsigned one = (vmask >> (31 - e)) & 1u;
                     Pn[one ? o : zk + (unsigned)e - o] = val[CACHE ? e : 0];
                     o += one;
                 }
@@ -323,7 +326,7 @@ __global__ void __launch_bounds__(T, T == 512 ? 2 : (T == 256 ? 3 : 512 / T)) sw
                 const unsigned mv = q >> 16;
                 a0 = min(a0, mv);
                 a1 = min(a1, mv);
-                const unsigned one = (vmask >> e) & 1u;
+                const unsigned one = (vmask >> (31 - e)) & 1u;
                 const unsigned mnv = one ? a1 : a0;
                 const unsigned hpv = one ? h1 : h0;
                 const unsigned out = hpv ? min(mnv + 1u, kInf16) : 0u;
