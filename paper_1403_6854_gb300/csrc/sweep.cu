@@ -58,22 +58,31 @@ __host__ __device__ inline int split_nw(int n) { return (n + 32) >> 5; }   // bi
 // A segment of the current order summarised as: the running minimum of the
 // run lengths since its last allele-0 / allele-1 element (or over the whole
 // segment if it has none) -- the "tails" -- the minimum over the segment, the
-// number of allele-0 elements, and whether each allele occurs.  Packed in
-// two words: A = tail0 | tail1 << 16; B = min | zeros << 16 | seen0 << 30 |
-// seen1 << 31.  compose(L, R) replaces R by the summary of L followed by R;
-// both tails are continued through R with one 16-bit SIMD minimum.
-__device__ __forceinline__ void compose(unsigned lA, unsigned lB, unsigned &rA, unsigned &rB)
+// number of allele-0 elements, and whether each allele occurs.  Three words:
+// A = tail0 | tail1 << 16; B = the minimum in both halves; C = zeros |
+// seen0 << 15 | seen1 << 31 (zeros < 2^14; the flags sit on byte sign bits,
+// so one byte permute in sign-replicate mode turns them into the halfword
+// mask of the tails that R decides).  compose(L, R) replaces R by the summary
+// of L followed by R: both tails are continued through R with one 16-bit
+// SIMD minimum.
+__device__ __forceinline__ unsigned seen_mask(unsigned c)
 {
-    const unsigned rmin2 = __byte_perm(rB, 0u, 0x1010u);          // R's minimum in both halves
-    const unsigned cont = __vminu2(lA, rmin2);                     // L's tails continued through R
-    const unsigned f = rB >> 30;                                   // alleles present in R
-    const unsigned keep = ((f & 1u) ? 0x0000FFFFu : 0u) | ((f & 2u) ? 0xFFFF0000u : 0u);
-    rA = (rA & keep) | (cont & ~keep);
-    const unsigned mn = min(lB & 0xFFFFu, rB & 0xFFFFu);
-    rB = mn | ((lB & 0x3FFF0000u) + (rB & 0x3FFF0000u)) | ((lB | rB) & 0xC0000000u);
+    unsigned r;   // bytes 0, 1 <- sign of byte 1 (seen0); bytes 2, 3 <- sign of byte 3 (seen1)
+    asm("prmt.b32 %0, %1, 0, 0xBB99;" : "=r"(r) : "r"(c));
+    return r;
 }
-constexpr unsigned kId0 = 0xFFFFFFFFu;
-constexpr unsigned kId1 = 0x0000FFFFu;
+__device__ __forceinline__ void compose(unsigned lA, unsigned lB, unsigned lC, unsigned &rA,
+                                        unsigned &rB, unsigned &rC)
+{
+    const unsigned cont = __vminu2(lA, rB);                        // L's tails continued through R
+    const unsigned keep = seen_mask(rC);                           // the tails R decides
+    rA = (rA & keep) | (cont & ~keep);
+    rB = __vminu2(lB, rB);
+    rC = ((lC + rC) & 0x3FFFu) | ((lC | rC) & 0x80008000u);
+}
+constexpr unsigned kIdA = 0xFFFFFFFFu;
+constexpr unsigned kIdB = 0xFFFFFFFFu;
+constexpr unsigned kIdC = 0u;
 
 // Asynchronous global -> shared copies of 8 bytes (rows start on 8-byte
 // boundaries whatever their stride), in per-thread commit groups.
@@ -112,7 +121,7 @@ __host__ __device__ inline size_t slot_list_at(int n, int xpehh) { return slot_o
 size_t sweep_smem_bytes(int n, int W, int T, int R)
 {
     const int W32 = ((2 * W) + 4) & ~3;
-    return (size_t)sweep_npad(n, T) * 4 * 2 + (size_t)W32 * 4 * kRowRing + T / 32 * 8 + 2 * 65 * 4 +
+    return (size_t)sweep_npad(n, T) * 4 * 2 + (size_t)W32 * 4 * kRowRing + T / 32 * 12 + 2 * 65 * 4 +
            (size_t)((R + 31) / 32) * 4;
 }
 
@@ -153,7 +162,7 @@ __global__ void __launch_bounds__(T, T == 512 ? 2 : (T == 256 ? 3 : 512 / T)) sw
     unsigned *P0 = (unsigned *)smem;             // buffer b at P0 + b * np
     unsigned *R0 = P0 + 2 * np;                  // row ring: slot r at R0 + r * W32r
     unsigned *wsum = R0 + kRowRing * W32r;
-    unsigned *hcnt = wsum + 2 * NW;              // a core's first window: per-step counts,
+    unsigned *hcnt = wsum + 3 * NW;              // a core's first window: per-step counts,
     unsigned *hoff = hcnt + 65;                  // then cursors and (at [64]) W1
     unsigned *cbits = hoff + 65;                 // the stage's cores that pass the filter
 
@@ -251,7 +260,8 @@ __global__ void __launch_bounds__(T, T == 512 ? 2 : (T == 256 ? 3 : 512 / T)) sw
 #pragma unroll
                 for (int h = 0; h < 4; ++h) {
                     const unsigned pv = q4[h];
-                    const unsigned wd = row[(pv & 0xFFFFu) >> 5];
+                    // the word of bit index pv & 0xFFFF, (pv & 0xFFFF) >> 5, by multiplies
+                    const unsigned wd = row[__umulhi(pv * 65536u, 2048u)];
                     const unsigned v = __funnelshift_r(wd, wd, pv) & 1u;   // bit pv % 32
                     vmask = vmask + vmask + v;            // element e at bit E - 1 - e
                     allw = min(allw, pv);                 // high half: the segment minimum
@@ -268,38 +278,44 @@ __global__ void __launch_bounds__(T, T == 512 ? 2 : (T == 256 ? 3 : 512 / T)) sw
         const unsigned zeros = (unsigned)E - ones;
         const unsigned hp0 = zeros != 0u, hp1 = ones != 0u;
         unsigned p0 = mn01;
-        unsigned p1 = (allw >> 16) | (zeros << 16) | (hp0 << 30) | (hp1 << 31);
+        unsigned p1 = (allw >> 16) * 0x00010001u;
+        unsigned p2 = zeros | (hp0 << 15) | (hp1 << 31);
         // warp inclusive scan
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
             const unsigned o0 = __shfl_up_sync(FULLMASK, p0, d);
             const unsigned o1 = __shfl_up_sync(FULLMASK, p1, d);
-            if (lane >= d) compose(o0, o1, p0, p1);
+            const unsigned o2 = __shfl_up_sync(FULLMASK, p2, d);
+            if (lane >= d) compose(o0, o1, o2, p0, p1, p2);
         }
         unsigned x0 = __shfl_up_sync(FULLMASK, p0, 1), x1 = __shfl_up_sync(FULLMASK, p1, 1);
-        if (lane == 0) { x0 = kId0; x1 = kId1; }
-        if (lane == 31) { wsum[2 * warp] = p0; wsum[2 * warp + 1] = p1; }
+        unsigned x2 = __shfl_up_sync(FULLMASK, p2, 1);
+        if (lane == 0) { x0 = kIdA; x1 = kIdB; x2 = kIdC; }
+        if (lane == 31) { wsum[3 * warp] = p0; wsum[3 * warp + 1] = p1; wsum[3 * warp + 2] = p2; }
         __syncthreads();
         fetch_row(q + kRowRing);                  // every thread is done with this row's slot
         // every warp scans the warp totals: its own prefix and the block total
-        unsigned q0 = lane < NW ? wsum[2 * lane] : kId0;
-        unsigned q1 = lane < NW ? wsum[2 * lane + 1] : kId1;
+        unsigned q0 = lane < NW ? wsum[3 * lane] : kIdA;
+        unsigned q1 = lane < NW ? wsum[3 * lane + 1] : kIdB;
+        unsigned q2 = lane < NW ? wsum[3 * lane + 2] : kIdC;
 #pragma unroll
         for (int d = 1; d < NW; d <<= 1) {
             const unsigned o0 = __shfl_up_sync(FULLMASK, q0, d);
             const unsigned o1 = __shfl_up_sync(FULLMASK, q1, d);
-            if (lane >= d) compose(o0, o1, q0, q1);
+            const unsigned o2 = __shfl_up_sync(FULLMASK, q2, d);
+            if (lane >= d) compose(o0, o1, o2, q0, q1, q2);
         }
         unsigned w0 = __shfl_sync(FULLMASK, q0, (warp + 31) & 31);
         unsigned w1 = __shfl_sync(FULLMASK, q1, (warp + 31) & 31);
-        if (warp == 0) { w0 = kId0; w1 = kId1; }
-        const unsigned tot1 = __shfl_sync(FULLMASK, q1, NW - 1);
-        const unsigned n0 = (tot1 >> 16) & 0x3FFFu;
-        compose(w0, w1, x0, x1);                  // this thread's exclusive prefix
+        unsigned w2 = __shfl_sync(FULLMASK, q2, (warp + 31) & 31);
+        if (warp == 0) { w0 = kIdA; w1 = kIdB; w2 = kIdC; }
+        const unsigned tot2 = __shfl_sync(FULLMASK, q2, NW - 1);
+        const unsigned n0 = tot2 & 0x3FFFu;
+        compose(w0, w1, w2, x0, x1, x2);          // this thread's exclusive prefix
         // pass 2: place the elements; the first allele-0 / allele-1 element of
         // the segment takes its run length from the prefix (0 if it is the
         // first of its allele overall)
-        const unsigned zs = (x1 >> 16) & 0x3FFFu;
+        const unsigned zs = x2 & 0x3FFFu;
         const unsigned os = n0 + (unsigned)base - zs;
         unsigned z = zs, o = os;
         unsigned *Pn = P0 + (cur ^ 1) * np;
@@ -318,7 +334,7 @@ __global__ void __launch_bounds__(T, T == 512 ? 2 : (T == 256 ? 3 : 512 / T)) sw
         if (!CACHE) {
             // second sweep over the segment for the run lengths (large samples)
             unsigned a0 = x0 & 0xFFFFu, a1 = x0 >> 16;
-            unsigned h0 = (x1 >> 30) & 1u, h1 = x1 >> 31;
+            unsigned h0 = (x2 >> 15) & 1u, h1 = x2 >> 31;
             z = zs;
             o = os;
             for (int e = 0; e < E; ++e) {
@@ -344,12 +360,12 @@ __global__ void __launch_bounds__(T, T == 512 ? 2 : (T == 256 ? 3 : 512 / T)) sw
             // / os): 1 + the minimum over the prefix tail and its own span
             if (hp0) {
                 const unsigned u = Pn[zs];
-                const unsigned out = ((x1 >> 30) & 1u) ? min((x0 & 0xFFFFu) + 1u, u >> 16) : 0u;
+                const unsigned out = ((x2 >> 15) & 1u) ? min((x0 & 0xFFFFu) + 1u, u >> 16) : 0u;
                 Pn[zs] = (u & 0xFFFFu) | (out << 16);
             }
             if (hp1) {
                 const unsigned u = Pn[os];
-                const unsigned out = (x1 >> 31) ? min((x0 >> 16) + 1u, u >> 16) : 0u;
+                const unsigned out = (x2 >> 31) ? min((x0 >> 16) + 1u, u >> 16) : 0u;
                 Pn[os] = (u & 0xFFFFu) | (out << 16);
             }
         }
