@@ -266,10 +266,10 @@ __global__ void __launch_bounds__(T, T == 512 ? 2 : (T == 256 ? 3 : 512 / T)) sw
                     vmask = vmask + vmask + v;            // element e at bit E - 1 - e
                     allw = min(allw, pv);                 // high half: the segment minimum
                     mn01 = __vminu2(mn01, __byte_perm(pv, 0u, 0x3232u));
-                    // selectors by multiply-add: v ? 0x7610 : 0x5410, and the tail of
-                    // allele v restarted (v ? 0x7610 : 0x3254 with 0xFFFF in the other half)
+                    // the selector by multiply-add (v ? 0x7610 : 0x5410), and the tail
+                    // of allele v restarted by a 16x2 maximum with 0xFFFF in its half
                     if (CACHE) val[e + h] = __byte_perm(pv, mn01 + 0x00010001u, 0x5410u + v * 0x2200u);
-                    mn01 = __byte_perm(mn01, 0xFFFFFFFFu, 0x3254u + v * 0x43BCu);
+                    mn01 = __vmaxu2(mn01, 0x0000FFFFu + v * 0xFFFE0001u);
                 }
             }
         }
@@ -394,12 +394,18 @@ __global__ void __launch_bounds__(T, T == 512 ? 2 : (T == 256 ? 3 : 512 / T)) sw
             uint4 *M4 = (uint4 *)(slot + 16);
             for (int t = tid; t < (n + 7) / 8; t += T) {
                 const uint4 a = P4[2 * t], b = P4[2 * t + 1];
-                M4[t] = make_uint4((a.x >> 16) | (a.y & 0xFFFF0000u), (a.z >> 16) | (a.w & 0xFFFF0000u),
-                                   (b.x >> 16) | (b.y & 0xFFFF0000u), (b.z >> 16) | (b.w & 0xFFFF0000u));
+                M4[t] = make_uint4(__byte_perm(a.x, a.y, 0x7632u), __byte_perm(a.z, a.w, 0x7632u),
+                                   __byte_perm(b.x, b.y, 0x7632u), __byte_perm(b.z, b.w, 0x7632u));
                 const unsigned e8[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+                if (8 * t + 8 <= n) {
 #pragma unroll
-                for (int j = 0; j < 8; ++j)
-                    if (e8[j] - 0x10000u < 0x400000u && 8 * t + j < n) atomicAdd(hcnt + (e8[j] >> 16) - 1, 1u);
+                    for (int j = 0; j < 8; ++j)
+                        if (e8[j] - 0x10000u < 0x400000u) atomicAdd(hcnt + (e8[j] >> 16) - 1, 1u);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 8; ++j)
+                        if (e8[j] - 0x10000u < 0x400000u && 8 * t + j < n) atomicAdd(hcnt + (e8[j] >> 16) - 1, 1u);
+                }
             }
             if (xp) {                            // population of each sorted position
                 const unsigned limA = 64u * (unsigned)w.a.WA;
@@ -451,10 +457,17 @@ __global__ void __launch_bounds__(T, T == 512 ? 2 : (T == 256 ? 3 : 512 / T)) sw
             for (int t = tid; t < (n + 7) / 8; t += T) {
                 const uint4 a = P4[2 * t], b = P4[2 * t + 1];
                 const unsigned e8[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+                if (8 * t + 8 <= n) {
 #pragma unroll
-                for (int j = 0; j < 8; ++j)
-                    if (e8[j] - 0x10000u < lim && 8 * t + j < n)
-                        slist[atomicAdd(hoff + (e8[j] >> 16) - 1, 1u)] = (unsigned short)(8 * t + j);
+                    for (int j = 0; j < 8; ++j)
+                        if (e8[j] - 0x10000u < lim)
+                            slist[atomicAdd(hoff + (e8[j] >> 16) - 1, 1u)] = (unsigned short)(8 * t + j);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 8; ++j)
+                        if (e8[j] - 0x10000u < lim && 8 * t + j < n)
+                            slist[atomicAdd(hoff + (e8[j] >> 16) - 1, 1u)] = (unsigned short)(8 * t + j);
+                }
             }
         }
         if (!more) break;
