@@ -211,14 +211,15 @@ def run_reference(args, rank, world):
 
 
 SWEEP_DRAM_BYTES_PER_CORE = 4.6139e9 / 125020
-# ncu capture of the 250k case (5,000 x 250,000, default sweep shape; the
-# launch list and capture summarised in profiles/sweep_split_walk_ihs250k_full.md):
-# sweep_kernel alone read + wrote 3.493 GB (125,020 core loci), and its ALU-pipe
-# instructions (sm__inst_executed_pipe_alu, 51.8 % of the elapsed peak over
-# 14.56 ms at 2,070 MHz on 152 SMs, 2 warp instructions per SM cycle) come to
-# 29.8 thread operations per sorted element and marker pass
-SORT_DRAM_BYTES_PER_CORE = 3.4930e9 / 125020
-SORT_ALU_OPS_PER_ELEMENT_PASS = 29.8
+# ncu capture of the 250k case (5,000 x 250,000, default sweep shape; summarised
+# in profiles/sweep_split_walk_ihs250k_full.md): sweep_kernel alone read + wrote
+# 3.487 GB (125,020 core loci) and issued 7.063e9 warp instructions over
+# 997,618 marker passes of 5,120 elements, i.e. 44.25 thread instructions per
+# sorted element and marker pass, 19.88 of them on the ALU pipe
+# (sm__inst_executed_pipe_alu 3.173e9 warp instructions)
+SORT_DRAM_BYTES_PER_CORE = 3.4871e9 / 125020
+SORT_INSTR_PER_ELEMENT_PASS = 44.25
+SORT_ALU_OPS_PER_ELEMENT_PASS = 19.88
 
 
 def main():
@@ -437,27 +438,37 @@ def main():
                 "peak_source": f"{src} hbm_gbs (MEASURED_PEAKS.json)"}
         work = sg.selscan_sweep_work(n, k1 - k0, sg.MODE_IHS, sg.make_launch(**launch_fields))
         if work is not None:
-            # the dominant kernel, the sort, against the integer-pipe peak measured here
+            # the dominant kernel, the sort, against the integer issue peak measured here:
+            # four warp instructions per SM cycle (128 thread operations), which the
+            # IADD3 / IMNMX chains of libselscan_peak reach; beside it the ALU pipe alone
+            # (LOP3 / PRMT / funnel shift: 64 per SM cycle)
             from paper_1403_6854_gb300 import peak as int_peak
             pk = int_peak.measure()
+            issue_peak = float(np.median([pk[o]["ops_per_s"] for o in ("IADD3", "IMNMX")]))
             alu_peak = float(np.median([pk[o]["ops_per_s"] for o in ("LOP3", "PRMT", "SHF")]))
             element_passes = work[0] * work[1]
-            ops = element_passes * SORT_ALU_OPS_PER_ELEMENT_PASS
-            alu = ops / (sort_ms / 1e3)
+            ops = element_passes * SORT_INSTR_PER_ELEMENT_PASS / (sort_ms / 1e3)
+            alu = element_passes * SORT_ALU_OPS_PER_ELEMENT_PASS / (sort_ms / 1e3)
             roofline = {"bound": "alu", "kernel": "sweep_kernel (the sort; first stage)",
-                        "achieved": alu / 1e9, "peak": alu_peak / 1e9, "unit": "Gop/s",
-                        "frac": alu / alu_peak,
+                        "achieved": ops / 1e9, "peak": issue_peak / 1e9, "unit": "Gop/s",
+                        "frac": ops / issue_peak,
                         "traffic": cores * SORT_DRAM_BYTES_PER_CORE,
-                        "traffic_note": "ncu capture of the 250k case (3.49 GB of sweep_kernel "
+                        "traffic_note": "ncu capture of the 250k case (3.487 GB of sweep_kernel "
                                         "DRAM traffic over 125,020 core loci), scaled by core loci",
                         "kernel_ms": sort_ms, "split_walk_ms": walk_ms - sort_ms,
                         "element_passes": element_passes, "marker_passes": work[0],
-                        "ops_per_element_pass": SORT_ALU_OPS_PER_ELEMENT_PASS,
-                        "ops_note": "ALU-pipe thread operations per sorted element and marker "
-                                    "pass from the ncu capture of the 250k case, times the passes "
-                                    "of this launch",
-                        "peak_source": "ALU pipe (LOP3 / PRMT / funnel shift: 64 lanes per SM "
-                                       "cycle) measured in this run by libselscan_peak",
+                        "ops_per_element_pass": SORT_INSTR_PER_ELEMENT_PASS,
+                        "ops_note": "integer thread instructions (all pipes) per sorted element and "
+                                    "marker pass from the ncu capture of the 250k case, times the "
+                                    "passes of this launch",
+                        "peak_source": "integer issue rate (IADD3 / IMNMX chains: 128 thread "
+                                       "operations = 4 warp instructions per SM cycle) measured "
+                                       "in this run by libselscan_peak",
+                        "alu_pipe": {"achieved": alu / 1e9, "peak": alu_peak / 1e9,
+                                     "frac": alu / alu_peak,
+                                     "ops_per_element_pass": SORT_ALU_OPS_PER_ELEMENT_PASS,
+                                     "peak_source": "LOP3 / PRMT / funnel shift chains: 64 "
+                                                    "lanes per SM cycle"},
                         "int_peaks_ops_per_sm_per_cycle": {k: round(v["ops_per_sm_per_cycle"], 2)
                                                            for k, v in pk.items()},
                         "path": path}
