@@ -408,16 +408,14 @@ __global__ void __launch_bounds__(T, T == 512 ? 2 : (T == 256 ? 3 : 512 / T)) sw
                 }
             }
             if (xp) {                            // population of each sorted position
+                // one 32-position word per warp iteration: a ballot over the lanes
                 const unsigned limA = 64u * (unsigned)w.a.WA;
                 unsigned *isA = (unsigned *)(slot + slot_isa_at(n));
                 const int nw = split_nw(n);
-                for (int q = tid; q < nw; q += T) {
-                    unsigned word = 0u;
-                    for (int b = 0; b < 32; ++b) {
-                        const int t = q * 32 + b;
-                        if (t < n && (Ps[t] & 0xFFFFu) < limA) word |= 1u << b;
-                    }
-                    isA[q] = word;
+                for (int q = warp; q < nw; q += NW) {
+                    const int t = q * 32 + lane;
+                    const unsigned word = __ballot_sync(FULLMASK, t < n && (Ps[t] & 0xFFFFu) < limA);
+                    if (lane == 0) isA[q] = word;
                 }
             }
             __syncthreads();
