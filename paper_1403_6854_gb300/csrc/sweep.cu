@@ -45,6 +45,7 @@ constexpr unsigned kInf16 = 0xFFFFu;
 constexpr int kRowRing = 4;                 // rows in flight ahead of the sort (cp.async)
 constexpr int kSlotListCap = 1024;          // first-window boundaries kept per slot
 constexpr int kSplitListSmem = 1024;        // window list entries a walking warp keeps on chip
+constexpr int kWin = 64;                    // steps of a window the walker groups itself (a power of 2)
 
 __host__ __device__ inline int sweep_e(int n, int T)
 {
@@ -503,8 +504,8 @@ __device__ inline SplitSmem split_smem(unsigned char *base, int n, int xpehh)
     s.A = p; p += s.nw;
     s.SO = p; p += s.ns;
     s.SA = p; p += s.ns;
-    s.cnt = p; p += 64;
-    s.off = p; p += 65;
+    s.cnt = p; p += kWin;
+    s.off = p; p += kWin + 1;
     s.isA = xpehh ? p : nullptr;
     s.PA = xpehh ? p + s.nw : nullptr;
     s.lst = (unsigned short *)(p + (xpehh ? 2 * s.nw : 0));
@@ -558,7 +559,7 @@ __device__ __forceinline__ unsigned count_a(const SplitSmem &s, int x)
     return s.PA[x >> 5] + (unsigned)__popc(s.isA[x >> 5] & ((1u << (x & 31)) - 1u));
 }
 
-// Offsets of the 64 step counts and placement of the K staged boundaries
+// Offsets of the kWin step counts and placement of the K staged boundaries
 // (position | step in window << 16 | rank in step << 32) by step.
 template <int G, typename Tile>
 __device__ const unsigned short *place_window(const Tile &tile, const SplitSmem &s, unsigned K,
@@ -566,7 +567,7 @@ __device__ const unsigned short *place_window(const Tile &tile, const SplitSmem 
 {
     const int lane = tile.thread_rank();
     tile.sync();
-    constexpr int C = 64 / G;
+    constexpr int C = kWin / G;
     unsigned own = 0;
 #pragma unroll
     for (int j = 0; j < C; ++j) own += s.cnt[C * lane + j];
@@ -583,19 +584,19 @@ __device__ const unsigned short *place_window(const Tile &tile, const SplitSmem 
         s.off[C * lane + j] = run;
         run += c;
     }
-    if (lane == G - 1) s.off[64] = incl;
+    if (lane == G - 1) s.off[kWin] = incl;
     tile.sync();
     // the list goes to shared memory when it fits, else to the global scratch
     unsigned short *dst = K <= (unsigned)kSplitListSmem ? s.lst : list;
     for (unsigned j = lane; j < K; j += G) {
         const unsigned long long e = stage[j];
-        dst[s.off[(unsigned)(e >> 16) & 63u] + (unsigned)(e >> 32)] = (unsigned short)(e & 0xFFFFu);
+        dst[s.off[(unsigned)(e >> 16) & (kWin - 1u)] + (unsigned)(e >> 32)] = (unsigned short)(e & 0xFFFFu);
     }
     tile.sync();
     return dst;
 }
 
-// Group the boundaries t with lo <= M[t] < lo + 64 by step: one pass over M
+// Group the boundaries t with lo <= M[t] < lo + kWin by step: one pass over M
 // (8 values per 16-byte load, four loads in flight per lane) marks the values
 // in the window with two integer operations per 16-bit half; only the marked
 // ones are ranked inside their step and staged, then placed by step.  Done by
@@ -609,9 +610,10 @@ __device__ const unsigned short *build_window(const Tile &tile, const SplitSmem 
     const int lane = tile.thread_rank();
     const uint4 *M4 = (const uint4 *)M32;
     const unsigned short *M16 = (const unsigned short *)M32;
-    for (int q = lane; q < 64; q += G) s.cnt[q] = 0u;
+    for (int q = lane; q < kWin; q += G) s.cnt[q] = 0u;
     tile.sync();
     const int n4 = (n + 7) >> 3;
+    constexpr unsigned kOut = 0xFFFFu & ~(kWin - 1u);      // a 16-bit difference is in the window
     const unsigned ulo = (unsigned)lo, uhi = (unsigned)lo << 16;
     unsigned K = 0;
     for (int base = 0; base < n4; base += 4 * G) {
@@ -628,8 +630,8 @@ __device__ const unsigned short *build_window(const Tile &tile, const SplitSmem 
             const unsigned wv[4] = {q[u].x, q[u].y, q[u].z, q[u].w};
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                if (((wv[j] - ulo) & 0xFFC0u) == 0u) hit |= 1u << (8 * u + 2 * j);
-                if (((wv[j] - uhi) & 0xFFC00000u) == 0u) hit |= 1u << (8 * u + 2 * j + 1);
+                if (((wv[j] - ulo) & kOut) == 0u) hit |= 1u << (8 * u + 2 * j);
+                if (((wv[j] - uhi) & (kOut << 16)) == 0u) hit |= 1u << (8 * u + 2 * j + 1);
             }
         }
         if (base + 4 * G > n4 && (n & 7)) {      // the last group holds values past n
@@ -737,7 +739,7 @@ __device__ __noinline__ void split_many(const Tile &tile, const SplitSmem &s,
 size_t split_smem_per_warp(int n, int xpehh)
 {
     const int nw = split_nw(n), ns = (nw + 31) >> 5;
-    size_t b = (size_t)nw * 4 * 2 + (size_t)ns * 4 * 2 + 64 * 4 + 65 * 4;
+    size_t b = (size_t)nw * 4 * 2 + (size_t)ns * 4 * 2 + (size_t)(2 * kWin + 1) * 4;
     if (xpehh) b += (size_t)nw * 4 * 2;
     b += (size_t)kSplitListSmem * 2;
     return (b + 15) & ~(size_t)15;
@@ -875,8 +877,8 @@ __global__ void __launch_bounds__(kSplitWarps * 32, SPLIT_MIN_CTAS) split_walk_k
         double gq = 0.0;        // this lane's step of the current G-step block: the map step g
         int gk = 0;             // its kind: 0 a step, WALK_EDGE past the array end, WALK_GAP a gap abort
         // steps [lo, lo + wlen) are grouped in cl: first the slot's window
-        // (steps 1..w1), then windows of 64 steps found in M
-        int lo = 1, wlen = w1 > 0 ? w1 : 64;
+        // (steps 1..w1), then windows of kWin steps found in M
+        int lo = 1, wlen = w1 > 0 ? w1 : kWin;
         const unsigned short *cl = s.lst;
         if (any) {
             if (w1 > 0) {                        // the slot's list, copied on chip
@@ -927,7 +929,7 @@ __global__ void __launch_bounds__(kSplitWarps * 32, SPLIT_MIN_CTAS) split_walk_k
             if (i > hz) { fin = WALK_UNFINISHED; break; }
             if (i >= lo + wlen) {
                 lo += wlen;
-                wlen = 64;
+                wlen = kWin;
                 cl = build_window<G>(tile, s, M32, n, lo, stage, list);
             }
             // ---- the boundaries that part at this step
