@@ -514,44 +514,40 @@ __device__ inline SplitSmem split_smem(unsigned char *base, int n, int xpehh)
 
 __device__ __forceinline__ int c2i(unsigned k) { return (int)(k * (k - 1u) / 2u); }
 
-// last set position < b among all run starts (ALL: A) or the old ones (O)
-template <bool ALL>
-__device__ __forceinline__ int prev_set(const SplitSmem &s, int b)
+// Bitmap searches with a third level: `sup` has bit q set when summary word q
+// is non-zero (at most 16 summary words: n <= 16383), so neither search loops.
+// last set position < b (b > 0; position 0 is always set)
+__device__ __forceinline__ int prev_start(const unsigned *B, const unsigned *S, unsigned sup, int b)
 {
-    const unsigned *B = ALL ? s.A : s.O, *S = ALL ? s.SA : s.SO;
     const int wd = b >> 5;
     const unsigned bits = B[wd] & ((1u << (b & 31)) - 1u);
     if (bits) return (wd << 5) + 31 - __clz(bits);
-    for (int sw = wd - 1; sw >= 0;) {
-        const int q = sw >> 5;
-        const unsigned sb = S[q] & (0xFFFFFFFFu >> (31 - (sw & 31)));
-        if (sb) {
-            const int ww = (q << 5) + 31 - __clz(sb);
-            return (ww << 5) + 31 - __clz(B[ww]);
-        }
-        sw = (q << 5) - 1;
+    const int sw = wd - 1;                       // >= 0: word 0 holds position 0
+    int q = sw >> 5;
+    unsigned sb = S[q] & (0xFFFFFFFFu >> (31 - (sw & 31)));
+    if (!sb) {                                   // q > 0 here: summary word 0 has bit 0
+        q = 31 - __clz(sup & ((1u << q) - 1u));
+        sb = S[q];
     }
-    return 0;                         // position 0 is always set
+    const int ww = (q << 5) + 31 - __clz(sb);
+    return (ww << 5) + 31 - __clz(B[ww]);
 }
 
-// first set position > b among all run starts (ALL: A) or the old ones (O)
-template <bool ALL>
-__device__ __forceinline__ int next_set(const SplitSmem &s, int b, int n)
+// first set position > b (b < n; position n is always set)
+__device__ __forceinline__ int next_start(const unsigned *B, const unsigned *S, unsigned sup, int b)
 {
-    const unsigned *B = ALL ? s.A : s.O, *S = ALL ? s.SA : s.SO;
     const int wd = b >> 5;
     const unsigned bits = B[wd] & ~((2u << (b & 31)) - 1u);
     if (bits) return (wd << 5) + __ffs(bits) - 1;
-    for (int sw = wd + 1; sw < s.nw;) {
-        const int q = sw >> 5;
-        const unsigned sb = S[q] & (0xFFFFFFFFu << (sw & 31));
-        if (sb) {
-            const int ww = (q << 5) + __ffs(sb) - 1;
-            return (ww << 5) + __ffs(B[ww]) - 1;
-        }
-        sw = (q + 1) << 5;
+    const int sw = wd + 1;                       // a word up to the one of position n
+    int q = sw >> 5;
+    unsigned sb = S[q] & (0xFFFFFFFFu << (sw & 31));
+    if (!sb) {
+        q = __ffs(sup & ~((2u << q) - 1u)) - 1;
+        sb = S[q];
     }
-    return n;                         // position n is always set
+    const int ww = (q << 5) + __ffs(sb) - 1;
+    return (ww << 5) + __ffs(B[ww]) - 1;
 }
 
 __device__ __forceinline__ unsigned count_a(const SplitSmem &s, int x)
@@ -691,11 +687,11 @@ struct ClassWalk {
 // (M < i, the bitmap O).  So boundary b removes (b - p)(e - b) pairs, and
 // per population the products of its members on either side.
 template <int NPOP>
-__device__ __forceinline__ void split_terms(const SplitSmem &s, int b, int n, int n0, int &d0,
-                                            int &d1, int &d2)
+__device__ __forceinline__ void split_terms(const SplitSmem &s, int b, int n0, unsigned supA,
+                                            unsigned supO, int &d0, int &d1, int &d2)
 {
-    const int p = prev_set<true>(s, b);
-    const int e = next_set<false>(s, b, n);
+    const int p = prev_start(s.A, s.SA, supA, b);
+    const int e = next_start(s.O, s.SO, supO, b);
     if (NPOP == 2) {
         const unsigned ap = count_a(s, p), ab = count_a(s, b), ae = count_a(s, e);
         const unsigned l1a = ab - ap, l2a = ae - ab;
@@ -713,25 +709,30 @@ __device__ __forceinline__ void split_terms(const SplitSmem &s, int b, int n, in
 // Steps that part more than G pairs (a few per walk): kept out of line so
 // that the common one-round path stays small in the instruction cache.
 template <int NPOP, int G, typename Tile>
-__device__ __noinline__ void split_many(const Tile &tile, const SplitSmem &s,
-                                        const unsigned short *list, unsigned j0, unsigned j1, int n,
-                                        int n0, int &d0, int &d1, int &d2)
+__device__ __noinline__ unsigned split_many(const Tile &tile, const SplitSmem &s,
+                                            const unsigned short *list, unsigned j0, unsigned j1,
+                                            int n0, unsigned supA, unsigned supO, int &d0, int &d1,
+                                            int &d2)
 {
     const int lane = tile.thread_rank();
+    unsigned r = 0u;
     for (unsigned j = j0 + lane; j < j1; j += G) {
         const int b = list[j];
         atomicOr(s.A + (b >> 5), 1u << (b & 31));
         atomicOr(s.SA + (b >> 10), 1u << ((b >> 5) & 31));
+        r |= 1u << (b >> 10);
     }
+    r = __reduce_or_sync(G == 32 ? 0xFFFFFFFFu : (0xFFFFu << (threadIdx.x & 16)), r);
     tile.sync();
     for (unsigned j = j0 + lane; j < j1; j += G)
-        split_terms<NPOP>(s, (int)list[j], n, n0, d0, d1, d2);
+        split_terms<NPOP>(s, (int)list[j], n0, supA | r, supO, d0, d1, d2);
     tile.sync();
     for (unsigned j = j0 + lane; j < j1; j += G) {
         const int b = list[j];
         atomicOr(s.O + (b >> 5), 1u << (b & 31));
         atomicOr(s.SO + (b >> 10), 1u << ((b >> 5) & 31));
     }
+    return r;                                    // summary words that gained a start
 }
 
 }  // namespace
@@ -831,6 +832,8 @@ __global__ void __launch_bounds__(kSplitWarps * 32, SPLIT_MIN_CTAS) split_walk_k
             atomicOr(s.SA + (mk >> 10), 1u << ((mk >> 5) & 31));
         }
         tile.sync();
+        // summary words with a start (third level of both bitmaps)
+        unsigned supA = 1u | (1u << (n0 >> 10)) | (1u << (n >> 10)), supO = supA;
 
         // ---- step 0 (the core marker splits the sample into its allele classes)
         constexpr int NWK = NPOP == 2 ? 1 : 2;    // walks handled by this warp
@@ -948,8 +951,11 @@ __global__ void __launch_bounds__(kSplitWarps * 32, SPLIT_MIN_CTAS) split_walk_k
                         atomicOr(s.A + (b >> 5), bw);
                         atomicOr(s.SA + (b >> 10), sw);
                     }
+                    const unsigned r = __reduce_or_sync(G == 32 ? 0xFFFFFFFFu : (0xFFFFu << (threadIdx.x & 16)),
+                                                        has ? 1u << (b >> 10) : 0u);
+                    supA |= r;
                     tile.sync();
-                    if (has) split_terms<NPOP>(s, b, n, n0, d0, d1, d2);
+                    if (has) split_terms<NPOP>(s, b, n0, supA, supO, d0, d1, d2);
                     tile.sync();
                     // this step's starts become old ones; the next step reads O
                     // only after its own sync
@@ -957,9 +963,12 @@ __global__ void __launch_bounds__(kSplitWarps * 32, SPLIT_MIN_CTAS) split_walk_k
                         atomicOr(s.O + (b >> 5), bw);
                         atomicOr(s.SO + (b >> 10), sw);
                     }
+                    supO |= r;
                     }
                 } else {
-                    split_many<NPOP, G>(tile, s, cl, j0, j1, n, n0, d0, d1, d2);
+                    const unsigned r = split_many<NPOP, G>(tile, s, cl, j0, j1, n0, supA, supO, d0, d1, d2);
+                    supA |= r;
+                    supO |= r;
                 }
                 d0 = cg::reduce(tile, d0, cg::plus<int>());
                 d1 = cg::reduce(tile, d1, cg::plus<int>());
