@@ -21,7 +21,10 @@ SHAPES = [dict(), dict(sweep_warmup=16, sweep_stage_cores=7), dict(sweep_warmup=
           dict(sweep_threads=256, sweep_warmup=64, sweep_stage_cores=33),
           dict(sweep_split_tile=16), dict(sweep_split_tile=16, sweep_warmup=16, sweep_stage_cores=5),
           dict(sweep_split_tile=32), dict(sweep_threads=32), dict(sweep_threads=128),
-          dict(sweep_threads=64, sweep_warmup=40, sweep_stage_cores=9), dict(sweep_threads=256)]
+          dict(sweep_threads=64, sweep_warmup=40, sweep_stage_cores=9), dict(sweep_threads=256),
+          # chunk counts set by the sorting CTAs per SM (one, and four of 256 threads)
+          dict(sweep_threads=256, sweep_ctas_per_sm=1, sweep_warmup=64),
+          dict(sweep_threads=256, sweep_ctas_per_sm=4, sweep_warmup=64, sweep_stage_cores=50)]
 
 
 @pytest.fixture(scope="module")
