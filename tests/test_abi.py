@@ -205,5 +205,9 @@ def test_sweep_work_on_host(sg):
     L = sg.make_launch(sg.SCHED_SWEEP, sweep_warmup=1024)
     p2, _ = sg.selscan_sweep_work(5000, 1_000_000, I, L)
     assert p2 < passes
+    # more sorting CTAs per SM: more chunks, each with its own warm-up
+    p1, _ = sg.selscan_sweep_work(5000, 1_000_000, I, sg.make_launch(sg.SCHED_SWEEP, sweep_ctas_per_sm=1))
+    p4, _ = sg.selscan_sweep_work(5000, 1_000_000, I, sg.make_launch(sg.SCHED_SWEEP, sweep_ctas_per_sm=4))
+    assert p1 < passes < p4
     assert sg.selscan_sweep_work(204, 22147, I) is None          # per-step default
     assert sg.selscan_sweep_work(204, 22147, I, sg.make_launch(sg.SCHED_SWEEP)) is not None
