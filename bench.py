@@ -381,22 +381,34 @@ def main():
                for f in ("status", "lnratio", "ihh1", "ihh0")}
         dh, dp, dg = torch.empty_like(hap), torch.empty_like(pos), torch.empty_like(gmap)
         steps_e2e = max(2, min(K, 3))
+        # events split each step into its parts (the timed region is the host clock around all)
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps_e2e)]
         torch.cuda.synchronize()
         a0 = time.perf_counter()
-        for _ in range(steps_e2e):
+        for st in range(steps_e2e):
+            evs[st][0].record()
             dh.copy_(h_rows, non_blocking=True)
             dp.copy_(h_pos, non_blocking=True)
             dg.copy_(h_gmap, non_blocking=True)
+            evs[st][1].record()
             o2 = sg.selscan_ihs(dh, n, dp, dg, params=params, workspace=ws,
                                 launch=sg.make_launch(**launch_fields))
+            evs[st][2].record()
             for f in res:
                 res[f].copy_(o2[f], non_blocking=True)
+            evs[st][3].record()
             torch.cuda.synchronize()
         e2e_s = (time.perf_counter() - a0) / steps_e2e
+        h2d_b = int(d.rows.nbytes + d.pos.nbytes + d.gmap.nbytes)
+        h2d_ms = float(np.median([e[0].elapsed_time(e[1]) for e in evs]))
         e2e = {"value": cores / e2e_s, "unit": "core loci/s",
-               "h2d_bytes_per_step": int(d.rows.nbytes + d.pos.nbytes + d.gmap.nbytes),
+               "h2d_bytes_per_step": h2d_b,
                "d2h_bytes_per_step": int(sum(r.numel() * r.element_size() for r in res.values())),
-               "ms_per_step": e2e_s * 1e3}
+               "ms_per_step": e2e_s * 1e3,
+               "parts_ms": {"h2d": h2d_ms,
+                            "scan": float(np.median([e[1].elapsed_time(e[2]) for e in evs])),
+                            "d2h": float(np.median([e[2].elapsed_time(e[3]) for e in evs]))},
+               "h2d_gbs": h2d_b / (h2d_ms / 1e3) / 1e9}
         e2e_bufs = (h_rows, h_pos, h_gmap, res, dh, dp, dg, o2)
 
     extras = {}
