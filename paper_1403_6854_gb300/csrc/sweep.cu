@@ -388,24 +388,24 @@ __global__ void __launch_bounds__(T, T == 512 ? 2 : (T == 256 ? 3 : 512 / T)) sw
                 hdr[1] = (int)hz;
             }
             const unsigned *Ps = P0 + cur * np;
-            // run lengths, 8 per 16-byte store (np is a multiple of 512, the
-            // slot's M region a multiple of 16 bytes; values past n are never
-            // read), counting the boundaries of each of steps 1..64 (M in [1, 64])
+            // run lengths, 4 per 8-byte store (four elements per item: finer
+            // items even out the threads' shares; the slot's M region is a
+            // multiple of 16 bytes, values past n are never read), counting the
+            // boundaries of each of steps 1..64 (M in [1, 64])
             const uint4 *P4 = (const uint4 *)Ps;
-            uint4 *M4 = (uint4 *)(slot + 16);
-            for (int t = tid; t < (n + 7) / 8; t += T) {
-                const uint4 a = P4[2 * t], b = P4[2 * t + 1];
-                M4[t] = make_uint4(__byte_perm(a.x, a.y, 0x7632u), __byte_perm(a.z, a.w, 0x7632u),
-                                   __byte_perm(b.x, b.y, 0x7632u), __byte_perm(b.z, b.w, 0x7632u));
-                const unsigned e8[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
-                if (8 * t + 8 <= n) {
+            uint2 *M2 = (uint2 *)(slot + 16);
+            for (int t = tid; t < (n + 3) / 4; t += T) {
+                const uint4 a = P4[t];
+                M2[t] = make_uint2(__byte_perm(a.x, a.y, 0x7632u), __byte_perm(a.z, a.w, 0x7632u));
+                const unsigned e4[4] = {a.x, a.y, a.z, a.w};
+                if (4 * t + 4 <= n) {
 #pragma unroll
-                    for (int j = 0; j < 8; ++j)
-                        if (e8[j] - 0x10000u < 0x400000u) atomicAdd(hcnt + (e8[j] >> 16) - 1, 1u);
+                    for (int j = 0; j < 4; ++j)
+                        if (e4[j] - 0x10000u < 0x400000u) atomicAdd(hcnt + (e4[j] >> 16) - 1, 1u);
                 } else {
 #pragma unroll
-                    for (int j = 0; j < 8; ++j)
-                        if (e8[j] - 0x10000u < 0x400000u && 8 * t + j < n) atomicAdd(hcnt + (e8[j] >> 16) - 1, 1u);
+                    for (int j = 0; j < 4; ++j)
+                        if (e4[j] - 0x10000u < 0x400000u && 4 * t + j < n) atomicAdd(hcnt + (e4[j] >> 16) - 1, 1u);
                 }
             }
             if (xp) {                            // population of each sorted position
@@ -453,19 +453,19 @@ __global__ void __launch_bounds__(T, T == 512 ? 2 : (T == 256 ? 3 : 512 / T)) sw
             // place the window's boundaries by step
             const unsigned lim = hoff[64] << 16;
             unsigned short *slist = (unsigned short *)(slot + slot_list_at(n, xp));
-            for (int t = tid; t < (n + 7) / 8; t += T) {
-                const uint4 a = P4[2 * t], b = P4[2 * t + 1];
-                const unsigned e8[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
-                if (8 * t + 8 <= n) {
+            for (int t = tid; t < (n + 3) / 4; t += T) {
+                const uint4 a = P4[t];
+                const unsigned e4[4] = {a.x, a.y, a.z, a.w};
+                if (4 * t + 4 <= n) {
 #pragma unroll
-                    for (int j = 0; j < 8; ++j)
-                        if (e8[j] - 0x10000u < lim)
-                            slist[atomicAdd(hoff + (e8[j] >> 16) - 1, 1u)] = (unsigned short)(8 * t + j);
+                    for (int j = 0; j < 4; ++j)
+                        if (e4[j] - 0x10000u < lim)
+                            slist[atomicAdd(hoff + (e4[j] >> 16) - 1, 1u)] = (unsigned short)(4 * t + j);
                 } else {
 #pragma unroll
-                    for (int j = 0; j < 8; ++j)
-                        if (e8[j] - 0x10000u < lim && 8 * t + j < n)
-                            slist[atomicAdd(hoff + (e8[j] >> 16) - 1, 1u)] = (unsigned short)(8 * t + j);
+                    for (int j = 0; j < 4; ++j)
+                        if (e4[j] - 0x10000u < lim && 4 * t + j < n)
+                            slist[atomicAdd(hoff + (e4[j] >> 16) - 1, 1u)] = (unsigned short)(4 * t + j);
                 }
             }
         }
