@@ -169,13 +169,14 @@ def test_first_window_shorter_than_64_steps(sg):
 
 @pytest.mark.parametrize("n,threads", [(6000, 256), (6000, 512), (9000, 0), (9000, 256), (13000, 0),
                                        (500, 0), (900, 32), (2000, 64), (3000, 64), (1500, 0),
-                                       (3000, 256), (4000, 256), (4500, 256)])
+                                       (3000, 256), (4000, 256), (4500, 256), (7000, 256), (8000, 256)])
 def test_elements_per_thread(sg, n, threads):
     """Samples near the register-cached limit of each CTA width, ones that
     re-read their elements from shared memory (more than 24 per thread),
     requests above 32 elements per thread (taken by the next wider CTA), and
     each exact element count of the 256-thread sort (4, 8, ..., 24 a thread:
-    n = 3000, 4000 and 4500 give 12, 16 and 20 with padding)."""
+    n = 3000, 4000 and 4500 give 12, 16 and 20 with padding), and 28 / 32 a
+    thread on 256 threads (n = 7000, 8000: elements re-read from shared memory)."""
     m = 90
     hap, pos, gmap = synth.tiny_mosaic(n, m, n + threads, founders=5, switch=0.05, flip=0.003)
     rows = synth.pack(hap)
