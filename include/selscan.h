@@ -140,7 +140,9 @@ typedef struct {
                                   up to 6144 haplotypes, else 512); a width is doubled until
                                   it holds at most 32 haplotypes per thread */
     int32_t sweep_split_tile;  /* sweep schedule: lanes per split walk, 32 or 16 (two walks
-                                  per warp) (0 = default) */
+                                  per warp) (0 = default, 32).  16 sums each trapezoid in 16
+                                  per-lane partial sums instead of 32: iHH may differ from the
+                                  default in the last bits; integer results are identical */
     int32_t sweep_ctas_per_sm; /* sweep schedule, 256- and 512-thread sorts: sorting CTAs per SM
                                   over both directions, which sets the chunk count (0 = 3 of
                                   256 threads, 2 of 512; at most 2,048 threads per SM; a count
