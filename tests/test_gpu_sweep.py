@@ -254,3 +254,29 @@ def test_xpehh_1m_sampled_cores(sg):
     ref = oracle.xpehh(d.rows, 2500, 2500, d.pos, d.gmap, cores=cores)
     assert_xpehh_equal(got, ref, idx=cores)
     assert np.array_equal(np.isfinite(got["lnratio"]), got["status"] == 0)
+
+
+def test_split_tile_16_against_32(sg, chr22, xp):
+    """16-lane split walks keep 16 trapezoid partial sums instead of 32: every
+    integer result (status, n1, stops, digests) is the 32-lane result bit for
+    bit, the iHH values agree to rounding."""
+    from parity_util import to_np
+    for (d, _), mode in ((chr22, "ihs"), (xp, "xpehh")):
+        hap, pos, gmap = sg.to_device(d.rows, d.pos, d.gmap)
+        outs = []
+        for tile in (32, 16):
+            L = sweep(sg, sweep_split_tile=tile, sweep_warmup=64, sweep_stage_cores=500)
+            if mode == "ihs":
+                o = sg.selscan_ihs(hap, 204, pos, gmap, launch=L)
+            else:
+                o = sg.selscan_xpehh(hap, 204, 210, pos, gmap, launch=L)
+            sg.check(o)
+            outs.append(to_np(o))
+        a, b = outs
+        for k in a:
+            if a[k].dtype.kind == "f":
+                ok = ~np.isnan(a[k])
+                assert np.array_equal(ok, ~np.isnan(b[k])), k
+                np.testing.assert_allclose(b[k][ok], a[k][ok], rtol=1e-12, atol=1e-12, err_msg=k)
+            else:
+                assert np.array_equal(a[k], b[k]), k
