@@ -750,12 +750,15 @@ size_t split_scratch_per_warp(int n) { return (((size_t)n * 10) + 255) & ~(size_
 
 // Persistent: each tile of G lanes (a warp, or half a warp so that one warp
 // walks two cores at once) takes slots of this stage (both directions) from a
-// counter and walks the cores in them.
+// counter and walks the cores in them.  iHS walks run four CTAs per SM at 64
+// registers; the XPEHH walk (three pair counts per boundary, the population
+// prefix table) spills more at that cap and runs three at 80 (1M XPEHH scan:
+// 51.35 ms against 51.82).
 #ifndef SPLIT_MIN_CTAS
 #define SPLIT_MIN_CTAS 4
 #endif
 template <int NPOP, int G>
-__global__ void __launch_bounds__(kSplitWarps * 32, SPLIT_MIN_CTAS) split_walk_kernel(SweepArgs w)
+__global__ void __launch_bounds__(kSplitWarps * 32, NPOP == 2 ? 3 : SPLIT_MIN_CTAS) split_walk_kernel(SweepArgs w)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     namespace cg = cooperative_groups;
