@@ -374,18 +374,40 @@ def main():
     # end to end: host buffers, H2D of the inputs and D2H of the scores every step
     e2e, e2e_bufs = None, None
     if rank == 0 and world == 1 and not args.no_extras:
+        from paper_1403_6854_gb300.stream import scan_host_stream
         h_rows = torch.from_numpy(d.rows.view(np.int64)).pin_memory()
         h_pos = torch.from_numpy(d.pos).pin_memory()
         h_gmap = torch.from_numpy(d.gmap).pin_memory()
-        res = {f: torch.empty(out[f].shape, dtype=out[f].dtype).pin_memory()
-               for f in ("status", "lnratio", "ihh1", "ihh0")}
+        e2e_fields = ("status", "lnratio", "ihh1", "ihh0")
+        h2d_b = int(d.rows.nbytes + d.pos.nbytes + d.gmap.nbytes)
+        d2h_b = int(sum(out[f].numel() * out[f].element_size() for f in e2e_fields))
+
+        def e2e_stream(steps):
+            # the public streaming call: upload of step k + 1 overlapped with scan k,
+            # scores of step k read back behind it; the last result is on the host
+            # before the clock stops
+            last = None
+            for r in scan_host_stream([(h_rows, h_pos, h_gmap)] * steps, sg.MODE_IHS, n,
+                                      params=params, launch=sg.make_launch(**launch_fields),
+                                      fields=e2e_fields, workspace=ws):
+                last = r
+            return last
+
+        e2e_stream(2)                     # untimed: the stream's buffers come from the caches
+        torch.cuda.synchronize()
+        steps_e2e = K
+        a0 = time.perf_counter()
+        last = e2e_stream(steps_e2e)
+        e2e_s = (time.perf_counter() - a0) / steps_e2e
+        assert int((last["status"].numpy() != sg.LOCUS_MAF_FILTERED).sum()) == cores
+        # one call at a time (no overlap), each step split into its parts by events
+        res = {f: torch.empty(out[f].shape, dtype=out[f].dtype).pin_memory() for f in e2e_fields}
         dh, dp, dg = torch.empty_like(hap), torch.empty_like(pos), torch.empty_like(gmap)
-        steps_e2e = max(2, min(K, 3))
-        # events split each step into its parts (the timed region is the host clock around all)
-        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps_e2e)]
+        steps_ser = max(2, min(K, 3))
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps_ser)]
         torch.cuda.synchronize()
         a0 = time.perf_counter()
-        for st in range(steps_e2e):
+        for st in range(steps_ser):
             evs[st][0].record()
             dh.copy_(h_rows, non_blocking=True)
             dp.copy_(h_pos, non_blocking=True)
@@ -398,18 +420,24 @@ def main():
                 res[f].copy_(o2[f], non_blocking=True)
             evs[st][3].record()
             torch.cuda.synchronize()
-        e2e_s = (time.perf_counter() - a0) / steps_e2e
-        h2d_b = int(d.rows.nbytes + d.pos.nbytes + d.gmap.nbytes)
+        ser_s = (time.perf_counter() - a0) / steps_ser
         h2d_ms = float(np.median([e[0].elapsed_time(e[1]) for e in evs]))
         e2e = {"value": cores / e2e_s, "unit": "core loci/s",
-               "h2d_bytes_per_step": h2d_b,
-               "d2h_bytes_per_step": int(sum(r.numel() * r.element_size() for r in res.values())),
-               "ms_per_step": e2e_s * 1e3,
-               "parts_ms": {"h2d": h2d_ms,
-                            "scan": float(np.median([e[1].elapsed_time(e[2]) for e in evs])),
-                            "d2h": float(np.median([e[2].elapsed_time(e[3]) for e in evs]))},
-               "h2d_gbs": h2d_b / (h2d_ms / 1e3) / 1e9}
-        e2e_bufs = (h_rows, h_pos, h_gmap, res, dh, dp, dg, o2)
+               "h2d_bytes_per_step": h2d_b, "d2h_bytes_per_step": d2h_b,
+               "ms_per_step": e2e_s * 1e3, "steps": steps_e2e,
+               "how": "paper_1403_6854_gb300.stream.scan_host_stream over the steps: pinned host "
+                      "matrix, positions and map uploaded every step (overlapped with the "
+                      "previous step's scan), scores read back to pinned host memory every "
+                      "step; host clock from the first upload to the last result on the host",
+               "serial": {"ms_per_step": ser_s * 1e3, "steps": steps_ser,
+                          "what": "one call at a time: H2D, scan, D2H, synchronise",
+                          "parts_ms": {"h2d": h2d_ms,
+                                       "scan": float(np.median([e[1].elapsed_time(e[2])
+                                                                for e in evs])),
+                                       "d2h": float(np.median([e[2].elapsed_time(e[3])
+                                                               for e in evs]))},
+                          "h2d_gbs": h2d_b / (h2d_ms / 1e3) / 1e9}}
+        e2e_bufs = (h_rows, h_pos, h_gmap, res, dh, dp, dg, o2, last)
 
     extras = {}
     if rank == 0 and world == 1 and not args.no_extras:
