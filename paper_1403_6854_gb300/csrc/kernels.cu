@@ -463,43 +463,107 @@ cudaError_t launch_ehh(const ScanArgs &a, long long locus, const Scratch &sc,
 }
 
 // ------------------------------------------------------------ pack
-// marker-major input: one warp per (marker, word); two ballots make a word
-__global__ void pack_mm_kernel(const uint8_t *hap01, int n, long long m, int W,
-                               unsigned long long *rows, long long ld)
+// marker-major input [m, n] bytes: a warp packs whole marker rows.  For word w
+// lane l reads the bytes of haplotypes 64 w + l and 64 w + 32 + l (two
+// coalesced 32-byte reads) and two ballots make the word; lane w % 32 keeps it
+// and the warp stores 32 consecutive words at once.
+__global__ void __launch_bounds__(256) pack_mm_kernel(const uint8_t *hap01, int n, long long m,
+                                                      int W, unsigned long long *rows, long long ld)
 {
     const int lane = threadIdx.x & 31;
     const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
-    for (long long t = warp; t < m * ld; t += nw) {
-        const long long k = t / ld;
-        const int w = (int)(t % ld);
-        unsigned lo = 0, hi = 0;
-        if (w < W) {
-            const long long h0 = 64ll * w + lane, h1 = h0 + 32;
-            const bool b0 = h0 < n && (hap01[k * n + h0] & 1);
-            const bool b1 = h1 < n && (hap01[k * n + h1] & 1);
-            lo = __ballot_sync(FULLMASK, b0);
-            hi = __ballot_sync(FULLMASK, b1);
+    for (long long k = warp; k < m; k += nw) {
+        const uint8_t *src = hap01 + k * n;
+        unsigned long long *dst = rows + k * ld;
+        for (long long w0 = 0; w0 < ld; w0 += 32) {
+            unsigned long long mine = 0;
+            for (int j = 0; j < 32 && w0 + j < ld; ++j) {      // warp-uniform bounds
+                const long long w = w0 + j;
+                unsigned lo = 0, hi = 0;
+                if (w < W) {
+                    const long long h0 = 64 * w + lane, h1 = h0 + 32;
+                    lo = __ballot_sync(FULLMASK, h0 < n && (src[h0] & 1));
+                    hi = __ballot_sync(FULLMASK, h1 < n && (src[h1] & 1));
+                }
+                if (lane == j) mine = (unsigned long long)lo | ((unsigned long long)hi << 32);
+            }
+            if (w0 + lane < ld) dst[w0 + lane] = mine;
         }
-        if (lane == 0) rows[k * ld + w] = (unsigned long long)lo | ((unsigned long long)hi << 32);
     }
 }
 
-// haplotype-major input: one thread per (marker, word), threads along markers
-__global__ void pack_hm_kernel(const uint8_t *hap01, int n, long long m, int W,
-                               unsigned long long *rows, long long ld)
+// bit 0 of each of the four bytes of x, as bits 0..3: with one bit per byte
+// kept, the multiply moves byte i's bit to bit 24 + i and nothing else reaches
+// bits 24..31
+__device__ __forceinline__ unsigned byte_lsbs(unsigned x) { return ((x & 0x01010101u) * 0x01020408u) >> 24; }
+
+// Bit j of (a, b) = bit 0 of p[j] (a: j < 32, b: j >= 32) for j < nk <= 64;
+// VEC: p is 16-byte aligned and nk = 64 (four 16-byte loads).
+template <bool VEC>
+__device__ __forceinline__ void lsb_mask64(const uint8_t *p, int nk, unsigned &a, unsigned &b)
 {
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < m * ld;
-         t += (long long)gridDim.x * blockDim.x) {
-        const long long w = t / m, k = t % m;
-        unsigned long long v = 0;
-        if (w < W) {
-            for (int b = 0; b < 64; ++b) {
-                const long long h = 64 * w + b;
-                if (h < n && (hap01[h * m + k] & 1)) v |= 1ull << b;
-            }
+    a = 0u;
+    b = 0u;
+    if (VEC && nk == 64) {
+        const uint4 *q = (const uint4 *)p;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const uint4 v = __ldg(q + i);
+            const unsigned s = byte_lsbs(v.x) | (byte_lsbs(v.y) << 4) | (byte_lsbs(v.z) << 8) |
+                               (byte_lsbs(v.w) << 12);
+            if (i < 2) a |= s << (16 * i);
+            else b |= s << (16 * (i - 2));
         }
-        rows[k * ld + w] = v;
+    } else {
+        for (int j = 0; j < nk; ++j) {
+            const unsigned bit = __ldg(p + j) & 1u;
+            if (j < 32) a |= bit << j;
+            else b |= bit << (j - 32);
+        }
+    }
+}
+
+// haplotype-major input [n, m] bytes: a warp packs word w of 64 consecutive
+// markers.  Lane l reads markers [k0, k0 + 64) of haplotypes 64 w + l and
+// 64 w + 32 + l (contiguous bytes of their rows), keeps bit 0 of each byte in a
+// 64-bit mask per haplotype, and one ballot per marker and half transposes the
+// masks into the markers' words; lane j stores the words of markers k0 + j and
+// k0 + 32 + j.  Consecutive warps take consecutive words of the same markers,
+// so the stores of a row segment meet in L2.
+template <bool VEC>
+__global__ void __launch_bounds__(256) pack_hm_kernel(const uint8_t *hap01, int n, long long m,
+                                                      int W, unsigned long long *rows, long long ld)
+{
+    const int lane = threadIdx.x & 31;
+    const long long tasks = (m + 63) / 64 * ld;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long t = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; t < tasks; t += nw) {
+        const long long kb = t / ld;
+        const long long w = t - kb * ld;
+        const long long k0 = kb * 64;
+        const int nk = m - k0 < 64 ? (int)(m - k0) : 64;
+        unsigned a0 = 0u, a1 = 0u, b0 = 0u, b1 = 0u;     // haplotype 64 w + l: a; + 32: b
+        if (w < W) {
+            const long long h0 = 64 * w + lane, h1 = h0 + 32;
+            if (h0 < n) lsb_mask64<VEC>(hap01 + h0 * m + k0, nk, a0, a1);
+            if (h1 < n) lsb_mask64<VEC>(hap01 + h1 * m + k0, nk, b0, b1);
+        }
+        unsigned long long mine0 = 0, mine1 = 0;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            const unsigned lo = __ballot_sync(FULLMASK, (a0 >> j) & 1u);
+            const unsigned hi = __ballot_sync(FULLMASK, (b0 >> j) & 1u);
+            if (lane == j) mine0 = (unsigned long long)lo | ((unsigned long long)hi << 32);
+        }
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            const unsigned lo = __ballot_sync(FULLMASK, (a1 >> j) & 1u);
+            const unsigned hi = __ballot_sync(FULLMASK, (b1 >> j) & 1u);
+            if (lane == j) mine1 = (unsigned long long)lo | ((unsigned long long)hi << 32);
+        }
+        if (lane < nk) rows[(k0 + lane) * ld + w] = mine0;
+        if (lane + 32 < nk) rows[(k0 + 32 + lane) * ld + w] = mine1;
     }
 }
 
@@ -507,13 +571,19 @@ cudaError_t launch_pack(const uint8_t *hap01, int n, long long m, int hap_major,
                         unsigned long long *rows, long long ld, cudaStream_t s)
 {
     const int W = (n + 63) / 64;
+    // grid-stride warps: 16 CTAs of 8 warps per SM at most
+    const long long cap = 16ll * device_sms();
     if (hap_major) {
-        long long blocks = (m * ld + 255) / 256;
-        if (blocks > 65536) blocks = 65536;
-        pack_hm_kernel<<<(unsigned)blocks, 256, 0, s>>>(hap01, n, m, W, rows, ld);
+        const long long tasks = (m + 63) / 64 * ld;
+        long long blocks = (tasks + 7) / 8;
+        if (blocks > cap) blocks = cap;
+        if (m % 16 == 0 && ((uintptr_t)hap01 & 15) == 0)
+            pack_hm_kernel<true><<<(unsigned)blocks, 256, 0, s>>>(hap01, n, m, W, rows, ld);
+        else
+            pack_hm_kernel<false><<<(unsigned)blocks, 256, 0, s>>>(hap01, n, m, W, rows, ld);
     } else {
-        long long blocks = (m * ld * 32 + 255) / 256;
-        if (blocks > 65536) blocks = 65536;
+        long long blocks = (m + 7) / 8;
+        if (blocks > cap) blocks = cap;
         pack_mm_kernel<<<(unsigned)blocks, 256, 0, s>>>(hap01, n, m, W, rows, ld);
     }
     return cudaGetLastError();

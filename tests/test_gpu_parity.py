@@ -287,6 +287,23 @@ def test_pack_matches_reference_packing(sg):
         assert np.array_equal(got2, want)
 
 
+def test_pack_any_byte_values_and_both_load_paths(sg):
+    """Only bit 0 of each byte counts; marker counts that are multiples of 16
+    take the haplotype-major kernel's 16-byte loads (with a ragged last block
+    of markers), the others its byte loads; row strides with pad words."""
+    rng = np.random.default_rng(7)
+    for n, m in ((130, 128), (70, 200), (64, 64), (65, 1024), (1000, 4096 + 16), (5, 80),
+                 (2049, 336)):
+        h = rng.integers(0, 256, size=(m, n), dtype=np.uint8)
+        for ld in ((n + 63) // 64, (n + 63) // 64 + 3):
+            want = synth.pack(h, ld=ld)
+            got = sg.selscan_pack(torch.from_numpy(h).cuda(), n, ld=ld)
+            assert np.array_equal(got.cpu().numpy().view(np.uint64), want), (n, m, ld, "mm")
+            hm = torch.from_numpy(np.ascontiguousarray(h.T)).cuda()
+            got2 = sg.selscan_pack(hm, n, hap_major=True, ld=ld)
+            assert np.array_equal(got2.cpu().numpy().view(np.uint64), want), (n, m, ld, "hm")
+
+
 def test_pack_matches_reference_packing_at_full_size(sg):
     """Device packing of the bench's 5,000 x 1,000,000 matrix from 0/1 bytes
     (5 GB), marker-major and haplotype-major, equals the generator's packing
