@@ -6,6 +6,7 @@
 // markers in a fixed order (thread stride, then a fixed tree); the segments
 // are combined in segment order.  Two passes: the mean, then the sum of
 // squared deviations about it (no cancellation of E[x^2] - E[x]^2).
+#include <limits.h>
 #include <math.h>
 
 #include "../../include/selscan.h"
@@ -41,6 +42,16 @@ __device__ __forceinline__ T block_sum(T v, T *red)
     return t;                       // valid in thread 0
 }
 
+// The markers of bin b are those with n1 in [lo, hi): bin_of(n1) = b exactly
+// when b n <= n1 nbins < (b + 1) n, i.e. ceil(b n / nbins) <= n1 <
+// ceil((b + 1) n / nbins), the first bin open below and the last open above
+// (bin_of clamps).  One interval per CTA, two compares per marker.
+__device__ __forceinline__ void bin_interval(int b, int n, int nbins, long long &lo, long long &hi)
+{
+    lo = b == 0 ? LLONG_MIN : ((long long)b * n + nbins - 1) / nbins;
+    hi = b == nbins - 1 ? LLONG_MAX : ((long long)(b + 1) * n + nbins - 1) / nbins;
+}
+
 // pass 0: count and sum per (bin, segment); pass 1: squared deviations about mean[bin]
 __global__ void __launch_bounds__(kNormThreads) norm_partial_kernel(
     const double *score, const int8_t *status, const int32_t *n1, long long m, int n, int nbins,
@@ -51,12 +62,15 @@ __global__ void __launch_bounds__(kNormThreads) norm_partial_kernel(
     const int b = blockIdx.x / kNormSegments, seg = blockIdx.x % kNormSegments;
     const long long per = (m + kNormSegments - 1) / kNormSegments;
     const long long lo = (long long)seg * per, hi = lo + per < m ? lo + per : m;
+    long long n1lo, n1hi;
+    bin_interval(b, n, nbins, n1lo, n1hi);
     double acc = 0.0;
     long long cnt = 0;
     const double mu = pass == 1 ? mean[b] : 0.0;
     for (long long k = lo + threadIdx.x; k < hi; k += kNormThreads) {
         if (status[k] != (int8_t)SELSCAN_LOCUS_OK) continue;
-        if (bin_of(n1[k], n, nbins) != b) continue;
+        const long long c = n1[k];
+        if (c < n1lo || c >= n1hi) continue;
         const double x = score[k];
         if (pass == 0) { acc += x; ++cnt; }
         else { const double d = x - mu; acc += d * d; }
