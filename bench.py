@@ -758,7 +758,7 @@ def hap_major_bytes(rows, n):
     return out
 
 
-def run_ingest(sg, torch, d, n, params, launch_fields, reps=3):
+def run_ingest(sg, torch, d, n, params, launch_fields, reps=3, streamed_steps=5):
     """Timed ingest of the bench's matrix: haplotype-major 0/1 bytes in pinned
     host memory -> H2D -> selscan_pack (device) -> the scan, per call; events
     split the three parts.  The packed rows equal the generator's."""
@@ -792,12 +792,36 @@ def run_ingest(sg, torch, d, n, params, launch_fields, reps=3):
     same = bool(torch.equal(rows, torch.from_numpy(d.rows.view(np.int64)).to(dev)))
     t = np.mean(np.array(times), axis=0)
     cores = int((out["status"] != sg.LOCUS_MAF_FILTERED).sum())
+    del dbytes, rows
+    # the same data sets streamed: upload and packing of data set k + 1 beside scan k
+    from paper_1403_6854_gb300.stream import scan_host_stream
+
+    def stream(steps):
+        last = None
+        for res in scan_host_stream([(host, h_pos, h_gmap)] * steps, sg.MODE_IHS, n,
+                                    params=params, launch=sg.make_launch(**launch_fields),
+                                    fields=("status", "lnratio"), workspace=ws,
+                                    layout="hap_major"):
+            last = res
+        return last
+
+    stream(2)                                   # untimed: buffers from the caches
+    torch.cuda.synchronize()
+    a0 = time.perf_counter()
+    last = stream(streamed_steps)
+    st_s = (time.perf_counter() - a0) / streamed_steps
+    assert int((last["status"].numpy() != sg.LOCUS_MAF_FILTERED).sum()) == cores
     return {"what": "haplotype-major 0/1 bytes in pinned host memory -> H2D -> selscan_pack -> "
                     "selscan_ihs, per call (CUDA events)",
             "h2d_bytes": int(host.numel() + h_pos.numel() * 8 + h_gmap.numel() * 8),
             "h2d_ms": float(t[0]), "pack_ms": float(t[1]), "scan_ms": float(t[2]),
             "total_ms": float(t.sum()), "value": cores / (float(t.sum()) / 1e3),
-            "unit": "core loci/s", "pack_equals_generator": same}
+            "unit": "core loci/s", "pack_equals_generator": same,
+            "streamed": {"what": "stream.scan_host_stream(layout='hap_major') over the same "
+                                 "data set: bytes uploaded and packed beside the previous scan, "
+                                 "scores read back; host clock to the last result",
+                         "steps": streamed_steps, "ms_per_scan": st_s * 1e3,
+                         "value": cores / st_s, "unit": "core loci/s"}}
 
 
 def run_served(args, torch, synth):

@@ -521,15 +521,22 @@ def selscan_ehh_noalloc(hap: torch.Tensor, n: int, pos: torch.Tensor, gmap: torc
 
 
 def selscan_pack(hap01: torch.Tensor, n: int, hap_major: bool = False, ld: Optional[int] = None,
-                 stream=None) -> torch.Tensor:
-    """uint8 0/1 matrix ([m, n], or [n, m] if hap_major) -> packed rows [m, ld] (int64 bits)."""
+                 stream=None, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """uint8 0/1 matrix ([m, n], or [n, m] if hap_major) -> packed rows [m, ld] (int64 bits),
+    written to ``out`` (a contiguous int64 [m, ld] CUDA tensor) if given."""
     lib = load_library()
     if hap01.dtype != torch.uint8 or not hap01.is_cuda or not hap01.is_contiguous():
         raise ValueError("hap01 must be a contiguous uint8 CUDA tensor")
     m = hap01.shape[1] if hap_major else hap01.shape[0]
     W = (n + 63) // 64
-    ld = W if ld is None else ld
-    rows = torch.empty((m, ld), dtype=torch.int64, device=hap01.device)
+    ld = (W if out is None else out.shape[1]) if ld is None else ld
+    if out is not None:
+        if (out.dtype != torch.int64 or not out.is_cuda or not out.is_contiguous()
+                or tuple(out.shape) != (m, ld)):
+            raise ValueError("out must be a contiguous int64 CUDA tensor [m, ld]")
+        rows = out
+    else:
+        rows = torch.empty((m, ld), dtype=torch.int64, device=hap01.device)
     rc = lib.selscan_pack(_ptr(hap01), n, m, 1 if hap_major else 0, _ptr(rows), ld, _stream(stream))
     if rc != OK:
         raise SelscanError(rc, "selscan_pack")

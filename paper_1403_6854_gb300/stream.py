@@ -11,6 +11,11 @@ CUDA events as the only ordering between the three.  The scans themselves are
 the library's ``selscan_ihs`` / ``selscan_xpehh`` calls on device buffers, so
 every result equals that of the same call on device-resident inputs bit for bit.
 
+iHS inputs may also be unpacked 0/1 bytes (haplotype-major [n, m] or
+marker-major [m, n], only bit 0 of each byte counts): they are uploaded as
+bytes and packed on the device (``selscan_pack``) on the upload stream, so
+the upload and packing of data set k + 1 run beside scan k.
+
 Host inputs should be in pinned memory (``tensor.pin_memory()``); pageable
 memory works but its copies do not overlap.
 """
@@ -21,7 +26,10 @@ from typing import Dict, Iterable, Iterator, Optional, Sequence, Tuple
 import torch
 
 from . import (MODE_IHS, MODE_XPEHH, SelscanError, _ihs_outputs, _workspace, _xpehh_outputs,
-               selscan_default_params, selscan_ihs, selscan_workspace_bytes, selscan_xpehh)
+               selscan_default_params, selscan_ihs, selscan_pack, selscan_workspace_bytes,
+               selscan_xpehh)
+
+LAYOUTS = ("rows", "hap_major", "marker_major")
 
 IHS_FIELDS = ("status", "n1", "ihh1", "ihh0", "lnratio", "stop")
 XPEHH_FIELDS = ("status", "n1", "ihhA", "ihhB", "lnratio", "stop")
@@ -30,7 +38,8 @@ XPEHH_FIELDS = ("status", "n1", "ihhA", "ihhB", "lnratio", "stop")
 def scan_host_stream(inputs: Iterable[Tuple[torch.Tensor, torch.Tensor, torch.Tensor]],
                      mode: int, n: int, nB: int = 0, max_m: int = 0, params=None, launch=None,
                      fields: Optional[Sequence[str]] = None,
-                     workspace: Optional[torch.Tensor] = None) -> Iterator[Dict[str, torch.Tensor]]:
+                     workspace: Optional[torch.Tensor] = None,
+                     layout: str = "rows") -> Iterator[Dict[str, torch.Tensor]]:
     """Scan each (rows [m, ld] 64-bit, pos [m] int64, gmap [m] float64) host triple in
     turn on the current CUDA device and yield its results in host tensors (the
     ``fields`` of the scan's output dict, trimmed to m entries), in input order.
@@ -45,11 +54,20 @@ def scan_host_stream(inputs: Iterable[Tuple[torch.Tensor, torch.Tensor, torch.Te
     device-side error (unsorted positions, a timed-out wait) raises SelscanError
     when the result of that scan is reached.  Closing the generator early waits
     for its copies in flight.
+
+    layout: "rows" (the default: each input's first tensor is the packed matrix),
+    or, for iHS, "hap_major" (uint8 [n, m]) / "marker_major" (uint8 [m, n]) 0/1
+    bytes, packed on the device into rows of (n + 63) // 64 words.
     """
     if mode not in (MODE_IHS, MODE_XPEHH):
         raise ValueError("mode must be MODE_IHS or MODE_XPEHH")
     if mode == MODE_XPEHH and nB < 1:
         raise ValueError("XPEHH needs nB >= 1")
+    if layout not in LAYOUTS:
+        raise ValueError(f"layout must be one of {LAYOUTS}")
+    if layout != "rows" and mode != MODE_IHS:
+        raise ValueError("byte layouts are packed for iHS scans only")
+    hap_major = layout == "hap_major"
     fields = tuple(fields) if fields is not None else (IHS_FIELDS if mode == MODE_IHS
                                                        else XPEHH_FIELDS)
     p = params if params is not None else selscan_default_params()
@@ -57,7 +75,11 @@ def scan_host_stream(inputs: Iterable[Tuple[torch.Tensor, torch.Tensor, torch.Te
     first = next(it, None)
     if first is None:
         return
-    m0, ld = first[0].shape
+    if layout == "rows":
+        m0, ld = first[0].shape
+    else:
+        m0 = first[0].shape[1] if hap_major else first[0].shape[0]
+        ld = (n + 63) // 64
     cap = max(int(max_m), int(m0))
     n_total = n + (nB if mode == MODE_XPEHH else 0)
     dev = torch.device("cuda", torch.cuda.current_device())
@@ -68,6 +90,9 @@ def scan_host_stream(inputs: Iterable[Tuple[torch.Tensor, torch.Tensor, torch.Te
     d_in = [(torch.empty((cap, ld), dtype=torch.int64, device=dev),
              torch.empty(cap, dtype=torch.int64, device=dev),
              torch.empty(cap, dtype=torch.float64, device=dev)) for _ in range(2)]
+    # byte layouts: the uploaded bytes of each slot, packed into its rows
+    d_bytes = ([torch.empty(n * cap, dtype=torch.uint8, device=dev) for _ in range(2)]
+               if layout != "rows" else None)
     mk = _ihs_outputs if mode == MODE_IHS else _xpehh_outputs
     d_out = [mk(cap, dev) for _ in range(2)]
     h_out = [{f: torch.empty(d_out[0][f].shape, dtype=d_out[0][f].dtype).pin_memory()
@@ -80,16 +105,28 @@ def scan_host_stream(inputs: Iterable[Tuple[torch.Tensor, torch.Tensor, torch.Te
 
     def upload(slot: int, item) -> int:
         rows, pos, gmap = item
-        m = rows.shape[0]
-        if rows.dim() != 2 or rows.shape[1] != ld or rows.element_size() != 8:
-            raise ValueError("every input's rows must be [m, ld] 64-bit with one ld")
+        if layout == "rows":
+            m = rows.shape[0]
+            if rows.dim() != 2 or rows.shape[1] != ld or rows.element_size() != 8:
+                raise ValueError("every input's rows must be [m, ld] 64-bit with one ld")
+        else:
+            m = rows.shape[1] if hap_major else rows.shape[0]
+            if (rows.dim() != 2 or rows.dtype != torch.uint8 or not rows.is_contiguous()
+                    or rows.shape[0 if hap_major else 1] != n):
+                raise ValueError("byte inputs must be contiguous uint8 [n, m] (hap_major) "
+                                 "or [m, n] (marker_major)")
         if m > cap or pos.shape[0] != m or gmap.shape[0] != m:
             raise ValueError(f"marker count {m} above max_m {cap} or inconsistent arrays")
         if used[slot]:                    # the scan before last read this input set
             up.wait_event(scan_done[slot])
         with torch.cuda.stream(up):
             r, ps, g = d_in[slot]
-            r[:m].copy_(rows.view(torch.int64), non_blocking=True)
+            if layout == "rows":
+                r[:m].copy_(rows.view(torch.int64), non_blocking=True)
+            else:
+                b = d_bytes[slot][:n * m].view(rows.shape)
+                b.copy_(rows, non_blocking=True)
+                selscan_pack(b, n, hap_major=hap_major, stream=up, out=r[:m])
             ps[:m].copy_(pos, non_blocking=True)
             g[:m].copy_(gmap, non_blocking=True)
         up_done[slot].record(up)

@@ -104,3 +104,21 @@ def test_stream_closed_early_then_reused(sg):
     r = list(scan_host_stream([h], sg.MODE_IHS, 100, fields=("lnratio", "stop")))
     assert len(r) == 1
     assert_bitwise_equal({f: v.numpy() for f, v in r[0].items()}, want)
+
+
+@pytest.mark.parametrize("layout", ["hap_major", "marker_major"])
+def test_ihs_stream_of_unpacked_bytes(sg, layout):
+    """0/1 bytes uploaded and packed on the device inside the stream: every
+    result equals the scan of the generator's packed rows."""
+    from paper_1403_6854_gb300.stream import IHS_FIELDS, scan_host_stream
+    sets = chr22_sets()
+    items = []
+    for rows, pos, gmap in sets:
+        mm = synth.unpack(np.ascontiguousarray(rows), 204)            # [m, n] bytes
+        b = np.ascontiguousarray(mm.T) if layout == "hap_major" else mm
+        items.append((torch.from_numpy(b).pin_memory(),) + host(rows, pos, gmap)[1:])
+    got = [{f: v.numpy().copy() for f, v in r.items()}
+           for r in scan_host_stream(items, sg.MODE_IHS, 204, max_m=22147, layout=layout)]
+    assert len(got) == len(sets)
+    for g, s in zip(got, sets):
+        assert_bitwise_equal(g, device_result(sg, sg.MODE_IHS, 204, 0, *s, None, IHS_FIELDS))
