@@ -501,17 +501,16 @@ __device__ __forceinline__ unsigned byte_lsbs(unsigned x) { return ((x & 0x01010
 // Bit j of (a, b) = bit 0 of p[j] (a: j < 32, b: j >= 32) for j < nk <= 64;
 // VEC: p is 16-byte aligned and nk = 64 (four 16-byte loads).
 template <bool VEC>
-__device__ __forceinline__ void lsb_mask64(const uint8_t *p, int nk, unsigned &a, unsigned &b)
+__device__ __forceinline__ void lsb_mask64(const uint4 *v, const uint8_t *p, int nk, unsigned &a,
+                                           unsigned &b)
 {
     a = 0u;
     b = 0u;
     if (VEC && nk == 64) {
-        const uint4 *q = (const uint4 *)p;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-            const uint4 v = __ldg(q + i);
-            const unsigned s = byte_lsbs(v.x) | (byte_lsbs(v.y) << 4) | (byte_lsbs(v.z) << 8) |
-                               (byte_lsbs(v.w) << 12);
+            const unsigned s = byte_lsbs(v[i].x) | (byte_lsbs(v[i].y) << 4) |
+                               (byte_lsbs(v[i].z) << 8) | (byte_lsbs(v[i].w) << 12);
             if (i < 2) a |= s << (16 * i);
             else b |= s << (16 * (i - 2));
         }
@@ -524,13 +523,28 @@ __device__ __forceinline__ void lsb_mask64(const uint8_t *p, int nk, unsigned &a
     }
 }
 
+// 32 x 32 bit transpose across a warp: lane l holds row l (bit c = entry (l, c));
+// afterwards lane j holds column j (bit i = entry (i, j)).  Five butterfly stages
+// exchange the off-diagonal blocks of halving size with the partner lane.
+__device__ __forceinline__ unsigned warp_transpose32(unsigned x, int lane)
+{
+    unsigned msk = 0x0000FFFFu;
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1, msk ^= msk << s) {
+        const unsigned y = __shfl_xor_sync(FULLMASK, x, s);
+        x = (lane & s) ? ((x & ~msk) | ((y >> s) & msk)) : ((x & msk) | ((y << s) & ~msk));
+    }
+    return x;
+}
+
 // haplotype-major input [n, m] bytes: a warp packs word w of 64 consecutive
 // markers.  Lane l reads markers [k0, k0 + 64) of haplotypes 64 w + l and
-// 64 w + 32 + l (contiguous bytes of their rows), keeps bit 0 of each byte in a
-// 64-bit mask per haplotype, and one ballot per marker and half transposes the
-// masks into the markers' words; lane j stores the words of markers k0 + j and
-// k0 + 32 + j.  Consecutive warps take consecutive words of the same markers,
-// so the stores of a row segment meet in L2.
+// 64 w + 32 + l (contiguous bytes of their rows, both rows' loads issued
+// together), keeps bit 0 of each byte in a 64-bit mask per haplotype, and four
+// 32 x 32 bit transposes across the warp turn the masks into the markers'
+// words; lane j stores the words of markers k0 + j and k0 + 32 + j.
+// Consecutive warps take consecutive words of the same markers, so the stores
+// of a row segment meet in L2.
 template <bool VEC>
 __global__ void __launch_bounds__(256) pack_hm_kernel(const uint8_t *hap01, int n, long long m,
                                                       int W, unsigned long long *rows, long long ld)
@@ -546,24 +560,28 @@ __global__ void __launch_bounds__(256) pack_hm_kernel(const uint8_t *hap01, int 
         unsigned a0 = 0u, a1 = 0u, b0 = 0u, b1 = 0u;     // haplotype 64 w + l: a; + 32: b
         if (w < W) {
             const long long h0 = 64 * w + lane, h1 = h0 + 32;
-            if (h0 < n) lsb_mask64<VEC>(hap01 + h0 * m + k0, nk, a0, a1);
-            if (h1 < n) lsb_mask64<VEC>(hap01 + h1 * m + k0, nk, b0, b1);
-        }
-        unsigned long long mine0 = 0, mine1 = 0;
+            const bool v0 = h0 < n, v1 = h1 < n;
+            // rows past n read row 0 (it exists) and are dropped
+            const uint8_t *p0 = hap01 + (v0 ? h0 : 0) * m + k0;
+            const uint8_t *p1 = hap01 + (v1 ? h1 : 0) * m + k0;
+            uint4 q0[4], q1[4];
+            if (VEC && nk == 64) {
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-            const unsigned lo = __ballot_sync(FULLMASK, (a0 >> j) & 1u);
-            const unsigned hi = __ballot_sync(FULLMASK, (b0 >> j) & 1u);
-            if (lane == j) mine0 = (unsigned long long)lo | ((unsigned long long)hi << 32);
+                for (int i = 0; i < 4; ++i) {
+                    q0[i] = __ldg((const uint4 *)p0 + i);
+                    q1[i] = __ldg((const uint4 *)p1 + i);
+                }
+            }
+            lsb_mask64<VEC>(q0, p0, nk, a0, a1);
+            lsb_mask64<VEC>(q1, p1, nk, b0, b1);
+            if (!v0) { a0 = 0u; a1 = 0u; }
+            if (!v1) { b0 = 0u; b1 = 0u; }
         }
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-            const unsigned lo = __ballot_sync(FULLMASK, (a1 >> j) & 1u);
-            const unsigned hi = __ballot_sync(FULLMASK, (b1 >> j) & 1u);
-            if (lane == j) mine1 = (unsigned long long)lo | ((unsigned long long)hi << 32);
-        }
-        if (lane < nk) rows[(k0 + lane) * ld + w] = mine0;
-        if (lane + 32 < nk) rows[(k0 + 32 + lane) * ld + w] = mine1;
+        const unsigned lo0 = warp_transpose32(a0, lane), hi0 = warp_transpose32(b0, lane);
+        const unsigned lo1 = warp_transpose32(a1, lane), hi1 = warp_transpose32(b1, lane);
+        if (lane < nk) rows[(k0 + lane) * ld + w] = (unsigned long long)lo0 | ((unsigned long long)hi0 << 32);
+        if (lane + 32 < nk)
+            rows[(k0 + 32 + lane) * ld + w] = (unsigned long long)lo1 | ((unsigned long long)hi1 << 32);
     }
 }
 
