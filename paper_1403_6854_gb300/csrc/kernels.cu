@@ -537,8 +537,9 @@ __device__ __forceinline__ unsigned warp_transpose32(unsigned x, int lane)
     return x;
 }
 
-// haplotype-major input [n, m] bytes: a warp packs word w of 64 consecutive
-// markers.  Lane l reads markers [k0, k0 + 64) of haplotypes 64 w + l and
+// haplotype-major input [n, m] bytes, markers [kbeg, m) (the ragged tail of
+// the staged kernel below, or everything when rows do not start on 16-byte
+// boundaries): a warp packs word w of 64 consecutive markers.  Lane l reads markers [k0, k0 + 64) of haplotypes 64 w + l and
 // 64 w + 32 + l (contiguous bytes of their rows, both rows' loads issued
 // together), keeps bit 0 of each byte in a 64-bit mask per haplotype, and four
 // 32 x 32 bit transposes across the warp turn the masks into the markers'
@@ -547,15 +548,16 @@ __device__ __forceinline__ unsigned warp_transpose32(unsigned x, int lane)
 // of a row segment meet in L2.
 template <bool VEC>
 __global__ void __launch_bounds__(256) pack_hm_kernel(const uint8_t *hap01, int n, long long m,
-                                                      int W, unsigned long long *rows, long long ld)
+                                                      int W, unsigned long long *rows, long long ld,
+                                                      long long kbeg)
 {
     const int lane = threadIdx.x & 31;
-    const long long tasks = (m + 63) / 64 * ld;
+    const long long tasks = (m - kbeg + 63) / 64 * ld;
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
     for (long long t = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; t < tasks; t += nw) {
         const long long kb = t / ld;
         const long long w = t - kb * ld;
-        const long long k0 = kb * 64;
+        const long long k0 = kbeg + kb * 64;
         const int nk = m - k0 < 64 ? (int)(m - k0) : 64;
         unsigned a0 = 0u, a1 = 0u, b0 = 0u, b1 = 0u;     // haplotype 64 w + l: a; + 32: b
         if (w < W) {
@@ -585,6 +587,60 @@ __global__ void __launch_bounds__(256) pack_hm_kernel(const uint8_t *hap01, int 
     }
 }
 
+// haplotype-major input [n, m] bytes, m a multiple of 16 and the input 16-byte
+// aligned, whole tiles of kPackTile markers: a CTA packs word w of one tile.
+// Warp v reads rows 64 w + 8 v .. + 7 as whole kPackTile-byte pieces (one
+// coalesced 16-byte load per lane and row), folds each lane's 16 bytes into a
+// 16-bit mask and pairs the masks of neighbouring lanes into the row's 32-bit
+// mask words in shared memory (stride 17 words: the transpose's reads of one
+// word of 32 rows hit distinct banks); then warp v transposes markers
+// [64 v, 64 v + 64) of the tile as the warp kernel does.
+constexpr int kPackTile = 512;
+__global__ void __launch_bounds__(256) pack_hm_staged_kernel(const uint8_t *hap01, int n,
+                                                             long long m, int W,
+                                                             unsigned long long *rows, long long ld)
+{
+    __shared__ unsigned msk[64][kPackTile / 32 + 1];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const long long tasks = m / kPackTile * ld;
+    for (long long t = blockIdx.x; t < tasks; t += gridDim.x) {
+        const long long kb = t / ld;
+        const long long w = t - kb * ld;
+        const long long k0 = kb * kPackTile;
+        if (w < W) {
+            uint4 q[8];
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {              // all eight loads in flight at once
+                const long long h = 64 * w + 8 * warp + r;
+                q[r] = __ldg((const uint4 *)(hap01 + (h < n ? h : 0) * m + k0) + lane);
+            }
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                const long long h = 64 * w + 8 * warp + r;
+                unsigned v = byte_lsbs(q[r].x) | (byte_lsbs(q[r].y) << 4) |
+                             (byte_lsbs(q[r].z) << 8) | (byte_lsbs(q[r].w) << 12);
+                if (h >= n) v = 0u;
+                const unsigned hi = __shfl_down_sync(FULLMASK, v, 1);
+                if ((lane & 1) == 0) msk[8 * warp + r][lane >> 1] = v | (hi << 16);
+            }
+        }
+        __syncthreads();
+        unsigned a0 = 0u, a1 = 0u, b0 = 0u, b1 = 0u;
+        if (w < W) {
+            a0 = msk[lane][2 * warp];
+            a1 = msk[lane][2 * warp + 1];
+            b0 = msk[lane + 32][2 * warp];
+            b1 = msk[lane + 32][2 * warp + 1];
+        }
+        __syncthreads();                               // the next tile may refill msk
+        const unsigned lo0 = warp_transpose32(a0, lane), hi0 = warp_transpose32(b0, lane);
+        const unsigned lo1 = warp_transpose32(a1, lane), hi1 = warp_transpose32(b1, lane);
+        const long long k = k0 + 64 * warp + lane;
+        rows[k * ld + w] = (unsigned long long)lo0 | ((unsigned long long)hi0 << 32);
+        rows[(k + 32) * ld + w] = (unsigned long long)lo1 | ((unsigned long long)hi1 << 32);
+    }
+}
+
 cudaError_t launch_pack(const uint8_t *hap01, int n, long long m, int hap_major,
                         unsigned long long *rows, long long ld, cudaStream_t s)
 {
@@ -592,13 +648,23 @@ cudaError_t launch_pack(const uint8_t *hap01, int n, long long m, int hap_major,
     // grid-stride warps: 16 CTAs of 8 warps per SM at most
     const long long cap = 16ll * device_sms();
     if (hap_major) {
-        const long long tasks = (m + 63) / 64 * ld;
-        long long blocks = (tasks + 7) / 8;
-        if (blocks > cap) blocks = cap;
-        if (m % 16 == 0 && ((uintptr_t)hap01 & 15) == 0)
-            pack_hm_kernel<true><<<(unsigned)blocks, 256, 0, s>>>(hap01, n, m, W, rows, ld);
-        else
-            pack_hm_kernel<false><<<(unsigned)blocks, 256, 0, s>>>(hap01, n, m, W, rows, ld);
+        const bool vec = m % 16 == 0 && ((uintptr_t)hap01 & 15) == 0;
+        long long kbeg = 0;
+        if (vec && m >= kPackTile) {
+            const long long tiles = m / kPackTile * ld;
+            const long long blocks = tiles < cap ? tiles : cap;
+            pack_hm_staged_kernel<<<(unsigned)blocks, 256, 0, s>>>(hap01, n, m, W, rows, ld);
+            kbeg = m / kPackTile * kPackTile;
+        }
+        if (kbeg < m) {
+            const long long tasks = (m - kbeg + 63) / 64 * ld;
+            long long blocks = (tasks + 7) / 8;
+            if (blocks > cap) blocks = cap;
+            if (vec)
+                pack_hm_kernel<true><<<(unsigned)blocks, 256, 0, s>>>(hap01, n, m, W, rows, ld, kbeg);
+            else
+                pack_hm_kernel<false><<<(unsigned)blocks, 256, 0, s>>>(hap01, n, m, W, rows, ld, kbeg);
+        }
     } else {
         long long blocks = (m + 7) / 8;
         if (blocks > cap) blocks = cap;
