@@ -213,11 +213,11 @@ def run_reference(args, rank, world):
 SWEEP_DRAM_BYTES_PER_CORE = 4.6139e9 / 125020
 # ncu capture of the 250k case (5,000 x 250,000, default sweep shape; summarised
 # in profiles/sweep_split_walk_ihs250k_full.md): sweep_kernel alone read + wrote
-# 3.486 GB (125,020 core loci) and issued 7.164e9 warp instructions over
+# 3.489 GB (125,020 core loci) and issued 7.164e9 warp instructions over
 # 997,618 marker passes of 5,120 elements, i.e. 44.88 thread instructions per
 # sorted element and marker pass, 19.80 of them on the ALU pipe
 # (sm__inst_executed_pipe_alu 3.161e9 warp instructions)
-SORT_DRAM_BYTES_PER_CORE = 3.4856e9 / 125020
+SORT_DRAM_BYTES_PER_CORE = 3.4889e9 / 125020
 SORT_INSTR_PER_ELEMENT_PASS = 44.88
 SORT_ALU_OPS_PER_ELEMENT_PASS = 19.80
 
@@ -493,7 +493,7 @@ def main():
                         "achieved": ops / 1e9, "peak": issue_peak / 1e9, "unit": "Gop/s",
                         "frac": ops / issue_peak,
                         "traffic": cores * SORT_DRAM_BYTES_PER_CORE,
-                        "traffic_note": "ncu capture of the 250k case (3.486 GB of sweep_kernel "
+                        "traffic_note": "ncu capture of the 250k case (3.489 GB of sweep_kernel "
                                         "DRAM traffic over 125,020 core loci), scaled by core loci",
                         "kernel_ms": sort_ms, "split_walk_ms": walk_ms - sort_ms,
                         "element_passes": element_passes, "marker_passes": work[0],
