@@ -2,10 +2,13 @@
 // score is centred and scaled by the mean and standard deviation of its
 // frequency bin, over all markers passed in (the caller's genome).
 //
-// Deterministic reduction: CTA (b, s) sums bin b over segment s of the
-// markers in a fixed order (thread stride, then a fixed tree); the segments
-// are combined in segment order.  Two passes: the mean, then the sum of
-// squared deviations about it (no cancellation of E[x^2] - E[x]^2).
+// Deterministic reduction, two forms.  Up to kNormPrivMaxBins bins: CTA s reads
+// segment s of the markers once; each of its threads adds its markers (thread
+// stride) into its own per-bin accumulators in shared memory, then one thread
+// per bin adds the threads' values in thread order.  More bins: CTA (b, s)
+// sums bin b over segment s (thread stride, then a fixed tree).  Either way
+// the segments are combined in segment order.  Two passes: the mean, then the
+// sum of squared deviations about it (no cancellation of E[x^2] - E[x]^2).
 #include <limits.h>
 #include <math.h>
 
@@ -17,7 +20,11 @@ namespace selscan {
 namespace {
 
 constexpr int kNormThreads = 256;
-constexpr int kNormSegments = 16;
+constexpr int kNormSegments = 16;           // per-bin form: segments per bin
+constexpr int kNormPrivThreads = 64;        // private-accumulator form
+constexpr int kNormPrivMaxBins = 128;       // its accumulators: 128 x 64 x 12 B = 96 KB
+constexpr int kNormPrivSegments = 304;
+constexpr int kNormMaxSegments = kNormPrivSegments > kNormSegments ? kNormPrivSegments : kNormSegments;
 
 __device__ __forceinline__ int bin_of(int32_t n1, int n, int nbins)
 {
@@ -83,17 +90,76 @@ __global__ void __launch_bounds__(kNormThreads) norm_partial_kernel(
     }
 }
 
-// Per-bin totals of the segment partials, segments in order: pass 0 the
+// pass 0: count and sum per (segment, bin); pass 1: squared deviations about
+// mean[bin].  Shared memory: sums [nbins][64] (double), counts [nbins][64].
+__global__ void __launch_bounds__(kNormPrivThreads) norm_partial_private_kernel(
+    const double *score, const int8_t *status, const int32_t *n1, long long m, int n, int nbins,
+    int pass, const double *mean, double *part_sum, long long *part_cnt)
+{
+    extern __shared__ double psum[];
+    int *pcnt = (int *)(psum + (size_t)nbins * kNormPrivThreads);
+    const int t = threadIdx.x;
+    for (int b = 0; b < nbins; ++b) {
+        psum[b * kNormPrivThreads + t] = 0.0;
+        pcnt[b * kNormPrivThreads + t] = 0;
+    }
+    const long long per = (m + kNormPrivSegments - 1) / kNormPrivSegments;
+    const long long lo = (long long)blockIdx.x * per, hi = lo + per < m ? lo + per : m;
+    const bool small = (unsigned long long)n * (unsigned long long)nbins < (1ull << 32);
+    constexpr int U = 4;                         // markers whose loads are in flight together
+    for (long long k0 = lo + t; k0 < hi; k0 += U * kNormPrivThreads) {
+        int8_t st[U];
+        int32_t c1[U];
+        double x[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const long long k = k0 + (long long)u * kNormPrivThreads;
+            st[u] = k < hi ? status[k] : (int8_t)-1;
+            c1[u] = k < hi ? n1[k] : 0;
+            x[u] = k < hi ? score[k] : 0.0;
+        }
+        // in marker order, as one marker at a time would add them
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (st[u] != (int8_t)SELSCAN_LOCUS_OK) continue;
+            // bin_of in 32 bits where n nbins fits them (0 <= n1 < n): n1 >= n is
+            // the last bin, n1 <= 0 the first
+            int b;
+            if (!small) b = bin_of(c1[u], n, nbins);
+            else if (c1[u] <= 0) b = 0;
+            else if (c1[u] >= n) b = nbins - 1;
+            else b = (int)((unsigned)c1[u] * (unsigned)nbins / (unsigned)n);
+            double v = x[u];
+            if (pass == 1) { const double d = x[u] - mean[b]; v = d * d; }
+            psum[b * kNormPrivThreads + t] += v;   // this thread's slot: no other writer
+            pcnt[b * kNormPrivThreads + t] += 1;
+        }
+    }
+    __syncthreads();
+    for (int b = t; b < nbins; b += kNormPrivThreads) {
+        double sum = 0.0;
+        long long c = 0;
+        for (int j = 0; j < kNormPrivThreads; ++j) {
+            sum += psum[b * kNormPrivThreads + j];
+            c += pcnt[b * kNormPrivThreads + j];
+        }
+        part_sum[(size_t)b * kNormPrivSegments + blockIdx.x] = sum;
+        if (pass == 0) part_cnt[(size_t)b * kNormPrivSegments + blockIdx.x] = c;
+    }
+}
+
+// Per-bin totals of the nseg segment partials, segments in order: pass 0 the
 // count and the sum, pass 1 the sum of squared deviations.
-__global__ void norm_sums_kernel(int nbins, int pass, const double *part_sum,
+__global__ void norm_sums_kernel(int nbins, int pass, int nseg, const double *part_sum,
                                  const long long *part_cnt, long long *bin_count, double *bin_sum)
 {
     for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nbins; b += gridDim.x * blockDim.x) {
         double s = 0.0;
         long long c = 0;
-        for (int seg = 0; seg < kNormSegments; ++seg) {
-            s += part_sum[b * kNormSegments + seg];
-            c += part_cnt[b * kNormSegments + seg];
+#pragma unroll 8
+        for (int seg = 0; seg < nseg; ++seg) {
+            s += part_sum[(size_t)b * nseg + seg];
+            c += part_cnt[(size_t)b * nseg + seg];
         }
         bin_sum[b] = s;
         if (pass == 0) bin_count[b] = c;
@@ -140,7 +206,7 @@ namespace {
 
 size_t parts_bytes(int nbins)
 {
-    return ((size_t)nbins * kNormSegments * 8 + 255) & ~(size_t)255;
+    return ((size_t)nbins * kNormMaxSegments * 8 + 255) & ~(size_t)255;
 }
 
 bool norm_args_ok(const double *score, const int8_t *status, const int32_t *n1, int64_t m,
@@ -156,11 +222,21 @@ void launch_bin_sums(const double *score, const int8_t *status, const int32_t *n
                      long long *bin_count, double *bin_sum, double *part_sum, long long *part_cnt,
                      cudaStream_t s)
 {
-    const unsigned grid = (unsigned)(nbins * kNormSegments);
-    norm_partial_kernel<<<grid, kNormThreads, 0, s>>>(score, status, n1, m, n, nbins, pass, bin_mean,
-                                                      part_sum, part_cnt);
-    norm_sums_kernel<<<(nbins + 127) / 128, 128, 0, s>>>(nbins, pass, part_sum, part_cnt, bin_count,
-                                                         bin_sum);
+    int nseg = kNormSegments;
+    if (nbins <= kNormPrivMaxBins) {
+        const size_t smem = (size_t)nbins * kNormPrivThreads * (sizeof(double) + sizeof(int));
+        cudaFuncSetAttribute(norm_partial_private_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)((size_t)kNormPrivMaxBins * kNormPrivThreads * 12));
+        norm_partial_private_kernel<<<kNormPrivSegments, kNormPrivThreads, smem, s>>>(
+            score, status, n1, m, n, nbins, pass, bin_mean, part_sum, part_cnt);
+        nseg = kNormPrivSegments;
+    } else {
+        const unsigned grid = (unsigned)(nbins * kNormSegments);
+        norm_partial_kernel<<<grid, kNormThreads, 0, s>>>(score, status, n1, m, n, nbins, pass,
+                                                          bin_mean, part_sum, part_cnt);
+    }
+    norm_sums_kernel<<<(nbins + 127) / 128, 128, 0, s>>>(nbins, pass, nseg, part_sum, part_cnt,
+                                                         bin_count, bin_sum);
 }
 
 void launch_apply(const double *score, const int8_t *status, const int32_t *n1, int64_t m,

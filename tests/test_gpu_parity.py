@@ -207,7 +207,9 @@ def test_normalize_xpehh_genome_wide_on_gpu(sg, xp):
 
 def test_normalize_edge_cases_on_gpu(sg):
     dev = torch.device("cuda")
-    for m, n, nbins in ((1, 10, 1), (7, 10, 4), (3000, 500, 1024)):
+    # 128 bins and fewer: per-thread accumulators, one read of the markers; more: per-bin CTAs
+    for m, n, nbins in ((1, 10, 1), (7, 10, 4), (3000, 500, 1024), (200_000, 5000, 128),
+                        (200_000, 5000, 129), (1_000_000, 5000, 100)):
         rng = np.random.default_rng(m)
         score = rng.normal(size=m)
         st = rng.choice(np.array([0, 0, 0, 1, 2, 3, 4], dtype=np.int8), size=m)

@@ -64,6 +64,20 @@ def test_ihs_stream_equals_device_calls(sg, schedule):
         assert_bitwise_equal(g, want)
 
 
+def test_stream_growing_marker_counts(sg):
+    """Data sets in increasing size: the workspace sized for the first is
+    replaced when a later one needs more (sorted sweep, stages by size)."""
+    from paper_1403_6854_gb300.stream import IHS_FIELDS, scan_host_stream
+    sets = list(reversed(sorted(chr22_sets(), key=lambda t: -t[0].shape[0])))
+    assert sets[0][0].shape[0] < sets[-1][0].shape[0]
+    launch = sg.make_launch(sg.SCHED_SWEEP)
+    got = [{f: v.numpy().copy() for f, v in r.items()}
+           for r in scan_host_stream([host(*s) for s in sets], sg.MODE_IHS, 204, max_m=22147,
+                                     launch=launch)]
+    for g, s in zip(got, sets):
+        assert_bitwise_equal(g, device_result(sg, sg.MODE_IHS, 204, 0, *s, launch, IHS_FIELDS))
+
+
 def test_xpehh_stream_equals_device_calls(sg):
     from paper_1403_6854_gb300.stream import XPEHH_FIELDS, scan_host_stream
     sets = []
