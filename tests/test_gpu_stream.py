@@ -136,3 +136,27 @@ def test_ihs_stream_of_unpacked_bytes(sg, layout):
     assert len(got) == len(sets)
     for g, s in zip(got, sets):
         assert_bitwise_equal(g, device_result(sg, sg.MODE_IHS, 204, 0, *s, None, IHS_FIELDS))
+
+
+def test_stream_passes_parameters(sg):
+    """Non-default parameters (physical map, the crossing term, a 1/4 cutoff)
+    reach every scan of the stream."""
+    from paper_1403_6854_gb300.stream import IHS_FIELDS, XPEHH_FIELDS, scan_host_stream
+    p = sg.selscan_default_params(use_physical_map=1, include_crossing_term=1, ehh_cut=(1, 4))
+    sets = chr22_sets()[:2]
+    got = [{f: v.numpy().copy() for f, v in r.items()}
+           for r in scan_host_stream([host(*s) for s in sets], sg.MODE_IHS, 204, max_m=22147,
+                                     params=p)]
+    for g, (rows, pos, gmap) in zip(got, sets):
+        hap, dp, dg = sg.to_device(rows, pos, gmap)
+        want = sg.selscan_ihs(hap, 204, dp, dg, params=p)
+        sg.check(want)
+        w = to_np(want)
+        assert_bitwise_equal(g, {f: w[f] for f in IHS_FIELDS})
+    d = synth.generate(synth.spec("xpehh"))
+    r = next(scan_host_stream([host(d.rows, d.pos, d.gmap)], sg.MODE_XPEHH, 204, 210, params=p))
+    hap, dp, dg = sg.to_device(d.rows, d.pos, d.gmap)
+    want = sg.selscan_xpehh(hap, 204, 210, dp, dg, params=p)
+    sg.check(want)
+    w = to_np(want)
+    assert_bitwise_equal({f: v.numpy() for f, v in r.items()}, {f: w[f] for f in XPEHH_FIELDS})
