@@ -231,6 +231,9 @@ def main():
     ap.add_argument("--workload", default="ihs1m", choices=list(WORKLOADS))
     ap.add_argument("--schedule", type=int, default=-1,
                     help="-1: autotuned launch shape; 0/1/2/3: fixed schedule with defaults")
+    ap.add_argument("--stage-cores", type=int, default=0,
+                    help="with --schedule 3: cores per chunk and sweep stage (0: the default "
+                         "single stage); smaller stages need less workspace")
     ap.add_argument("--tune-cache", action="store_true")
     ap.add_argument("--served", type=int, default=200, help="requests in the served mix (0: skip)")
     ap.add_argument("--load", type=float, default=0.7, help="served arrival rate / capacity")
@@ -296,6 +299,9 @@ def main():
     if args.schedule >= 0:
         launch_fields, shape = dict(schedule=args.schedule), {"schedule": args.schedule,
                                                               "source": "--schedule"}
+        if args.stage_cores > 0:
+            launch_fields["sweep_stage_cores"] = args.stage_cores
+            shape["sweep_stage_cores"] = args.stage_cores
     else:
         tuner = Autotuner(cache_path=os.path.join(ROOT, "_build_tune.json") if args.tune_cache else None)
         _, shape = tuner.launch_for(hap, pos, gmap, "ihs", n)
@@ -512,6 +518,13 @@ def main():
                         "int_peaks_ops_per_sm_per_cycle": {k: round(v["ops_per_sm_per_cycle"], 2)
                                                            for k, v in pk.items()},
                         "path": path}
+            if args.stage_cores > 0:
+                # several stages: the timed sort is the first stage's, the passes are every
+                # stage's, so no fraction is formed from them
+                for r in (roofline, roofline["alu_pipe"]):
+                    r["achieved"] = None
+                    r["frac"] = None
+                roofline["note"] = "several sweep stages (--stage-cores): no sort fraction"
         else:
             roofline = dict(path, kernel="walk_persistent_kernel (both passes)", traffic=None)
         line = {
