@@ -122,7 +122,9 @@ def test_gap_rules_and_parameters(sg):
 
 
 def test_xpehh_small_and_maf_flag(sg):
-    for nA, nB in ((2, 2), (5, 64), (64, 65), (100, 31)):
+    # pooled sizes 32, 64 and 128 too: the population flags' last word then holds
+    # only position n
+    for nA, nB in ((2, 2), (5, 64), (64, 65), (100, 31), (20, 12), (40, 24), (64, 64)):
         hap, pos, gmap = synth.tiny_mosaic(nA + nB, 35, nA * 31 + nB, founders=3, switch=0.1,
                                            flip=0.03)
         rows = np.concatenate([synth.pack(hap[:, :nA]), synth.pack(hap[:, nA:])], 1)
