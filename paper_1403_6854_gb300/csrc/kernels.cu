@@ -40,6 +40,10 @@ cudaError_t launch_validate(const long long *pos, const double *gmap, long long 
 }
 
 // ------------------------------------------------------------ core select
+// A warp counts the derived alleles of kCoreRows rows at once: lane l reads the
+// 64-bit words l, l + 32, ... of each of them, all of a round's loads issued
+// before the popcounts, then one warp sum per row.
+constexpr int kCoreRows = 4;
 __global__ void core_select_kernel(ScanArgs a, int mode, unsigned maf_num, unsigned maf_den,
                                    int maf_filter, int32_t *n1, int8_t *core_status)
 {
@@ -47,17 +51,32 @@ __global__ void core_select_kernel(ScanArgs a, int mode, unsigned maf_num, unsig
     const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
     const unsigned n_total = (unsigned)(a.nA + a.nB);
-    for (long long k = a.k0 + warp; k < a.k1; k += nw) {
-        const unsigned int *row = (const unsigned int *)(a.hap + k * a.ld);
-        unsigned c = 0;
-        for (int w = lane; w < 2 * a.W; w += 32) c += (unsigned)__popc(__ldg(row + w) & valid32(a, w));
-        c = __reduce_add_sync(FULLMASK, c);
-        if (lane == 0) {
-            n1[k] = (int32_t)c;
-            const unsigned minor = c < n_total - c ? c : n_total - c;
-            const bool filt = (mode == 0 || maf_filter) &&
-                              (unsigned long long)maf_den * minor < (unsigned long long)maf_num * n_total;
-            core_status[k] = filt ? (int8_t)SELSCAN_LOCUS_MAF_FILTERED : (int8_t)0;
+    const unsigned long long *hap = (const unsigned long long *)a.hap;
+    for (long long k0 = a.k0 + warp * kCoreRows; k0 < a.k1; k0 += nw * kCoreRows) {
+        unsigned c[kCoreRows];
+#pragma unroll
+        for (int r = 0; r < kCoreRows; ++r) c[r] = 0u;
+        for (int w = lane; w < a.W; w += 32) {
+            const unsigned long long vm = (unsigned long long)valid32(a, 2 * w) |
+                                          ((unsigned long long)valid32(a, 2 * w + 1) << 32);
+            unsigned long long v[kCoreRows];
+#pragma unroll
+            for (int r = 0; r < kCoreRows; ++r)
+                v[r] = k0 + r < a.k1 ? __ldg(hap + (k0 + r) * a.ld + w) : 0ull;
+#pragma unroll
+            for (int r = 0; r < kCoreRows; ++r) c[r] += (unsigned)__popcll(v[r] & vm);
+        }
+#pragma unroll
+        for (int r = 0; r < kCoreRows; ++r) {
+            const unsigned cr = __reduce_add_sync(FULLMASK, c[r]);
+            const long long k = k0 + r;
+            if (lane == 0 && k < a.k1) {
+                n1[k] = (int32_t)cr;
+                const unsigned minor = cr < n_total - cr ? cr : n_total - cr;
+                const bool filt = (mode == 0 || maf_filter) &&
+                                  (unsigned long long)maf_den * minor < (unsigned long long)maf_num * n_total;
+                core_status[k] = filt ? (int8_t)SELSCAN_LOCUS_MAF_FILTERED : (int8_t)0;
+            }
         }
     }
 }
@@ -65,7 +84,8 @@ __global__ void core_select_kernel(ScanArgs a, int mode, unsigned maf_num, unsig
 cudaError_t launch_core_select(const ScanArgs &a, int mode, unsigned maf_num, unsigned maf_den,
                                int maf_filter, int32_t *n1, int8_t *core_status, cudaStream_t s)
 {
-    long long blocks = ((a.k1 - a.k0) * 32 + 255) / 256;
+    const long long warps = (a.k1 - a.k0 + kCoreRows - 1) / kCoreRows;
+    long long blocks = (warps * 32 + 255) / 256;
     if (blocks > 8192) blocks = 8192;
     if (blocks < 1) blocks = 1;
     core_select_kernel<<<(unsigned)blocks, 256, 0, s>>>(a, mode, maf_num, maf_den, maf_filter,
